@@ -1,0 +1,324 @@
+"""Benchmark of the GB300 hydro update (one RK2 step = the whole hot path).
+
+Default workload: 3D point blast, 256^3 cells on [-1, 1]^3, gamma = 1.4,
+reflecting walls, HLLC, FP32 storage/fluxes with FP64 recovery and reductions,
+C_CFL = 0.3, device-side CFL time step and conserved totals every step.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--precision fp32|fp64] [--solver hllc|hll] [--n 256]
+
+Prints one JSON line (rank 0).  Metric: cell-updates per second per RK stage
+(cells x 2 stages x steps / time), whole job.  With N > 1 (torchrun) every
+rank runs an independent replica of the workload ("replicas only": the
+single-grid update needs no data exchange between problems) and the value is
+the sum over ranks with the max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-updates/s per RK stage"
+UNIT = "cell-updates/s"
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--solver", default="hllc", choices=["hllc", "hll"])
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _workload(n, solver_name):
+    from paper_1207_3392_gb300 import problems as P
+    solver = P.HLLC if solver_name == "hllc" else P.HLL
+    return P.sedov_3d(n, solver=solver)
+
+
+def _config(args, n):
+    return {"workload": f"sedov3d_{n}^3_{args.solver}_{args.precision}",
+            "cells": n ** 3, "domain": "[-1,1]^3", "gamma": 1.4, "bc": "reflecting",
+            "solver": args.solver.upper(),
+            "precision": ("fp32 storage and fluxes, fp64 internal-energy recovery and reductions"
+                          if args.precision == "fp32" else "fp64"),
+            "cfl": 0.3, "step": "one TVD-RK2 step: 2 stage kernels + dt/totals finalize",
+            "l2": f"inputs larger than L2 (state {n**3 * 5 * (4 if args.precision == 'fp32' else 8) / 1e6:.0f} MB)",
+            "parallelism": "replicas" if args.gpus > 1 else "single GPU"}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index=0):
+        self.idx = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.idx), "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def cpu_baseline(n_sample=128, steps=2):
+    """The oracle, as it stands, on a bounded sample of the workload: the same
+    point blast at n_sample^3 for `steps` RK2 steps, all host cores."""
+    import oracle as O
+    from paper_1207_3392_gb300 import problems as P
+    cores = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    pr = P.sedov_3d(n_sample)
+    g = O.Grid(pr)
+    U = O.initial_state(pr, g)
+    t0 = time.perf_counter()
+    U, _, done = O.evolve(g, U, pr.cfl, max_steps=steps)
+    dt = time.perf_counter() - t0
+    return {"value": pr.ncells * 2 * done / dt, "unit": UNIT, "cores": int(os.environ["OMP_NUM_THREADS"]),
+            "kind": "oracle",
+            "sample": f"FP64 oracle, same point blast at {n_sample}^3 for {done} RK2 steps ({dt:.1f} s)"}
+
+
+def run_reference(args):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return
+    import oracle as O
+    from paper_1207_3392_gb300 import problems as P
+    n_sample = 128
+    cores = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    pr = P.sedov_3d(n_sample, solver=P.HLLC if args.solver == "hllc" else P.HLL)
+    g = O.Grid(pr)
+    U = O.initial_state(pr, g)
+    U, _, _ = O.evolve(g, U, pr.cfl, max_steps=args.warmup)
+    t0 = time.perf_counter()
+    U, _, done = O.evolve(g, U, pr.cfl, max_steps=args.steps)
+    el = time.perf_counter() - t0
+    val = pr.ncells * 2 * done / el
+    cfg = _config(args, args.n)
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / max(done, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"kind": "oracle", "cores": int(os.environ["OMP_NUM_THREADS"]), "value": val,
+                             "unit": UNIT,
+                             "sample": f"FP64 oracle, point blast at {n_sample}^3 (per-cell work of the "
+                                       f"{args.n}^3 workload), {done} timed steps"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_1207_3392_gb300 import build
+    from paper_1207_3392_gb300 import hydro as H
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build()
+    n = args.n
+    prob = _workload(n, args.solver)
+    prec = H.FP32_MIXED if args.precision == "fp32" else H.FP64
+    stream = torch.cuda.current_stream()
+    h = H.Hydro.from_problem(prob, precision=prec, stream=stream.cuda_stream)
+    del prob
+    cells = h.ncell
+    cfl = 0.3
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    # warm-up (also captures the one-step graph)
+    for _ in range(max(args.warmup, 3)):
+        h.advance(1, cfl, sync=False)
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        h.advance(1, cfl, sync=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    h.status()
+    value = world * cells * 2 / (ms * 1e-3)
+
+    # per-kernel durations (CUDA events between the launches on the same stream)
+    ks = [h.profile_step(cfl) for _ in range(args.steps)]
+    st1 = float(np.mean([k[0] for k in ks]))
+    fin = float(np.mean([k[1] for k in ks]))
+    st2 = float(np.mean([k[2] for k in ks]))
+    b = 4 if prec == H.FP32_MIXED else 8
+    nv = 5
+    bytes1, bytes2 = 2 * nv * b * cells, 3 * nv * b * cells
+    peak, peak_kind = _peaks()
+    dom = "stage2" if st2 >= st1 else "stage1"
+    dom_ms, dom_bytes = (st2, bytes2) if dom == "stage2" else (st1, bytes1)
+    achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": f"hydro_stage_kernel<3,{'float' if b == 4 else 'double'},"
+                                          f"{args.solver.upper()},{2 if dom == 'stage2' else 1}>",
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_source": f"{peak_kind} hbm_gbs", "traffic": None,
+                "algorithmic_bytes_per_cell": dom_bytes // cells,
+                "kernel_ms": {"stage1": st1, "finalize": fin, "stage2": st2},
+                "step_frac_hbm": (bytes1 + bytes2) / ((st1 + fin + st2) * 1e-3) / 1e9 / peak}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if prec == H.FP32_MIXED else "f64", "data": "synthetic",
+            "config": _config(args, n), "roofline": roofline, "clocks": clocks,
+            "gpu_launches": args.steps * h.launches_per_step()}
+
+    # end to end through the C ABI with host buffers: set_conserved (pinned
+    # host -> device), one step, get_conserved (device -> pinned host)
+    if not args.no_e2e:
+        host = torch.empty((h.nvar,) + h.shape, dtype=torch.float32 if b == 4 else torch.float64).pin_memory()
+        h.get_conserved(host)
+        k = max(3, min(args.steps, 10))
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(k):
+            h.set_conserved(host)
+            h.advance(1, cfl, sync=False)
+            h.get_conserved(host)
+        el = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([el], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        nbytes = host.numel() * host.element_size()
+        line["e2e"] = {"value": world * cells * 2 * k / el, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+                       "d2h_bytes_per_step": nbytes, "ms_per_step": 1e3 * el / k}
+    h.close()
+
+    # other precision / solver combinations of the same workload (context)
+    if not args.no_variants and rank == 0:
+        variants = {}
+        for pname, pc in (("fp32", H.FP32_MIXED), ("fp64", H.FP64)):
+            for sname in ("hllc", "hll"):
+                if (pname, sname) == (args.precision, args.solver):
+                    continue
+                pr = _workload(n, sname)
+                hv = H.Hydro.from_problem(pr, precision=pc, stream=stream.cuda_stream)
+                del pr
+                kv = 3 if pc == H.FP64 else 5
+                for _ in range(2):
+                    hv.advance(1, cfl, sync=False)
+                torch.cuda.synchronize()
+                a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                for _ in range(kv):
+                    hv.advance(1, cfl, sync=False)
+                z.record(stream)
+                torch.cuda.synchronize()
+                mv = a.elapsed_time(z) / kv
+                variants[f"{sname}_{pname}"] = {"value": cells * 2 / (mv * 1e-3), "ms_per_step": mv}
+                hv.close()
+        line["variants"] = variants
+
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,168 @@
+/*
+ * genasis_hydro.h -- C ABI of the GB300 (sm_103a) finite-volume update of
+ * nonrelativistic ideal hydrodynamics described in Cardall, Budiardja, Endeve
+ * & Mezzacappa, "GenASiS: General Astrophysical Simulation System. I.
+ * Refinable mesh and nonrelativistic hydrodynamics" (arXiv:1207.3392).
+ *
+ * The library advances the balance equations dU/dt = L[U] (Eq. BalanceEquation,
+ * no sources) on one single-level Cartesian mesh with non-uniform widths per
+ * axis:
+ *   - primitive recovery n = D, v = S / (m D), e = G - m n |v|^2 / 2,
+ *     p = (gamma - 1) e, m = 1                           (Sec. 3.5)
+ *   - limited linear reconstruction, Eq. MinMod with parameter theta  (Sec. 3.1)
+ *   - HLL (Eq. FluxHLL) or HLLC (Eqs. MiddleWaveSpeed..FluxHLLC) face fluxes (Sec. 3.2, 3.5)
+ *   - flux divergence, Eq. BalanceEquationAverage with A_q / V = 1 / dq
+ *   - second-order TVD Runge-Kutta (Heun), Eqs. Update, RungeKutta1-3  (Sec. 3.4)
+ *   - CFL time step, Eq. courantTimeStep times C_CFL      (Sec. 3.6)
+ *
+ * Conventions for every entry point
+ *   - Arrays are structure-of-arrays, C order, x fastest: element (v, k, j, i)
+ *     of a field with nv components sits at ((v * nz + k) * ny + j) * nx + i,
+ *     with ny = nz = 1 below 3D (nz = 1 in 2D).  Conserved fields have
+ *     nv = ndim + 2 components (D, S_1..S_ndim, G).
+ *   - Pointers marked "host or device" may point to host memory (pageable or
+ *     pinned) or to device memory of the current device; the library detects
+ *     which.  The caller keeps ownership of every pointer it passes; the
+ *     library copies what it needs before the call returns (or, for device
+ *     pointers, in stream order before the next call's work).
+ *   - The library owns all device state of a handle and frees it in
+ *     genasis_hydro_destroy.
+ *   - All work runs on the handle's CUDA stream.  Calls that return numbers to
+ *     the host (compute_dt, get_*, status) synchronise that stream; the others
+ *     are asynchronous.
+ *   - Every call returns GENASIS_OK or a negative error code and never aborts.
+ *     genasis_hydro_last_error() describes the last failure of the calling
+ *     thread.  A non-physical state (rho <= 0, p <= 0, or a non-finite value)
+ *     detected on the device sets a sticky status reported by
+ *     genasis_hydro_status and by every later synchronising call.
+ *   - A handle must not be used from two host threads at once.
+ */
+#ifndef GENASIS_HYDRO_H
+#define GENASIS_HYDRO_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GENASIS_OK 0
+#define GENASIS_EINVAL (-1)    /* bad argument */
+#define GENASIS_ENOMEM (-2)    /* device allocation failed */
+#define GENASIS_ECUDA (-3)     /* CUDA runtime error */
+#define GENASIS_ENONPHYS (-4)  /* rho <= 0, p <= 0 or non-finite value met on the device */
+#define GENASIS_ETIMEOUT (-5)  /* a bounded device wait gave up */
+
+#define GENASIS_HLL 0
+#define GENASIS_HLLC 1
+
+#define GENASIS_BC_PERIODIC 0  /* wrap-around */
+#define GENASIS_BC_REFLECT 1   /* mirror, normal momentum negated */
+#define GENASIS_BC_OUTFLOW 2   /* copy of the edge cell */
+
+#define GENASIS_FP64 0         /* state stored and processed in FP64 */
+#define GENASIS_FP32_MIXED 1   /* state stored and fluxes in FP32; internal-energy
+                                  cancellation, dt and totals reductions in FP64 */
+
+typedef struct genasis_hydro *genasis_hydro_t;
+
+/* Mesh and solver description (Sec. 2 mesh, single level; Secs. 3.1-3.5).
+ *   ndim        1, 2 or 3
+ *   n[q]        cells along axis q (>= 2 on active axes; ignored beyond ndim)
+ *   widths[q]   host pointer to n[q] strictly positive cell widths along q
+ *   bc_lo/hi[q] GENASIS_BC_* at the low / high end of axis q (periodic must be
+ *               set on both ends)
+ *   gamma       adiabatic index of p = (gamma - 1) e (> 1)
+ *   solver      GENASIS_HLL or GENASIS_HLLC
+ *   theta       slope limiter parameter of Eq. MinMod, in [1, 2] (paper: 1.4)
+ *   precision   GENASIS_FP64 or GENASIS_FP32_MIXED
+ *   stream      cudaStream_t to run on, or NULL for a stream owned by the handle */
+typedef struct {
+  int ndim;
+  int n[3];
+  const double *widths[3];
+  int bc_lo[3];
+  int bc_hi[3];
+  double gamma;
+  int solver;
+  double theta;
+  int precision;
+  void *stream;
+} genasis_hydro_desc;
+
+/* Create a handle: validates desc, allocates the device state (two state
+ * buffers, the stage buffer, geometry tables, reduction partials) and picks
+ * the default tile shape.  The state is zero until set_primitive or
+ * set_conserved.  Returns EINVAL on a bad description, ENOMEM, ECUDA. */
+int genasis_hydro_create(const genasis_hydro_desc *desc, genasis_hydro_t *out);
+
+/* Release every device resource of h (synchronises its stream).  NULL is OK. */
+int genasis_hydro_destroy(genasis_hydro_t h);
+
+/* Set the state from primitives (Eqs. BalancedBaryonDensity, MomentumDensity,
+ * balancedEnergy with p = (gamma-1) e): rho[ncell], vel[ndim * ncell] (one
+ * plane per axis), p[ncell]; FP64, host or device.  Resets time to 0. */
+int genasis_hydro_set_primitive(genasis_hydro_t h, const double *rho, const double *vel, const double *p);
+
+/* Set / read the conserved state U[(ndim + 2) * ncell] in the given precision
+ * (GENASIS_FP64 = double, GENASIS_FP32_MIXED = float), host or device,
+ * converting if it differs from the handle's.  get_conserved synchronises. */
+int genasis_hydro_set_conserved(genasis_hydro_t h, const void *U, int precision);
+int genasis_hydro_get_conserved(genasis_hydro_t h, void *U, int precision);
+
+/* dt = cfl * dt_CFL of the current state (Eq. courantTimeStep); synchronises. */
+int genasis_hydro_compute_dt(genasis_hydro_t h, double cfl, double *dt);
+
+/* One full RK2 step (Eqs. RungeKutta1-3) with the given dt (> 0); asynchronous. */
+int genasis_hydro_step(genasis_hydro_t h, double dt);
+
+/* nsteps RK2 steps, each with dt = cfl * dt_CFL taken on the device from the
+ * state at the start of the step; if t_end > 0 the last step is shortened so
+ * that time stops exactly at t_end and later steps do nothing (Algorithm
+ * Evolve, single level).  Runs as one CUDA graph launch (captured on first use
+ * per (nsteps, cfl, t_end)).  If t_out is non-NULL it synchronises and stores
+ * the time reached. */
+int genasis_hydro_advance(genasis_hydro_t h, int nsteps, double cfl, double t_end, double *t_out);
+
+/* Current time (synchronises) / reset the time counter. */
+int genasis_hydro_get_time(genasis_hydro_t h, double *t);
+int genasis_hydro_set_time(genasis_hydro_t h, double t);
+
+/* Volume-integrated conserved totals sum_cells U dV, FP64, of the current
+ * state: totals[0 .. ndim + 1] (Sec. 3.3 conservation tally).  Synchronises. */
+int genasis_hydro_get_totals(genasis_hydro_t h, double *totals);
+
+/* Synchronise and return GENASIS_ENONPHYS if the sticky device status is set,
+ * else GENASIS_OK; clear_status resets it. */
+int genasis_hydro_status(genasis_hydro_t h);
+int genasis_hydro_clear_status(genasis_hydro_t h);
+
+/* Launch configuration: tile index (0 .. tile_count - 1 for this ndim) and
+ * planes per CTA along the march axis (0 = automatic).  info[0..5] receives
+ * (tile index, tile x, tile y, planes per CTA, CTAs per stage, tile count). */
+int genasis_hydro_set_tile(genasis_hydro_t h, int tile, int kchunk);
+int genasis_hydro_get_tile(genasis_hydro_t h, int *info);
+
+/* Time every compiled tile shape (and a few plane counts) on the current
+ * state for `trial_steps` steps each, keep the fastest, restore the state.
+ * If cache_path is non-NULL the choice is read from / appended to that text
+ * file, keyed by (ndim, n, precision, solver).  Synchronises. */
+int genasis_hydro_autotune(genasis_hydro_t h, int trial_steps, const char *cache_path);
+
+/* Number of kernel launches one step enqueues. */
+int genasis_hydro_launches_per_step(genasis_hydro_t h);
+
+/* One CFL step like genasis_hydro_advance(h, 1, cfl, 0, NULL), launched
+ * kernel by kernel with CUDA events around each launch on the handle's stream;
+ * ms[0..2] receive the device durations of stage 1, the dt/totals
+ * finalisation and stage 2 (milliseconds).  Synchronises. */
+int genasis_hydro_profile_step(genasis_hydro_t h, double cfl, float *ms);
+
+/* Text of the last error of the calling thread (never NULL). */
+const char *genasis_hydro_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GENASIS_HYDRO_H */

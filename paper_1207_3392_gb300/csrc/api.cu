@@ -1,0 +1,747 @@
+// api.cu -- host runtime behind include/genasis_hydro.h: handle lifetime,
+// device memory, geometry tables, launch configuration, CUDA-graph capture of
+// multi-step advances, and the tile autotuner.
+#include <cuda_runtime.h>
+
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "genasis_hydro.h"
+#include "aux_kernels.h"
+#include "hydro_device.cuh"
+#include "registry.h"
+#include "stage_kernel.cuh"
+
+namespace gh {
+
+static thread_local char g_err[512] = "no error";
+
+int fail(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+#define GH_CK(call)                                                                          \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess)                                                                   \
+      return fail(e_ == cudaErrorMemoryAllocation ? GENASIS_ENOMEM : GENASIS_ECUDA, "%s: %s", \
+                  #call, cudaGetErrorString(e_));                                            \
+  } while (0)
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+int tile_count(int ndim) { return ndim == 1 ? tile_count_1d() : ndim == 2 ? tile_count_2d() : tile_count_3d(); }
+
+bool stage_variant(int ndim, bool fp64, int solver, int stage, int tile, StageVariant* out) {
+  if (ndim == 1) return stage_variant_1d(fp64, solver, stage, tile, out);
+  if (ndim == 2) return stage_variant_2d(fp64, solver, stage, tile, out);
+  return fp64 ? stage_variant_3d_f64(solver, stage, tile, out) : stage_variant_3d_f32(solver, stage, tile, out);
+}
+
+int stage_tile_count(int ndim) { return tile_count(ndim); }
+
+}  // namespace gh
+
+using namespace gh;
+
+struct genasis_hydro {
+  int ndim = 0, nv = 0, n[3] = {1, 1, 1}, bc_lo[3] = {0, 0, 0}, bc_hi[3] = {0, 0, 0};
+  double gamma = 1.4, theta = 1.4;
+  int solver = 1, prec = 0;
+  size_t ncell = 0, esize = 8;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int device = 0, num_sms = 0;
+  void* U[2] = {nullptr, nullptr};
+  int cur = 0;
+  void* K = nullptr;
+  void* geo[3] = {nullptr, nullptr, nullptr};
+  void* iw[3] = {nullptr, nullptr, nullptr};
+  double* wd[3] = {nullptr, nullptr, nullptr};
+  double* part_speed = nullptr;
+  double* part_tot = nullptr;
+  size_t part_cap = 0;  // blocks the partial buffers hold
+  double* scal = nullptr;
+  unsigned* status = nullptr;
+  // launch configuration
+  int tile = 0, kchunk_req = 0, kchunk = 1;
+  StageVariant v1{}, v2{};
+  dim3 grid;
+  int want_totals = 1;
+  // cached graphs of `advance`, one per starting state buffer
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  int g_nsteps = -1;
+  double g_cfl = 0, g_tend = 0;
+};
+
+namespace {
+
+int validate(const genasis_hydro_desc* d) {
+  if (!d) return fail(GENASIS_EINVAL, "desc is NULL");
+  if (d->ndim < 1 || d->ndim > 3) return fail(GENASIS_EINVAL, "ndim must be 1, 2 or 3 (got %d)", d->ndim);
+  for (int q = 0; q < d->ndim; ++q) {
+    if (d->n[q] < 2) return fail(GENASIS_EINVAL, "n[%d] = %d: need at least 2 cells", q, d->n[q]);
+    if (!d->widths[q]) return fail(GENASIS_EINVAL, "widths[%d] is NULL", q);
+    for (int i = 0; i < d->n[q]; ++i)
+      if (!(d->widths[q][i] > 0.0) || !isfinite(d->widths[q][i]))
+        return fail(GENASIS_EINVAL, "widths[%d][%d] = %g is not a positive finite width", q, i, d->widths[q][i]);
+    for (int s = 0; s < 2; ++s) {
+      int bc = s ? d->bc_hi[q] : d->bc_lo[q];
+      if (bc < 0 || bc > 2) return fail(GENASIS_EINVAL, "bad boundary code %d on axis %d", bc, q);
+    }
+    if ((d->bc_lo[q] == GENASIS_BC_PERIODIC) != (d->bc_hi[q] == GENASIS_BC_PERIODIC))
+      return fail(GENASIS_EINVAL, "axis %d: periodic must be set on both ends", q);
+  }
+  if (!(d->gamma > 1.0) || !isfinite(d->gamma)) return fail(GENASIS_EINVAL, "gamma must be > 1");
+  if (d->solver != GENASIS_HLL && d->solver != GENASIS_HLLC) return fail(GENASIS_EINVAL, "bad solver %d", d->solver);
+  if (!(d->theta >= 1.0 && d->theta <= 2.0)) return fail(GENASIS_EINVAL, "theta must lie in [1, 2]");
+  if (d->precision != GENASIS_FP64 && d->precision != GENASIS_FP32_MIXED)
+    return fail(GENASIS_EINVAL, "bad precision %d", d->precision);
+  size_t cells = 1;
+  for (int q = 0; q < d->ndim; ++q) {
+    cells *= (size_t)d->n[q];
+    if (cells > ((size_t)1 << 34)) return fail(GENASIS_EINVAL, "mesh too large");
+  }
+  return GENASIS_OK;
+}
+
+// Widths including two ghost cells on each side, by the boundary rule.
+std::vector<double> extended_widths(const double* w, int n, int lo, int hi) {
+  std::vector<double> e(n + 4);
+  for (int c = -2; c < n + 2; ++c) {
+    int s = c;
+    if (c < 0) s = lo == GENASIS_BC_PERIODIC ? c + n : lo == GENASIS_BC_REFLECT ? -1 - c : 0;
+    else if (c >= n) s = hi == GENASIS_BC_PERIODIC ? c - n : hi == GENASIS_BC_REFLECT ? 2 * n - 1 - c : n - 1;
+    e[c + 2] = w[s];
+  }
+  return e;
+}
+
+// Reconstruction geometry (Eq. MinMod with centre distances of a non-uniform
+// Cartesian mesh): q_c - q_- = (d_{c-1} + d_c)/2, q_+ - q_- = d_{c-1}/2 + d_c +
+// d_{c+1}/2, q_+ - q_c = (d_c + d_{c+1})/2, face offset d_c / 2.
+template <class T>
+void build_geometry(const std::vector<double>& e, std::vector<Geo<T>>& geo, std::vector<T>& iw) {
+  const int m = (int)e.size();
+  geo.resize(m);
+  iw.resize(m);
+  for (int k = 0; k < m; ++k) {
+    const double dc = e[k];
+    const double dm = e[k > 0 ? k - 1 : 0], dp = e[k + 1 < m ? k + 1 : m - 1];
+    geo[k].icm = (T)(1.0 / (0.5 * (dm + dc)));
+    geo[k].ipm = (T)(1.0 / (0.5 * dm + dc + 0.5 * dp));
+    geo[k].ipc = (T)(1.0 / (0.5 * (dc + dp)));
+    geo[k].h = (T)(0.5 * dc);
+    iw[k] = (T)(1.0 / dc);
+  }
+}
+
+template <class T>
+int upload_geometry(genasis_hydro* h, const genasis_hydro_desc* d) {
+  for (int q = 0; q < 3; ++q) {
+    std::vector<double> w;
+    if (q < h->ndim) w.assign(d->widths[q], d->widths[q] + d->n[q]);
+    else w.assign(2, 1.0);  // inactive axis: unit width, never read as a flux axis
+    const int n = q < h->ndim ? d->n[q] : 1;
+    std::vector<double> e = extended_widths(w.data(), n < 2 ? 2 : n, h->bc_lo[q], h->bc_hi[q]);
+    std::vector<Geo<T>> geo;
+    std::vector<T> iw;
+    build_geometry<T>(e, geo, iw);
+    GH_CK(cudaMalloc(&h->geo[q], geo.size() * sizeof(Geo<T>)));
+    GH_CK(cudaMalloc(&h->iw[q], iw.size() * sizeof(T)));
+    GH_CK(cudaMalloc(&h->wd[q], w.size() * sizeof(double)));
+    GH_CK(cudaMemcpy(h->geo[q], geo.data(), geo.size() * sizeof(Geo<T>), cudaMemcpyHostToDevice));
+    GH_CK(cudaMemcpy(h->iw[q], iw.data(), iw.size() * sizeof(T), cudaMemcpyHostToDevice));
+    GH_CK(cudaMemcpy(h->wd[q], w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice));
+  }
+  return GENASIS_OK;
+}
+
+int configure(genasis_hydro* h, int tile, int kchunk_req) {
+  if (tile < 0 || tile >= tile_count(h->ndim)) return fail(GENASIS_EINVAL, "tile %d out of range", tile);
+  StageVariant v1, v2;
+  const bool fp64 = h->prec == GENASIS_FP64;
+  if (!stage_variant(h->ndim, fp64, h->solver, 1, tile, &v1) || !stage_variant(h->ndim, fp64, h->solver, 2, tile, &v2))
+    return fail(GENASIS_EINVAL, "no compiled kernel for this configuration");
+  const int gx = (h->n[0] + v1.tx - 1) / v1.tx;
+  const int gy = h->ndim == 3 ? (h->n[1] + v1.ty - 1) / v1.ty : 1;
+  const int nm = h->ndim >= 2 ? h->n[h->ndim - 1] : 1;
+  int kchunk = 1, gz = 1;
+  if (h->ndim >= 2) {
+    if (kchunk_req > 0) {
+      kchunk = kchunk_req;
+    } else {
+      // about four CTAs per SM per stage, at least 8 planes per CTA
+      const long target = 4L * h->num_sms;
+      long chunks = (target + (long)gx * gy - 1) / ((long)gx * gy);
+      long maxchunks = nm / 8 > 0 ? nm / 8 : 1;
+      if (chunks > maxchunks) chunks = maxchunks;
+      if (chunks < 1) chunks = 1;
+      kchunk = (int)((nm + chunks - 1) / chunks);
+    }
+    if (kchunk > nm) kchunk = nm;
+    gz = (nm + kchunk - 1) / kchunk;
+  }
+  const size_t nblk = (size_t)gx * gy * gz;
+  for (const StageVariant* v : {&v1, &v2}) {
+    if (v->smem > 48 * 1024) {
+      GH_CK(cudaFuncSetAttribute(v->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v->smem));
+    }
+  }
+  const size_t need = nblk > 4096 ? nblk : 4096;
+  if (need > h->part_cap) {
+    if (h->part_speed) cudaFree(h->part_speed);
+    if (h->part_tot) cudaFree(h->part_tot);
+    h->part_speed = nullptr;
+    h->part_tot = nullptr;
+    GH_CK(cudaMalloc(&h->part_speed, need * sizeof(double)));
+    GH_CK(cudaMalloc(&h->part_tot, need * 5 * sizeof(double)));
+    h->part_cap = need;
+  }
+  h->v1 = v1;
+  h->v2 = v2;
+  h->tile = tile;
+  h->kchunk_req = kchunk_req;
+  h->kchunk = kchunk;
+  h->grid = dim3(gx, gy, gz);
+  for (int b = 0; b < 2; ++b)
+    if (h->graph[b]) {
+      cudaGraphExecDestroy(h->graph[b]);
+      h->graph[b] = nullptr;
+    }
+  return GENASIS_OK;
+}
+
+template <class T>
+StageArgs<T> stage_args(genasis_hydro* h, int stage) {
+  StageArgs<T> A;
+  memset(&A, 0, sizeof(A));
+  for (int q = 0; q < 3; ++q) {
+    A.n[q] = h->n[q];
+    A.bc_lo[q] = h->bc_lo[q];
+    A.bc_hi[q] = h->bc_hi[q];
+    A.geo[q] = (const Geo<T>*)h->geo[q];
+    A.iw[q] = (const T*)h->iw[q];
+    A.wd[q] = h->wd[q];
+  }
+  A.gamma = (T)h->gamma;
+  A.gm1 = (T)(h->gamma - 1.0);
+  A.theta = (T)h->theta;
+  A.un = (const T*)h->U[h->cur];
+  A.k1 = (const T*)h->K;
+  A.out = stage == 1 ? (T*)h->K : (T*)h->U[1 - h->cur];
+  A.dt = h->scal + SCAL_DT;
+  A.kchunk = h->kchunk;
+  A.part_speed = h->part_speed;
+  A.part_tot = h->part_tot;
+  A.status = h->status;
+  A.want_totals = h->want_totals;
+  return A;
+}
+
+template <class T>
+int enqueue_step_t(genasis_hydro* h, int mode, double fixed_dt, double cfl, double t_end, cudaEvent_t* ev) {
+  const dim3 block(h->v1.tx * h->v1.ty);
+  StageArgs<T> a1 = stage_args<T>(h, 1);
+  void* p1[] = {&a1};
+  if (ev) GH_CK(cudaEventRecord(ev[0], h->stream));
+  GH_CK(cudaLaunchKernel(h->v1.fn, h->grid, block, p1, h->v1.smem, h->stream));
+  if (ev) GH_CK(cudaEventRecord(ev[1], h->stream));
+  FinalizeArgs F;
+  F.part_speed = h->part_speed;
+  F.part_tot = h->want_totals ? h->part_tot : nullptr;
+  F.nblk = (int)(h->grid.x * h->grid.y * h->grid.z);
+  F.nv = h->nv;
+  F.mode = mode;
+  F.cfl = cfl;
+  F.fixed_dt = fixed_dt;
+  F.t_end = t_end;
+  F.scal = h->scal;
+  F.status = h->status;
+  GH_CK(launch_finalize(F, h->stream));
+  if (ev) GH_CK(cudaEventRecord(ev[2], h->stream));
+  StageArgs<T> a2 = stage_args<T>(h, 2);
+  void* p2[] = {&a2};
+  GH_CK(cudaLaunchKernel(h->v2.fn, h->grid, block, p2, h->v2.smem, h->stream));
+  if (ev) GH_CK(cudaEventRecord(ev[3], h->stream));
+  h->cur = 1 - h->cur;
+  return GENASIS_OK;
+}
+
+int enqueue_step(genasis_hydro* h, int mode, double fixed_dt, double cfl, double t_end,
+                 cudaEvent_t* ev = nullptr) {
+  return h->prec == GENASIS_FP64 ? enqueue_step_t<double>(h, mode, fixed_dt, cfl, t_end, ev)
+                                 : enqueue_step_t<float>(h, mode, fixed_dt, cfl, t_end, ev);
+}
+
+template <class T>
+ReduceArgs<T> reduce_args(genasis_hydro* h) {
+  ReduceArgs<T> A;
+  memset(&A, 0, sizeof(A));
+  A.ncell = h->ncell;
+  for (int q = 0; q < 3; ++q) {
+    A.n[q] = h->n[q];
+    A.iw[q] = (const T*)h->iw[q];
+    A.wd[q] = h->wd[q];
+  }
+  A.gamma = h->gamma;
+  A.U = (const T*)h->U[h->cur];
+  A.part_speed = h->part_speed;
+  A.part_tot = h->part_tot;
+  A.status = h->status;
+  size_t nb = (h->ncell + 255) / 256;
+  A.nblk = (int)(nb > 2048 ? 2048 : (nb < 1 ? 1 : nb));
+  return A;
+}
+
+int reduce_now(genasis_hydro* h, bool speed) {
+  int nblk;
+  if (h->prec == GENASIS_FP64) {
+    ReduceArgs<double> A = reduce_args<double>(h);
+    nblk = A.nblk;
+    GH_CK(speed ? launch_speed<double>(h->ndim, A, h->stream) : launch_totals<double>(h->ndim, A, h->stream));
+  } else {
+    ReduceArgs<float> A = reduce_args<float>(h);
+    nblk = A.nblk;
+    GH_CK(speed ? launch_speed<float>(h->ndim, A, h->stream) : launch_totals<float>(h->ndim, A, h->stream));
+  }
+  FinalizeArgs F;
+  memset(&F, 0, sizeof(F));
+  F.part_speed = speed ? h->part_speed : nullptr;
+  F.part_tot = speed ? nullptr : h->part_tot;
+  F.nblk = nblk;
+  F.nv = h->nv;
+  F.mode = FIN_REDUCE;
+  F.scal = h->scal;
+  F.status = h->status;
+  GH_CK(launch_finalize(F, h->stream));
+  return GENASIS_OK;
+}
+
+int sync_status(genasis_hydro* h) {
+  unsigned st = 0;
+  GH_CK(cudaMemcpyAsync(&st, h->status, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
+  GH_CK(cudaStreamSynchronize(h->stream));
+  if (st & STATUS_NONPHYS) return fail(GENASIS_ENONPHYS, "non-physical state (rho <= 0, p <= 0 or NaN) on the device");
+  if (st & STATUS_TIMEOUT) return fail(GENASIS_ETIMEOUT, "a bounded device wait gave up");
+  return GENASIS_OK;
+}
+
+// Copy `count` elements of precision `src_prec` from src (host or device) into
+// device buffer dst of the handle's precision.
+int import_array(genasis_hydro* h, const void* src, int src_prec, size_t count, void* dst) {
+  const size_t ssize = src_prec == GENASIS_FP64 ? 8 : 4;
+  const bool dev = is_device_ptr(src);
+  if (src_prec == h->prec) {
+    GH_CK(cudaMemcpyAsync(dst, src, count * ssize, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+    return GENASIS_OK;
+  }
+  const void* dsrc = src;
+  void* tmp = nullptr;
+  if (!dev) {
+    GH_CK(cudaMallocAsync(&tmp, count * ssize, h->stream));
+    GH_CK(cudaMemcpyAsync(tmp, src, count * ssize, cudaMemcpyHostToDevice, h->stream));
+    dsrc = tmp;
+  }
+  cudaError_t e = src_prec == GENASIS_FP64
+                      ? launch_convert<double, float>(count, (const double*)dsrc, (float*)dst, h->stream)
+                      : launch_convert<float, double>(count, (const float*)dsrc, (double*)dst, h->stream);
+  if (tmp) cudaFreeAsync(tmp, h->stream);
+  GH_CK(e);
+  return GENASIS_OK;
+}
+
+int free_all(genasis_hydro* h) {
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  for (int b = 0; b < 2; ++b)
+    if (h->graph[b]) cudaGraphExecDestroy(h->graph[b]);
+  for (int b = 0; b < 2; ++b) cudaFree(h->U[b]);
+  cudaFree(h->K);
+  for (int q = 0; q < 3; ++q) {
+    cudaFree(h->geo[q]);
+    cudaFree(h->iw[q]);
+    cudaFree(h->wd[q]);
+  }
+  cudaFree(h->part_speed);
+  cudaFree(h->part_tot);
+  cudaFree(h->scal);
+  cudaFree(h->status);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+  return GENASIS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* genasis_hydro_last_error(void) { return g_err; }
+
+int genasis_hydro_create(const genasis_hydro_desc* d, genasis_hydro_t* out) {
+  if (!out) return fail(GENASIS_EINVAL, "out is NULL");
+  *out = nullptr;
+  int rc = validate(d);
+  if (rc) return rc;
+  genasis_hydro* h = new genasis_hydro();
+  h->ndim = d->ndim;
+  h->nv = d->ndim + 2;
+  h->ncell = 1;
+  for (int q = 0; q < 3; ++q) {
+    h->n[q] = q < d->ndim ? d->n[q] : 1;
+    h->bc_lo[q] = q < d->ndim ? d->bc_lo[q] : GENASIS_BC_OUTFLOW;
+    h->bc_hi[q] = q < d->ndim ? d->bc_hi[q] : GENASIS_BC_OUTFLOW;
+    h->ncell *= (size_t)h->n[q];
+  }
+  h->gamma = d->gamma;
+  h->theta = d->theta;
+  h->solver = d->solver;
+  h->prec = d->precision;
+  h->esize = h->prec == GENASIS_FP64 ? 8 : 4;
+#define GH_CK_CREATE(call)                                                                          \
+  do {                                                                                              \
+    cudaError_t e_ = (call);                                                                        \
+    if (e_ != cudaSuccess) {                                                                        \
+      int code_ = fail(e_ == cudaErrorMemoryAllocation ? GENASIS_ENOMEM : GENASIS_ECUDA, "%s: %s", #call, \
+                       cudaGetErrorString(e_));                                                     \
+      free_all(h);                                                                                  \
+      return code_;                                                                                 \
+    }                                                                                               \
+  } while (0)
+  GH_CK_CREATE(cudaGetDevice(&h->device));
+  GH_CK_CREATE(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device));
+  if (d->stream) {
+    h->stream = (cudaStream_t)d->stream;
+  } else {
+    GH_CK_CREATE(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+    h->own_stream = true;
+  }
+  const size_t bytes = h->ncell * h->nv * h->esize;
+  for (int b = 0; b < 2; ++b) {
+    GH_CK_CREATE(cudaMalloc(&h->U[b], bytes));
+    GH_CK_CREATE(cudaMemsetAsync(h->U[b], 0, bytes, h->stream));
+  }
+  GH_CK_CREATE(cudaMalloc(&h->K, bytes));
+  GH_CK_CREATE(cudaMalloc(&h->scal, SCAL_COUNT * sizeof(double)));
+  GH_CK_CREATE(cudaMemsetAsync(h->scal, 0, SCAL_COUNT * sizeof(double), h->stream));
+  GH_CK_CREATE(cudaMalloc(&h->status, sizeof(unsigned)));
+  GH_CK_CREATE(cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream));
+  rc = h->prec == GENASIS_FP64 ? upload_geometry<double>(h, d) : upload_geometry<float>(h, d);
+  if (!rc) rc = configure(h, 0, 0);
+  if (rc) {
+    free_all(h);
+    return rc;
+  }
+  GH_CK_CREATE(cudaStreamSynchronize(h->stream));
+#undef GH_CK_CREATE
+  *out = h;
+  return GENASIS_OK;
+}
+
+int genasis_hydro_destroy(genasis_hydro_t h) {
+  if (!h) return GENASIS_OK;
+  return free_all(h);
+}
+
+int genasis_hydro_set_primitive(genasis_hydro_t h, const double* rho, const double* vel, const double* p) {
+  if (!h || !rho || !vel || !p) return fail(GENASIS_EINVAL, "NULL argument");
+  const double* src[3] = {rho, vel, p};
+  const size_t cnt[3] = {h->ncell, h->ncell * h->ndim, h->ncell};
+  double* dev[3] = {nullptr, nullptr, nullptr};
+  int rc = GENASIS_OK;
+  for (int a = 0; a < 3 && !rc; ++a) {
+    if (is_device_ptr(src[a])) continue;
+    cudaError_t e = cudaMallocAsync((void**)&dev[a], cnt[a] * sizeof(double), h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dev[a], src[a], cnt[a] * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) rc = fail(GENASIS_ECUDA, "staging primitives: %s", cudaGetErrorString(e));
+  }
+  if (!rc) {
+    const double* r = dev[0] ? dev[0] : rho;
+    const double* v = dev[1] ? dev[1] : vel;
+    const double* pp = dev[2] ? dev[2] : p;
+    cudaError_t e = h->prec == GENASIS_FP64
+                        ? launch_init_from_primitive<double>(h->ndim, h->ncell, h->gamma, r, v, pp, (double*)h->U[h->cur], h->stream)
+                        : launch_init_from_primitive<float>(h->ndim, h->ncell, h->gamma, r, v, pp, (float*)h->U[h->cur], h->stream);
+    if (e != cudaSuccess) rc = fail(GENASIS_ECUDA, "init kernel: %s", cudaGetErrorString(e));
+  }
+  for (int a = 0; a < 3; ++a)
+    if (dev[a]) cudaFreeAsync(dev[a], h->stream);
+  if (!rc) {
+    GH_CK(cudaMemsetAsync(h->scal + SCAL_T, 0, sizeof(double), h->stream));
+    if (!is_device_ptr(rho) || !is_device_ptr(vel) || !is_device_ptr(p)) GH_CK(cudaStreamSynchronize(h->stream));
+  }
+  return rc;
+}
+
+int genasis_hydro_set_conserved(genasis_hydro_t h, const void* U, int precision) {
+  if (!h || !U) return fail(GENASIS_EINVAL, "NULL argument");
+  if (precision != GENASIS_FP64 && precision != GENASIS_FP32_MIXED) return fail(GENASIS_EINVAL, "bad precision");
+  int rc = import_array(h, U, precision, h->ncell * h->nv, h->U[h->cur]);
+  if (rc) return rc;
+  if (!is_device_ptr(U)) GH_CK(cudaStreamSynchronize(h->stream));
+  return GENASIS_OK;
+}
+
+int genasis_hydro_get_conserved(genasis_hydro_t h, void* U, int precision) {
+  if (!h || !U) return fail(GENASIS_EINVAL, "NULL argument");
+  if (precision != GENASIS_FP64 && precision != GENASIS_FP32_MIXED) return fail(GENASIS_EINVAL, "bad precision");
+  const size_t count = h->ncell * h->nv;
+  const bool dev = is_device_ptr(U);
+  if (precision == h->prec) {
+    GH_CK(cudaMemcpyAsync(U, h->U[h->cur], count * h->esize, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                          h->stream));
+  } else {
+    const size_t dsize = precision == GENASIS_FP64 ? 8 : 4;
+    void* dst = U;
+    if (!dev) GH_CK(cudaMallocAsync(&dst, count * dsize, h->stream));
+    cudaError_t e = h->prec == GENASIS_FP64
+                        ? launch_convert<double, float>(count, (const double*)h->U[h->cur], (float*)dst, h->stream)
+                        : launch_convert<float, double>(count, (const float*)h->U[h->cur], (double*)dst, h->stream);
+    GH_CK(e);
+    if (!dev) {
+      GH_CK(cudaMemcpyAsync(U, dst, count * dsize, cudaMemcpyDeviceToHost, h->stream));
+      GH_CK(cudaFreeAsync(dst, h->stream));
+    }
+  }
+  return sync_status(h);
+}
+
+int genasis_hydro_compute_dt(genasis_hydro_t h, double cfl, double* dt) {
+  if (!h || !dt) return fail(GENASIS_EINVAL, "NULL argument");
+  if (!(cfl > 0.0)) return fail(GENASIS_EINVAL, "cfl must be > 0");
+  int rc = reduce_now(h, true);
+  if (rc) return rc;
+  double v = 0;
+  GH_CK(cudaMemcpyAsync(&v, h->scal + SCAL_DTCFL, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  rc = sync_status(h);
+  if (rc) return rc;
+  *dt = cfl * v;
+  return GENASIS_OK;
+}
+
+int genasis_hydro_step(genasis_hydro_t h, double dt) {
+  if (!h) return fail(GENASIS_EINVAL, "NULL handle");
+  if (!(dt > 0.0) || !isfinite(dt)) return fail(GENASIS_EINVAL, "dt must be positive and finite");
+  return enqueue_step(h, FIN_FIXED, dt, 0.0, 0.0);
+}
+
+int genasis_hydro_advance(genasis_hydro_t h, int nsteps, double cfl, double t_end, double* t_out) {
+  if (!h) return fail(GENASIS_EINVAL, "NULL handle");
+  if (nsteps < 0) return fail(GENASIS_EINVAL, "nsteps < 0");
+  if (!(cfl > 0.0)) return fail(GENASIS_EINVAL, "cfl must be > 0");
+  if (nsteps > 0) {
+    const int cur0 = h->cur;
+    if (h->g_nsteps != nsteps || h->g_cfl != cfl || h->g_tend != t_end) {
+      for (int b = 0; b < 2; ++b)
+        if (h->graph[b]) {
+          cudaGraphExecDestroy(h->graph[b]);
+          h->graph[b] = nullptr;
+        }
+      h->g_nsteps = nsteps;
+      h->g_cfl = cfl;
+      h->g_tend = t_end;
+    }
+    if (!h->graph[cur0]) {
+      cudaGraph_t g;
+      GH_CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+      int rc = GENASIS_OK;
+      for (int s = 0; s < nsteps && !rc; ++s) rc = enqueue_step(h, FIN_CFL, 0.0, cfl, t_end);
+      cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+      h->cur = cur0;
+      if (rc) {
+        if (e == cudaSuccess) cudaGraphDestroy(g);
+        return rc;
+      }
+      GH_CK(e);
+      e = cudaGraphInstantiate(&h->graph[cur0], g, 0);
+      cudaGraphDestroy(g);
+      GH_CK(e);
+    }
+    GH_CK(cudaGraphLaunch(h->graph[cur0], h->stream));
+    h->cur = cur0 ^ (nsteps & 1);
+  }
+  if (t_out) {
+    GH_CK(cudaMemcpyAsync(t_out, h->scal + SCAL_T, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    return sync_status(h);
+  }
+  return GENASIS_OK;
+}
+
+int genasis_hydro_get_time(genasis_hydro_t h, double* t) {
+  if (!h || !t) return fail(GENASIS_EINVAL, "NULL argument");
+  GH_CK(cudaMemcpyAsync(t, h->scal + SCAL_T, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  GH_CK(cudaStreamSynchronize(h->stream));
+  return GENASIS_OK;
+}
+
+int genasis_hydro_set_time(genasis_hydro_t h, double t) {
+  if (!h || !isfinite(t)) return fail(GENASIS_EINVAL, "bad argument");
+  GH_CK(cudaMemcpyAsync(h->scal + SCAL_T, &t, sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  GH_CK(cudaStreamSynchronize(h->stream));
+  return GENASIS_OK;
+}
+
+int genasis_hydro_get_totals(genasis_hydro_t h, double* totals) {
+  if (!h || !totals) return fail(GENASIS_EINVAL, "NULL argument");
+  int rc = reduce_now(h, false);
+  if (rc) return rc;
+  GH_CK(cudaMemcpyAsync(totals, h->scal + SCAL_TOT, h->nv * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  return sync_status(h);
+}
+
+int genasis_hydro_status(genasis_hydro_t h) {
+  if (!h) return fail(GENASIS_EINVAL, "NULL handle");
+  return sync_status(h);
+}
+
+int genasis_hydro_clear_status(genasis_hydro_t h) {
+  if (!h) return fail(GENASIS_EINVAL, "NULL handle");
+  GH_CK(cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream));
+  GH_CK(cudaStreamSynchronize(h->stream));
+  return GENASIS_OK;
+}
+
+int genasis_hydro_set_tile(genasis_hydro_t h, int tile, int kchunk) {
+  if (!h) return fail(GENASIS_EINVAL, "NULL handle");
+  if (kchunk < 0) return fail(GENASIS_EINVAL, "kchunk < 0");
+  GH_CK(cudaStreamSynchronize(h->stream));
+  return configure(h, tile, kchunk);
+}
+
+int genasis_hydro_get_tile(genasis_hydro_t h, int* info) {
+  if (!h || !info) return fail(GENASIS_EINVAL, "NULL argument");
+  info[0] = h->tile;
+  info[1] = h->v1.tx;
+  info[2] = h->v1.ty;
+  info[3] = h->kchunk;
+  info[4] = (int)(h->grid.x * h->grid.y * h->grid.z);
+  info[5] = tile_count(h->ndim);
+  return GENASIS_OK;
+}
+
+int genasis_hydro_launches_per_step(genasis_hydro_t h) {
+  if (!h) return fail(GENASIS_EINVAL, "NULL handle");
+  return 3;
+}
+
+int genasis_hydro_profile_step(genasis_hydro_t h, double cfl, float* ms) {
+  if (!h || !ms) return fail(GENASIS_EINVAL, "NULL argument");
+  if (!(cfl > 0.0)) return fail(GENASIS_EINVAL, "cfl must be > 0");
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  int rc = GENASIS_OK;
+  for (int i = 0; i < 4 && !rc; ++i)
+    if (cudaEventCreate(&ev[i]) != cudaSuccess) rc = fail(GENASIS_ECUDA, "cudaEventCreate failed");
+  if (!rc) rc = enqueue_step(h, FIN_CFL, 0.0, cfl, 0.0, ev);
+  if (!rc && cudaEventSynchronize(ev[3]) != cudaSuccess) rc = fail(GENASIS_ECUDA, "profile sync failed");
+  if (!rc) {
+    cudaEventElapsedTime(&ms[0], ev[0], ev[1]);
+    cudaEventElapsedTime(&ms[1], ev[1], ev[2]);
+    cudaEventElapsedTime(&ms[2], ev[2], ev[3]);
+  }
+  for (int i = 0; i < 4; ++i)
+    if (ev[i]) cudaEventDestroy(ev[i]);
+  if (rc) return rc;
+  return sync_status(h);
+}
+
+int genasis_hydro_autotune(genasis_hydro_t h, int trial_steps, const char* cache_path) {
+  if (!h || trial_steps < 1) return fail(GENASIS_EINVAL, "bad argument");
+  char key[160];
+  snprintf(key, sizeof(key), "ndim=%d n=%d,%d,%d prec=%d solver=%d", h->ndim, h->n[0], h->n[1], h->n[2], h->prec,
+           h->solver);
+  if (cache_path) {
+    FILE* f = fopen(cache_path, "r");
+    if (f) {
+      char line[256];
+      int tile = -1, kc = -1;
+      while (fgets(line, sizeof(line), f)) {
+        const size_t kl = strlen(key);
+        if (strncmp(line, key, kl) == 0 && line[kl] == ' ') {
+          int t2, k2;
+          if (sscanf(line + kl, " tile=%d kchunk=%d", &t2, &k2) == 2) {
+            tile = t2;
+            kc = k2;
+          }
+        }
+      }
+      fclose(f);
+      if (tile >= 0 && tile < tile_count(h->ndim)) return configure(h, tile, kc);
+    }
+  }
+  // save state, time, status
+  const size_t bytes = h->ncell * h->nv * h->esize;
+  void* save = nullptr;
+  double scal_save[SCAL_COUNT];
+  GH_CK(cudaMalloc(&save, bytes));
+  GH_CK(cudaMemcpyAsync(save, h->U[h->cur], bytes, cudaMemcpyDeviceToDevice, h->stream));
+  GH_CK(cudaMemcpyAsync(scal_save, h->scal, sizeof(scal_save), cudaMemcpyDeviceToHost, h->stream));
+  const int cur_save = h->cur;
+  cudaEvent_t e0, e1;
+  GH_CK(cudaEventCreate(&e0));
+  GH_CK(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int best_tile = 0, best_kc = 0;
+  int rc = GENASIS_OK;
+  const int nm = h->ndim >= 2 ? h->n[h->ndim - 1] : 1;
+  for (int tile = 0; tile < tile_count(h->ndim) && !rc; ++tile) {
+    std::vector<int> kcs = {0};
+    if (h->ndim >= 2)
+      for (int kc : {16, 32, 64})
+        if (kc < nm) kcs.push_back(kc);
+    for (int kc : kcs) {
+      rc = configure(h, tile, kc);
+      if (rc) break;
+      rc = enqueue_step(h, FIN_CFL, 0.0, 0.1, 0.0);  // warm-up
+      if (rc) break;
+      cudaEventRecord(e0, h->stream);
+      for (int s = 0; s < trial_steps && !rc; ++s) rc = enqueue_step(h, FIN_CFL, 0.0, 0.1, 0.0);
+      cudaEventRecord(e1, h->stream);
+      if (cudaEventSynchronize(e1) != cudaSuccess) rc = fail(GENASIS_ECUDA, "autotune timing failed");
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (!rc && ms < best) {
+        best = ms;
+        best_tile = tile;
+        best_kc = kc;
+      }
+      // restore the state after every trial
+      h->cur = cur_save;
+      cudaMemcpyAsync(h->U[h->cur], save, bytes, cudaMemcpyDeviceToDevice, h->stream);
+    }
+  }
+  cudaMemcpyAsync(h->scal, scal_save, sizeof(scal_save), cudaMemcpyHostToDevice, h->stream);
+  cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream);
+  cudaStreamSynchronize(h->stream);
+  cudaFree(save);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  rc = configure(h, best_tile, best_kc);
+  if (rc) return rc;
+  if (cache_path) {
+    FILE* f = fopen(cache_path, "a");
+    if (f) {
+      fprintf(f, "%s tile=%d kchunk=%d ms_per_step=%.6f\n", key, best_tile, best_kc, best / trial_steps);
+      fclose(f);
+    }
+  }
+  return GENASIS_OK;
+}
+
+}  // extern "C"

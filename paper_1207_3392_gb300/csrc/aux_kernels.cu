@@ -1,0 +1,203 @@
+// aux_kernels.cu -- small kernels around the stage kernels: initial state
+// from primitives, precision conversion, the standalone CFL and totals
+// reductions, and the single-CTA finalisation of dt and totals.
+#include "aux_kernels.h"
+#include "hydro_device.cuh"
+
+namespace gh {
+
+// U = (D, S, G) from (rho, v, p): D = rho, S = rho v, G = p/(gamma-1) + rho |v|^2 / 2
+// (Sec. 3.5, m = 1), evaluated in FP64 and rounded once to the storage type.
+template <class T>
+__global__ void init_from_primitive_kernel(int ndim, size_t ncell, double gamma, const double* __restrict__ rho,
+                                           const double* __restrict__ vel, const double* __restrict__ p,
+                                           T* __restrict__ U) {
+  const int nv = ndim + 2;
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < ncell; c += (size_t)gridDim.x * blockDim.x) {
+    const double n = rho[c];
+    double v2 = 0.0;
+    for (int q = 0; q < ndim; ++q) {
+      const double v = vel[q * ncell + c];
+      v2 += v * v;
+      U[(1 + q) * ncell + c] = (T)(n * v);
+    }
+    U[c] = (T)n;
+    U[(nv - 1) * ncell + c] = (T)(p[c] / (gamma - 1.0) + 0.5 * n * v2);
+  }
+}
+
+template <class Tin, class Tout>
+__global__ void convert_kernel(size_t count, const Tin* __restrict__ in, Tout* __restrict__ out) {
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < count; c += (size_t)gridDim.x * blockDim.x)
+    out[c] = (Tout)in[c];
+}
+
+// Per-block max over cells of max_q (|v_q| + c_s) / dq, i.e. the inverse of the
+// cell's CFL time (Eq. courantTimeStep).
+template <class T, int NDIM>
+__global__ void speed_kernel(ReduceArgs<T> A) {
+  constexpr int NV = NDIM + 2;
+  __shared__ double red[32];
+  double best = 0.0;
+  bool bad = false;
+  const T gm1 = (T)(A.gamma - 1.0), gamma = (T)A.gamma;
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < A.ncell; c += (size_t)gridDim.x * blockDim.x) {
+    T u[NV], w[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) u[v] = A.U[v * A.ncell + c];
+    recover<NDIM>(u, w);
+    const T p = gm1 * w[NV - 1];
+    bad |= !(w[0] > T(0)) || !(p > T(0));
+    const T cs = sqrt(gamma * p / w[0]);
+    size_t r = c;
+    T s = T(0);
+#pragma unroll
+    for (int q = 0; q < NDIM; ++q) {
+      const size_t i = r % A.n[q];
+      r /= A.n[q];
+      s = fmax(s, (fabs(w[1 + q]) + cs) * A.iw[q][i + 2]);
+    }
+    best = fmax(best, (double)s);
+  }
+  if (bad) atomicOr(A.status, STATUS_NONPHYS);
+  best = warp_max(best);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = best;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double acc = red[0];
+    for (int i = 1; i < (int)(blockDim.x >> 5); ++i) acc = fmax(acc, red[i]);
+    A.part_speed[blockIdx.x] = acc;
+  }
+}
+
+// Per-block sums of U dV (FP64, fixed order).
+template <class T, int NDIM>
+__global__ void totals_kernel(ReduceArgs<T> A) {
+  constexpr int NV = NDIM + 2;
+  __shared__ double red[32][NV];
+  double acc[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) acc[v] = 0.0;
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < A.ncell; c += (size_t)gridDim.x * blockDim.x) {
+    size_t r = c;
+    double dV = 1.0;
+#pragma unroll
+    for (int q = 0; q < NDIM; ++q) {
+      const size_t i = r % A.n[q];
+      r /= A.n[q];
+      dV *= A.wd[q][i];
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v] = fma((double)A.U[v * A.ncell + c], dV, acc[v]);
+  }
+#pragma unroll
+  for (int v = 0; v < NV; ++v) acc[v] = warp_sum(acc[v]);
+  if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) red[threadIdx.x >> 5][v] = acc[v];
+  }
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    double s = red[0][threadIdx.x];
+    for (int i = 1; i < (int)(blockDim.x >> 5); ++i) s += red[i][threadIdx.x];
+    A.part_tot[blockIdx.x * NV + threadIdx.x] = s;
+  }
+}
+
+// One CTA: fold the per-CTA partials in a fixed order, then set dt and t.
+//   mode FIN_FIXED : dt = fixed_dt
+//   mode FIN_CFL   : dt = cfl / max speed            (Eq. courantTimeStep x C_CFL)
+//   mode FIN_REDUCE: only store dt_CFL and totals
+// With t_end > 0 the step is clamped so that t never passes t_end.
+__global__ void finalize_kernel(FinalizeArgs A) {
+  __shared__ double red[32];
+  double best = 0.0;
+  if (A.part_speed)
+    for (int i = threadIdx.x; i < A.nblk; i += blockDim.x) best = fmax(best, A.part_speed[i]);
+  best = warp_max(best);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = best;
+  __syncthreads();
+  if (A.part_tot && threadIdx.x < A.nv) {
+    double s = 0.0;
+    for (int i = 0; i < A.nblk; ++i) s += A.part_tot[(size_t)i * A.nv + threadIdx.x];
+    A.scal[SCAL_TOT + threadIdx.x] = s;
+  }
+  if (threadIdx.x == 0) {
+    double m = red[0];
+    for (int i = 1; i < (int)(blockDim.x >> 5); ++i) m = fmax(m, red[i]);
+    if (A.part_speed) A.scal[SCAL_DTCFL] = 1.0 / m;
+    if (A.mode != FIN_REDUCE) {
+      double dt = A.mode == FIN_CFL ? A.cfl * (1.0 / m) : A.fixed_dt;
+      const double t = A.scal[SCAL_T];
+      if (A.t_end > 0.0) {
+        if (t + dt > A.t_end) dt = A.t_end - t;
+        if (!(dt > 0.0)) dt = 0.0;
+      }
+      if (!(dt >= 0.0) || !(dt < INFINITY)) {
+        atomicOr(A.status, STATUS_NONPHYS);
+        dt = 0.0;
+      }
+      A.scal[SCAL_DT] = dt;
+      A.scal[SCAL_T] = t + dt;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ launchers
+
+static int grid_for(size_t count, int block, int max_blocks) {
+  size_t g = (count + block - 1) / block;
+  if (g < 1) g = 1;
+  return (int)(g > (size_t)max_blocks ? max_blocks : g);
+}
+
+template <class T>
+cudaError_t launch_init_from_primitive(int ndim, size_t ncell, double gamma, const double* rho, const double* vel,
+                                       const double* p, T* U, cudaStream_t s) {
+  init_from_primitive_kernel<T><<<grid_for(ncell, 256, 4096), 256, 0, s>>>(ndim, ncell, gamma, rho, vel, p, U);
+  return cudaGetLastError();
+}
+
+template <class Tin, class Tout>
+cudaError_t launch_convert(size_t count, const Tin* in, Tout* out, cudaStream_t s) {
+  convert_kernel<Tin, Tout><<<grid_for(count, 256, 4096), 256, 0, s>>>(count, in, out);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_speed(int ndim, const ReduceArgs<T>& A, cudaStream_t s) {
+  switch (ndim) {
+    case 1: speed_kernel<T, 1><<<A.nblk, 256, 0, s>>>(A); break;
+    case 2: speed_kernel<T, 2><<<A.nblk, 256, 0, s>>>(A); break;
+    default: speed_kernel<T, 3><<<A.nblk, 256, 0, s>>>(A); break;
+  }
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_totals(int ndim, const ReduceArgs<T>& A, cudaStream_t s) {
+  switch (ndim) {
+    case 1: totals_kernel<T, 1><<<A.nblk, 256, 0, s>>>(A); break;
+    case 2: totals_kernel<T, 2><<<A.nblk, 256, 0, s>>>(A); break;
+    default: totals_kernel<T, 3><<<A.nblk, 256, 0, s>>>(A); break;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const FinalizeArgs& A, cudaStream_t s) {
+  finalize_kernel<<<1, 256, 0, s>>>(A);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_init_from_primitive<float>(int, size_t, double, const double*, const double*,
+                                                       const double*, float*, cudaStream_t);
+template cudaError_t launch_init_from_primitive<double>(int, size_t, double, const double*, const double*,
+                                                        const double*, double*, cudaStream_t);
+template cudaError_t launch_convert<float, double>(size_t, const float*, double*, cudaStream_t);
+template cudaError_t launch_convert<double, float>(size_t, const double*, float*, cudaStream_t);
+template cudaError_t launch_speed<float>(int, const ReduceArgs<float>&, cudaStream_t);
+template cudaError_t launch_speed<double>(int, const ReduceArgs<double>&, cudaStream_t);
+template cudaError_t launch_totals<float>(int, const ReduceArgs<float>&, cudaStream_t);
+template cudaError_t launch_totals<double>(int, const ReduceArgs<double>&, cudaStream_t);
+
+}  // namespace gh

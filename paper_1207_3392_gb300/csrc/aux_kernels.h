@@ -1,0 +1,49 @@
+// aux_kernels.h -- launchers of the small kernels around the stage kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+namespace gh {
+
+// Slots of the per-handle device scalar block.
+enum { SCAL_DT = 0, SCAL_T = 1, SCAL_DTCFL = 2, SCAL_TOT = 3, SCAL_COUNT = 8 };
+enum { FIN_FIXED = 0, FIN_CFL = 1, FIN_REDUCE = 2 };
+
+template <class T>
+struct ReduceArgs {
+  size_t ncell;
+  int n[3];
+  double gamma;
+  const T* U;
+  const T* iw[3];        // inverse widths, index c + 2
+  const double* wd[3];   // widths, index c
+  double* part_speed;
+  double* part_tot;
+  unsigned* status;
+  int nblk;
+};
+
+struct FinalizeArgs {
+  const double* part_speed;  // may be null
+  const double* part_tot;    // may be null
+  int nblk;
+  int nv;
+  int mode;
+  double cfl, fixed_dt, t_end;
+  double* scal;
+  unsigned* status;
+};
+
+template <class T>
+cudaError_t launch_init_from_primitive(int ndim, size_t ncell, double gamma, const double* rho, const double* vel,
+                                       const double* p, T* U, cudaStream_t s);
+template <class Tin, class Tout>
+cudaError_t launch_convert(size_t count, const Tin* in, Tout* out, cudaStream_t s);
+template <class T>
+cudaError_t launch_speed(int ndim, const ReduceArgs<T>& A, cudaStream_t s);
+template <class T>
+cudaError_t launch_totals(int ndim, const ReduceArgs<T>& A, cudaStream_t s);
+cudaError_t launch_finalize(const FinalizeArgs& A, cudaStream_t s);
+
+}  // namespace gh

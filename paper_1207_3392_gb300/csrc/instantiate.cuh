@@ -1,0 +1,30 @@
+// instantiate.cuh -- helpers that register explicit instantiations of the stage
+// kernel in the variant table (one translation unit per dimensionality and
+// precision so that they compile in parallel).
+#pragma once
+
+#include "registry.h"
+#include "stage_kernel.cuh"
+
+namespace gh {
+
+template <int NDIM, class T, int SOLVER, int STAGE, int TX, int TY>
+inline void fill_variant(StageVariant* out) {
+  using K = StageKernel<NDIM, T, SOLVER, STAGE, TX, TY>;
+  out->fn = reinterpret_cast<const void*>(&hydro_stage_kernel<NDIM, T, SOLVER, STAGE, TX, TY>);
+  out->smem = sizeof(typename K::Smem);
+  out->tx = TX;
+  out->ty = TY;
+}
+
+template <int NDIM, class T, int TX, int TY>
+inline bool pick_variant(int solver, int stage, StageVariant* out) {
+  if (solver == SOLVER_HLL && stage == 1) fill_variant<NDIM, T, SOLVER_HLL, 1, TX, TY>(out);
+  else if (solver == SOLVER_HLL && stage == 2) fill_variant<NDIM, T, SOLVER_HLL, 2, TX, TY>(out);
+  else if (solver == SOLVER_HLLC && stage == 1) fill_variant<NDIM, T, SOLVER_HLLC, 1, TX, TY>(out);
+  else if (solver == SOLVER_HLLC && stage == 2) fill_variant<NDIM, T, SOLVER_HLLC, 2, TX, TY>(out);
+  else return false;
+  return true;
+}
+
+}  // namespace gh

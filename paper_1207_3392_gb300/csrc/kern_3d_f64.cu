@@ -1,0 +1,15 @@
+// kern_3d_f64.cu -- 3D stage kernels, FP64 throughout.
+#include "instantiate.cuh"
+
+namespace gh {
+
+bool stage_variant_3d_f64(int solver, int stage, int tile, StageVariant* out) {
+  switch (tile) {
+    case 0: return pick_variant<3, double, 32, 8>(solver, stage, out);
+    case 1: return pick_variant<3, double, 32, 4>(solver, stage, out);
+    case 2: return pick_variant<3, double, 64, 4>(solver, stage, out);
+  }
+  return false;
+}
+
+}  // namespace gh

@@ -1,0 +1,29 @@
+// registry.h -- host-side table of the compiled stage-kernel variants.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+namespace gh {
+
+// One compiled instantiation of hydro_stage_kernel.
+struct StageVariant {
+  const void* fn;      // kernel entry
+  size_t smem;         // dynamic shared memory per CTA (bytes)
+  int tx, ty;          // tile shape (threads = tx * ty)
+};
+
+// Tile shapes compiled per dimensionality; index `tile` selects one.
+int stage_tile_count(int ndim);
+// Fills *out for (ndim, fp64?, solver, stage, tile); returns false if absent.
+bool stage_variant(int ndim, bool fp64, int solver, int stage, int tile, StageVariant* out);
+
+bool stage_variant_1d(bool fp64, int solver, int stage, int tile, StageVariant* out);
+bool stage_variant_2d(bool fp64, int solver, int stage, int tile, StageVariant* out);
+bool stage_variant_3d_f32(int solver, int stage, int tile, StageVariant* out);
+bool stage_variant_3d_f64(int solver, int stage, int tile, StageVariant* out);
+int tile_count_1d();
+int tile_count_2d();
+int tile_count_3d();
+
+}  // namespace gh

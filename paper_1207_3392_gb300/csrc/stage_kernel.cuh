@@ -1,0 +1,337 @@
+// stage_kernel.cuh -- one Runge-Kutta stage of the single-level update
+// (Algorithm 1 of arXiv:1207.3392 fused into one pass per stage).
+//
+// Time stepping (Sec. 3.4, Eqs. Update, RungeKutta1-3):
+//   stage 1 : K = L[U^n]                      (written to `out`)
+//   stage 2 : U1 = U^n + dt K  (formed on the fly while loading),
+//             U^{n+1} = U^n + dt (K + L[U1]) / 2  (written to `out`)
+// so that the CFL reduction (Eq. courantTimeStep) and the conserved totals can
+// be taken from the primitive recovery stage 1 already does on U^n.
+//
+// Tiling: a CTA owns a TX x TY tile of the "plane" axes and marches along the
+// last axis (z in 3D, y in 2D; 1D has one plane).  Per plane it
+//   1. loads + recovers the plane two ahead for its own columns (register ring
+//      of W along the march axis; limited slopes and the march-axis face flux
+//      are computed once per cell per stage),
+//   2. loads + recovers the cross-shaped in-plane halo (2 cells each side),
+//   3. computes every in-plane face flux exactly once into shared memory,
+//   4. forms the flux divergence (Eq. BalanceEquationAverage, A_q/V = 1/dq)
+//      and the stage combine for its own cells.
+// Boundary conditions are applied by index mapping on load (bc_map).
+#pragma once
+
+#include "hydro_device.cuh"
+
+namespace gh {
+
+template <class T>
+struct StageArgs {
+  int n[3];               // cells per axis; 1 on inactive axes
+  int bc_lo[3], bc_hi[3];
+  T gamma, gm1, theta;
+  const Geo<T>* geo[3];   // per axis, index c + 2 for c in [-2, n + 2)
+  const T* iw[3];         // inverse widths, index c + 2
+  const double* wd[3];    // widths in FP64, index c (totals)
+  const T* __restrict__ un;   // U^n      [NV][n2][n1][n0]
+  const T* __restrict__ k1;   // K of stage 1 (stage 2 only)
+  T* __restrict__ out;        // stage 1: K; stage 2: U^{n+1}
+  const double* dt;           // device scalar (stage 2)
+  int kchunk;                 // planes per CTA along the march axis
+  double* part_speed;         // stage 1: per-CTA max over cells of max_q (|v_q| + c_s) / dq
+  double* part_tot;           // stage 1: per-CTA sums of U dV, [nblocks][NV]
+  unsigned* status;
+  int want_totals;
+};
+
+template <int NDIM, class T, int SOLVER, int STAGE, int TX, int TY>
+struct StageKernel {
+  static constexpr int NV = NDIM + 2;
+  static constexpr bool MARCH = NDIM >= 2;
+  static constexpr bool HAS_Y = NDIM == 3;
+  static constexpr int AM = NDIM - 1;  // march axis (2D: y, 3D: z)
+  static constexpr int NT = TX * TY;
+  static constexpr int SX = TX + 4;
+  static constexpr int SY = HAS_Y ? TY + 4 : 1;
+  static constexpr int NHALO = HAS_Y ? 4 * TX + 4 * TY : 4;
+  static_assert(HAS_Y || TY == 1, "tiles of 1D/2D runs are one row high");
+  static_assert(NT % 32 == 0, "whole warps");
+
+  struct Smem {
+    T w[NV][SY][SX];
+    T fx[NV][TY][TX + 1];
+    T fy[HAS_Y ? NV : 1][HAS_Y ? TY + 1 : 1][TX];
+    double red[NT / 32][NV + 1];
+  };
+
+  // Linear index of cell (a, b, m): a = x, b = in-plane y (3D), m = march
+  // coordinate; all three already inside the domain.
+  static __device__ __forceinline__ size_t cell(const StageArgs<T>& A, int a, int b, int m) {
+    if (NDIM == 3) return ((size_t)m * A.n[1] + b) * A.n[0] + a;
+    if (NDIM == 2) return (size_t)m * A.n[0] + a;
+    return (size_t)a;
+  }
+
+  // Load the conserved state of (possibly ghost) cell (a, b, m) -- for stage 2
+  // the provisional U1 = U^n + dt K -- and recover primitives.
+  static __device__ __forceinline__ void load_prim(const StageArgs<T>& A, int a, int b, int m, T dt,
+                                                   size_t vs, T (&w)[NV]) {
+    bool fa, fb = false, fm = false;
+    const int sa = bc_map(a, A.n[0], A.bc_lo[0], A.bc_hi[0], fa);
+    int sb = 0, sm = 0;
+    if constexpr (HAS_Y) sb = bc_map(b, A.n[1], A.bc_lo[1], A.bc_hi[1], fb);
+    if constexpr (MARCH) sm = bc_map(m, A.n[AM], A.bc_lo[AM], A.bc_hi[AM], fm);
+    const size_t c = cell(A, sa, sb, sm);
+    T u[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      T x = __ldg(A.un + v * vs + c);
+      if (STAGE == 2) x = fma(dt, __ldg(A.k1 + v * vs + c), x);
+      u[v] = x;
+    }
+    if (fa) u[1] = -u[1];
+    if constexpr (HAS_Y) { if (fb) u[2] = -u[2]; }
+    if constexpr (MARCH) { if (fm) u[1 + AM] = -u[1 + AM]; }
+    recover<NDIM>(u, w);
+  }
+
+  static __device__ __forceinline__ Geo<T> geo(const StageArgs<T>& A, int q, int c) {
+    c = c < -2 ? -2 : (c > A.n[q] + 1 ? A.n[q] + 1 : c);
+    return A.geo[q][c + 2];
+  }
+
+  // Flux through the face between slot positions (s - 1, s) along x of shared
+  // row `row`; slot s holds cell a0 + s - 2.
+  static __device__ __forceinline__ void x_face(const StageArgs<T>& A, Smem& S, int a0, int face, int srow,
+                                                int frow) {
+    const int sl = face + 1;  // slot of the left cell
+    const Geo<T> gl = geo(A, 0, a0 + face - 1), gr = geo(A, 0, a0 + face);
+    T wl[NV], wr[NV], f[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const T w0 = S.w[v][srow][sl - 1], w1 = S.w[v][srow][sl], w2 = S.w[v][srow][sl + 1],
+              w3 = S.w[v][srow][sl + 2];
+      wl[v] = w1 + limited_slope(w0, w1, w2, gl, A.theta) * gl.h;
+      wr[v] = w2 - limited_slope(w1, w2, w3, gr, A.theta) * gr.h;
+    }
+    face_flux<T, NDIM, 0, SOLVER>(wl, wr, A.gamma, A.gm1, f);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) S.fx[v][frow][face] = f[v];
+  }
+
+  static __device__ __forceinline__ void y_face(const StageArgs<T>& A, Smem& S, int b0, int face, int scol) {
+    const int sl = face + 1;
+    const Geo<T> gl = geo(A, 1, b0 + face - 1), gr = geo(A, 1, b0 + face);
+    T wl[NV], wr[NV], f[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const T w0 = S.w[v][sl - 1][scol], w1 = S.w[v][sl][scol], w2 = S.w[v][sl + 1][scol],
+              w3 = S.w[v][sl + 2][scol];
+      wl[v] = w1 + limited_slope(w0, w1, w2, gl, A.theta) * gl.h;
+      wr[v] = w2 - limited_slope(w1, w2, w3, gr, A.theta) * gr.h;
+    }
+    face_flux<T, NDIM, 1, SOLVER>(wl, wr, A.gamma, A.gm1, f);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) S.fy[v][face][scol - 2] = f[v];
+  }
+
+  // Flux through the march-axis face between cells with primitives wa (below,
+  // slope sa, geometry ga) and wb (above, slope sb, geometry gb).
+  static __device__ __forceinline__ void m_face(const StageArgs<T>& A, const T (&wa)[NV], const T (&sa)[NV],
+                                                T ha, const T (&wb)[NV], const T (&sb)[NV], T hb,
+                                                T (&f)[NV]) {
+    T wl[NV], wr[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      wl[v] = wa[v] + sa[v] * ha;
+      wr[v] = wb[v] - sb[v] * hb;
+    }
+    face_flux<T, NDIM, AM, SOLVER>(wl, wr, A.gamma, A.gm1, f);
+  }
+
+  static __device__ __forceinline__ void slopes(const StageArgs<T>& A, const T (&wm)[NV], const T (&wc)[NV],
+                                                const T (&wp)[NV], const Geo<T>& g, T (&s)[NV]) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) s[v] = limited_slope(wm[v], wc[v], wp[v], g, A.theta);
+  }
+
+  static __device__ __forceinline__ bool nonphysical(const T (&w)[NV], T gm1) {
+    bool bad = !(w[0] > T(0)) || !(gm1 * w[NV - 1] > T(0));
+#pragma unroll
+    for (int v = 1; v < NV - 1; ++v) bad |= !(fabs(w[v]) < T(INFINITY));
+    return bad;
+  }
+
+  static __device__ void run(const StageArgs<T>& A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem& S = *reinterpret_cast<Smem*>(smem_raw);
+    const int tid = threadIdx.x;
+    const int tx = tid % TX, ty = tid / TX;
+    const int nx = A.n[0];
+    const int ny = HAS_Y ? A.n[1] : 1;
+    const int nm = MARCH ? A.n[AM] : 1;
+    const size_t vs = (size_t)A.n[0] * A.n[1] * A.n[2];
+    const int a0 = blockIdx.x * TX;
+    const int b0 = HAS_Y ? blockIdx.y * TY : 0;
+    const int ca = a0 + tx, cb = b0 + ty;
+    const bool own_valid = ca < nx && cb < ny;
+    const int m0 = MARCH ? blockIdx.z * A.kchunk : 0;
+    const int m1 = MARCH ? min(nm, m0 + A.kchunk) : 1;
+    const T dt = STAGE == 2 ? (T)(*A.dt) : T(0);
+
+    const T iwx = A.iw[0][min(ca, nx + 1) + 2];
+    const T iwy = HAS_Y ? A.iw[1][min(cb, ny + 1) + 2] : T(0);
+
+    // per-thread reductions (stage 1)
+    double speed_max = 0.0;
+    double tot[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) tot[v] = 0.0;
+    bool bad = false;
+
+    // march-axis register ring: W at planes m and m+1, slope at m, flux at m-1/2
+    T wk[NV], wk1[NV], sk[NV], flo[NV];
+    if constexpr (MARCH) {
+      T wa[NV], wb[NV], sa[NV];
+      load_prim(A, ca, cb, m0 - 2, dt, vs, wa);
+      load_prim(A, ca, cb, m0 - 1, dt, vs, wb);
+      load_prim(A, ca, cb, m0, dt, vs, wk);
+      load_prim(A, ca, cb, m0 + 1, dt, vs, wk1);
+      const Geo<T> ga = geo(A, AM, m0 - 1), g0 = geo(A, AM, m0);
+      slopes(A, wa, wb, wk, ga, sa);
+      slopes(A, wb, wk, wk1, g0, sk);
+      m_face(A, wb, sa, ga.h, wk, sk, g0.h, flo);
+    }
+
+    for (int m = m0; m < m1; ++m) {
+      T fhi[NV], wk2[NV], sk1[NV];
+      T wown[NV];
+      if constexpr (MARCH) {
+        load_prim(A, ca, cb, m + 2, dt, vs, wk2);
+        const Geo<T> g0 = geo(A, AM, m), g1 = geo(A, AM, m + 1);
+        slopes(A, wk, wk1, wk2, g1, sk1);
+        m_face(A, wk, sk, g0.h, wk1, sk1, g1.h, fhi);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) wown[v] = wk[v];
+      } else {
+        load_prim(A, ca, 0, 0, dt, vs, wown);
+      }
+      // own cell into the shared plane
+#pragma unroll
+      for (int v = 0; v < NV; ++v) S.w[v][HAS_Y ? ty + 2 : 0][tx + 2] = wown[v];
+      // cross-shaped in-plane halo
+      for (int h = tid; h < NHALO; h += NT) {
+        int sx, sy;
+        if (HAS_Y && h < 4 * TX) {
+          const int r = h / TX;
+          sx = h % TX + 2;
+          sy = r < 2 ? r : TY + r;
+        } else {
+          const int hh = HAS_Y ? h - 4 * TX : h;
+          const int c = hh & 3;
+          sy = HAS_Y ? (hh >> 2) + 2 : 0;
+          sx = c < 2 ? c : TX + c;
+        }
+        T wh[NV];
+        load_prim(A, a0 + sx - 2, HAS_Y ? b0 + sy - 2 : 0, m, dt, vs, wh);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) S.w[v][sy][sx] = wh[v];
+      }
+      __syncthreads();
+
+      // in-plane faces, each computed once
+      const int srow = HAS_Y ? ty + 2 : 0;
+      x_face(A, S, a0, tx, srow, ty);
+      if constexpr (HAS_Y) y_face(A, S, b0, ty, tx + 2);
+      {
+        const int extra = tid - (NT - (HAS_Y ? TY + TX : 32));
+        // last x face of each row (TY items) and last y face of each column (TX items)
+        if constexpr (HAS_Y) {
+          if (extra >= 0 && extra < TY) x_face(A, S, a0, TX, extra + 2, extra);
+          else if (extra >= TY && extra < TY + TX) y_face(A, S, b0, TY, extra - TY + 2);
+        } else {
+          if (extra == 0) x_face(A, S, a0, TX, 0, 0);
+        }
+      }
+      __syncthreads();
+
+      if (own_valid) {
+        const T iwm = MARCH ? A.iw[AM][m + 2] : T(0);
+        T L[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          T d = (S.fx[v][ty][tx + 1] - S.fx[v][ty][tx]) * iwx;
+          if constexpr (HAS_Y) d += (S.fy[v][ty + 1][tx] - S.fy[v][ty][tx]) * iwy;
+          if constexpr (MARCH) d += (fhi[v] - flo[v]) * iwm;
+          L[v] = -d;
+        }
+        const size_t c = cell(A, ca, cb, m);
+        bad |= nonphysical(wown, A.gm1);
+        if (STAGE == 1) {
+#pragma unroll
+          for (int v = 0; v < NV; ++v) A.out[v * vs + c] = L[v];
+          // CFL speed (Eq. courantTimeStep) on U^n at the cell centre
+          const T cs = sqrt(A.gamma * (A.gm1 * wown[NV - 1]) / wown[0]);
+          T s = (fabs(wown[1]) + cs) * iwx;
+          if constexpr (HAS_Y) s = fmax(s, (fabs(wown[2]) + cs) * iwy);
+          if constexpr (MARCH) s = fmax(s, (fabs(wown[1 + AM]) + cs) * iwm);
+          speed_max = fmax(speed_max, (double)s);
+          if (A.want_totals) {
+            const double dm = MARCH ? A.wd[AM][m] : 1.0;
+#pragma unroll
+            for (int v = 0; v < NV; ++v) tot[v] = fma((double)__ldg(A.un + v * vs + c), dm, tot[v]);
+          }
+        } else {
+          const T hdt = T(0.5) * dt;
+#pragma unroll
+          for (int v = 0; v < NV; ++v) {
+            const T u0 = __ldg(A.un + v * vs + c), k = __ldg(A.k1 + v * vs + c);
+            A.out[v * vs + c] = fma(hdt, k + L[v], u0);
+          }
+        }
+      }
+      if constexpr (MARCH) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          flo[v] = fhi[v];
+          wk[v] = wk1[v];
+          wk1[v] = wk2[v];
+          sk[v] = sk1[v];
+        }
+      }
+    }
+
+    if (bad) atomicOr(A.status, STATUS_NONPHYS);
+    if (STAGE == 1) {
+      // per-CTA partials, fixed-order reduction
+      const int warp = tid >> 5, lane = tid & 31;
+      double area = 0.0;
+      if (own_valid && A.want_totals) {
+        area = A.wd[0][ca];
+        if constexpr (HAS_Y) area *= A.wd[1][cb];
+      }
+      double r[NV + 1];
+      r[0] = warp_max(speed_max);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) r[1 + v] = warp_sum(tot[v] * area);
+      if (lane == 0) {
+#pragma unroll
+        for (int v = 0; v <= NV; ++v) S.red[warp][v] = r[v];
+      }
+      __syncthreads();
+      if (tid <= NV) {
+        double acc = S.red[0][tid];
+        for (int wi = 1; wi < NT / 32; ++wi) acc = tid == 0 ? fmax(acc, S.red[wi][0]) : acc + S.red[wi][tid];
+        const size_t blk = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+        if (tid == 0) A.part_speed[blk] = acc;
+        else A.part_tot[blk * NV + (tid - 1)] = acc;
+      }
+    }
+  }
+};
+
+template <int NDIM, class T, int SOLVER, int STAGE, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY) hydro_stage_kernel(const StageArgs<T> A) {
+  StageKernel<NDIM, T, SOLVER, STAGE, TX, TY>::run(A);
+}
+
+}  // namespace gh

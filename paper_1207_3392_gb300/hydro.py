@@ -1,0 +1,259 @@
+"""Thin Python binding of the C ABI in include/genasis_hydro.h.
+
+Argument marshalling only: every step of the update runs in the CUDA library
+``_lib/libgenasis_hydro.so``.  There is no fallback: if the library is missing
+or fails to load, every call raises.  Arrays may be numpy arrays (host) or
+torch tensors (host or CUDA); they must be C-contiguous and of the documented
+dtype.  PyTorch is used only for device memory and streams.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import problems as _problems
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libgenasis_hydro.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ENONPHYS, ETIMEOUT = 0, -1, -2, -3, -4, -5
+HLL, HLLC = 0, 1
+BC_PERIODIC, BC_REFLECT, BC_OUTFLOW = 0, 1, 2
+FP64, FP32_MIXED = 0, 1
+
+
+class HydroError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"genasis_hydro error {code}: {msg}")
+        self.code = code
+
+
+class NonPhysicalState(HydroError):
+    pass
+
+
+class Desc(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int), ("n", ctypes.c_int * 3), ("widths", ctypes.c_void_p * 3),
+                ("bc_lo", ctypes.c_int * 3), ("bc_hi", ctypes.c_int * 3), ("gamma", ctypes.c_double),
+                ("solver", ctypes.c_int), ("theta", ctypes.c_double), ("precision", ctypes.c_int),
+                ("stream", ctypes.c_void_p)]
+
+
+_lib = None
+
+# (name, argtypes); every function returns int except last_error.
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+SIGNATURES = {
+    "genasis_hydro_create": [ctypes.POINTER(Desc), ctypes.POINTER(_P)],
+    "genasis_hydro_destroy": [_P],
+    "genasis_hydro_set_primitive": [_P, _P, _P, _P],
+    "genasis_hydro_set_conserved": [_P, _P, _I],
+    "genasis_hydro_get_conserved": [_P, _P, _I],
+    "genasis_hydro_compute_dt": [_P, _D, _P],
+    "genasis_hydro_step": [_P, _D],
+    "genasis_hydro_advance": [_P, _I, _D, _D, _P],
+    "genasis_hydro_get_time": [_P, _P],
+    "genasis_hydro_set_time": [_P, _D],
+    "genasis_hydro_get_totals": [_P, _P],
+    "genasis_hydro_status": [_P],
+    "genasis_hydro_clear_status": [_P],
+    "genasis_hydro_set_tile": [_P, _I, _I],
+    "genasis_hydro_get_tile": [_P, _P],
+    "genasis_hydro_autotune": [_P, _I, ctypes.c_char_p],
+    "genasis_hydro_launches_per_step": [_P],
+    "genasis_hydro_profile_step": [_P, _D, _P],
+}
+
+
+def load(path: str = LIB_PATH):
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise HydroError(ECUDA, f"CUDA library not built: {path} is missing "
+                                    "(run `python -m paper_1207_3392_gb300.build`)")
+        lib = ctypes.CDLL(path)
+        for name, args in SIGNATURES.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = ctypes.c_int
+        lib.genasis_hydro_last_error.argtypes = []
+        lib.genasis_hydro_last_error.restype = ctypes.c_char_p
+        _lib = lib
+    return _lib
+
+
+def check(rc):
+    if rc == OK or (isinstance(rc, int) and rc > 0):
+        return rc
+    msg = load().genasis_hydro_last_error().decode()
+    if rc == ENONPHYS:
+        raise NonPhysicalState(rc, msg)
+    raise HydroError(rc, msg)
+
+
+def _ptr(a, dtype, count=None, name="array"):
+    """Raw address of a contiguous numpy array or torch tensor (host or CUDA)."""
+    if hasattr(a, "data_ptr"):  # torch tensor
+        import torch
+        want = {np.float64: torch.float64, np.float32: torch.float32}[dtype]
+        if a.dtype != want or not a.is_contiguous():
+            raise ValueError(f"{name}: need a contiguous {want} tensor")
+        if count is not None and a.numel() != count:
+            raise ValueError(f"{name}: expected {count} elements, got {a.numel()}")
+        return a.data_ptr(), a
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    if count is not None and arr.size != count:
+        raise ValueError(f"{name}: expected {count} elements, got {arr.size}")
+    return arr.ctypes.data, arr
+
+
+class Hydro:
+    """One mesh + state on the GPU (a genasis_hydro_t handle)."""
+
+    def __init__(self, ndim, n, widths, bc_lo, bc_hi, gamma=1.4, solver=HLLC, theta=1.4,
+                 precision=FP64, stream=None):
+        lib = load()
+        self.ndim = int(ndim)
+        self.n = tuple(int(x) for x in (list(n) + [1, 1, 1])[:3])
+        self.precision = int(precision)
+        self.dtype = np.float64 if self.precision == FP64 else np.float32
+        self._widths = [np.ascontiguousarray(widths[q], dtype=np.float64) for q in range(self.ndim)]
+        d = Desc()
+        d.ndim = self.ndim
+        for q in range(3):
+            d.n[q] = self.n[q] if q < self.ndim else 1
+            d.widths[q] = self._widths[q].ctypes.data if q < self.ndim else None
+            d.bc_lo[q] = int(bc_lo[q]) if q < self.ndim else 0
+            d.bc_hi[q] = int(bc_hi[q]) if q < self.ndim else 0
+        d.gamma, d.solver, d.theta, d.precision = float(gamma), int(solver), float(theta), self.precision
+        if stream is not None:
+            d.stream = stream if isinstance(stream, int) else int(getattr(stream, "cuda_stream", stream))
+        self._h = ctypes.c_void_p()
+        check(lib.genasis_hydro_create(ctypes.byref(d), ctypes.byref(self._h)))
+        self.ncell = int(np.prod(self.n[: self.ndim]))
+        self.nvar = self.ndim + 2
+        self.shape = tuple(reversed(self.n[: self.ndim]))
+
+    @classmethod
+    def from_problem(cls, prob, precision=FP64, solver=None, stream=None, set_state=True):
+        h = cls(prob.ndim, prob.n, prob.widths, prob.bc_lo, prob.bc_hi, prob.gamma,
+                prob.solver if solver is None else solver, prob.theta, precision, stream)
+        if set_state:
+            h.set_primitive(prob.rho, prob.vel, prob.p)
+        return h
+
+    # -- state ---------------------------------------------------------------
+    def set_primitive(self, rho, vel, p):
+        pr, a = _ptr(rho, np.float64, self.ncell, "rho")
+        pv, b = _ptr(vel, np.float64, self.ncell * self.ndim, "vel")
+        pp, c = _ptr(p, np.float64, self.ncell, "p")
+        check(load().genasis_hydro_set_primitive(self._h, pr, pv, pp))
+
+    def set_conserved(self, U, precision=None):
+        precision = self.precision if precision is None else precision
+        dt = np.float64 if precision == FP64 else np.float32
+        pu, keep = _ptr(U, dt, self.ncell * self.nvar, "U")
+        check(load().genasis_hydro_set_conserved(self._h, pu, precision))
+
+    def get_conserved(self, out=None, precision=None):
+        """Return the conserved state, shape (nvar,) + shape; into `out` (numpy
+        or torch, host or CUDA) if given."""
+        precision = self.precision if precision is None else precision
+        dt = np.float64 if precision == FP64 else np.float32
+        if out is None:
+            out = np.empty((self.nvar,) + self.shape, dtype=dt)
+        po, _ = _ptr(out, dt, self.ncell * self.nvar, "out")
+        check(load().genasis_hydro_get_conserved(self._h, po, precision))
+        return out
+
+    # -- stepping -------------------------------------------------------------
+    def compute_dt(self, cfl):
+        out = ctypes.c_double()
+        check(load().genasis_hydro_compute_dt(self._h, float(cfl), ctypes.byref(out)))
+        return out.value
+
+    def step(self, dt):
+        check(load().genasis_hydro_step(self._h, float(dt)))
+
+    def advance(self, nsteps, cfl, t_end=0.0, sync=True):
+        t = ctypes.c_double()
+        check(load().genasis_hydro_advance(self._h, int(nsteps), float(cfl), float(t_end),
+                                           ctypes.byref(t) if sync else None))
+        return t.value if sync else None
+
+    def evolve(self, cfl, t_end, chunk=64, max_steps=1 << 30):
+        """Advance until t_end in graph launches of `chunk` steps."""
+        t = self.time
+        steps = 0
+        while t < t_end and steps < max_steps:
+            t = self.advance(chunk, cfl, t_end)
+            steps += chunk
+        return t
+
+    @property
+    def time(self):
+        t = ctypes.c_double()
+        check(load().genasis_hydro_get_time(self._h, ctypes.byref(t)))
+        return t.value
+
+    @time.setter
+    def time(self, value):
+        check(load().genasis_hydro_set_time(self._h, float(value)))
+
+    def totals(self):
+        out = np.zeros(5)
+        check(load().genasis_hydro_get_totals(self._h, out.ctypes.data))
+        return out[: self.nvar]
+
+    def status(self):
+        return check(load().genasis_hydro_status(self._h))
+
+    def clear_status(self):
+        check(load().genasis_hydro_clear_status(self._h))
+
+    # -- launch configuration -------------------------------------------------
+    def set_tile(self, tile, kchunk=0):
+        check(load().genasis_hydro_set_tile(self._h, int(tile), int(kchunk)))
+
+    def tile_info(self):
+        info = (ctypes.c_int * 6)()
+        check(load().genasis_hydro_get_tile(self._h, info))
+        keys = ("tile", "tx", "ty", "kchunk", "ctas", "tile_count")
+        return dict(zip(keys, list(info)))
+
+    def autotune(self, trial_steps=3, cache_path=None):
+        check(load().genasis_hydro_autotune(self._h, int(trial_steps),
+                                            cache_path.encode() if cache_path else None))
+        return self.tile_info()
+
+    def profile_step(self, cfl):
+        """One CFL step with per-kernel CUDA-event timing: (stage1, finalize,
+        stage2) in milliseconds."""
+        ms = (ctypes.c_float * 3)()
+        check(load().genasis_hydro_profile_step(self._h, float(cfl), ms))
+        return tuple(ms)
+
+    def launches_per_step(self):
+        return check(load().genasis_hydro_launches_per_step(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load().genasis_hydro_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,225 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle, element
+by element on the same seeded inputs: FP64 within 1e-10 relative L1 per
+conserved variable, FP32-mixed within 1e-5 (L-infinity reported in the failure
+message).  Sizes span several tiles and ragged tails; every boundary rule,
+both solvers, non-uniform widths, and the full-size workloads (one step)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1207_3392_gb300 import hydro as H
+from paper_1207_3392_gb300 import problems as P
+from parity_util import TOL_FP32, TOL_FP64, gpu_run, linf_rel, oracle_run, rel_l1
+
+pytestmark = pytest.mark.gpu
+
+PRECISIONS = ((H.FP64, TOL_FP64), (H.FP32_MIXED, TOL_FP32))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1207_3392_gb300 import build
+    build.build()
+    yield
+
+
+def _check(gpu, ref, ndim, tol, what):
+    e = rel_l1(gpu, ref, ndim)
+    assert np.all(e <= tol), f"{what}: rel L1 {e}, Linf {linf_rel(gpu, ref):.3e}"
+
+
+@pytest.mark.parametrize("solver", [H.HLL, H.HLLC])
+def test_sod_1d_full_run(solver):
+    """The 1D benchmark case in full: Sod, 256 cells, C_CFL 0.8, to t = 0.2."""
+    pr = P.sod(256, solver=solver)
+    Uo, to = oracle_run(pr, t_end=pr.t_end)
+    for precision, tol in PRECISIONS:
+        Ug, tg = gpu_run(pr, precision, t_end=pr.t_end)
+        assert tg == pytest.approx(to, rel=1e-12)
+        _check(Ug, Uo, 1, tol, f"sod prec={precision}")
+
+
+@pytest.mark.parametrize("solver", [H.HLL, H.HLLC])
+@pytest.mark.parametrize("bc", [P.PERIODIC, P.REFLECT, P.OUTFLOW])
+def test_random_blocks_2d(solver, bc):
+    """Discontinuous 2D state, non-uniform widths, ragged tile tails (197 x 75)."""
+    pr = P.random_blocks(2, (197, 75), seed=20 + bc, bc=bc)
+    Uo, _ = oracle_run(pr, solver=solver, steps=12)
+    for precision, tol in PRECISIONS:
+        Ug, _ = gpu_run(pr, precision, solver=solver, steps=12)
+        _check(Ug, Uo, 2, tol, f"2d bc={bc} prec={precision}")
+
+
+@pytest.mark.parametrize("solver", [H.HLL, H.HLLC])
+@pytest.mark.parametrize("bc", [P.PERIODIC, P.REFLECT, P.OUTFLOW])
+def test_random_blocks_3d(solver, bc):
+    """Discontinuous 3D state, non-uniform widths, ragged tiles (45 x 21 x 38)."""
+    pr = P.random_blocks(3, (45, 21, 38), seed=40 + bc, bc=bc)
+    Uo, _ = oracle_run(pr, solver=solver, steps=6)
+    for precision, tol in PRECISIONS:
+        Ug, _ = gpu_run(pr, precision, solver=solver, steps=6)
+        _check(Ug, Uo, 3, tol, f"3d bc={bc} prec={precision}")
+
+
+def test_mixed_boundaries_3d():
+    """Different rules on each face of the box."""
+    pr = P.random_blocks(3, (36, 40, 20), seed=77, bc=P.REFLECT)
+    pr = pr.with_(bc_lo=(P.REFLECT, P.OUTFLOW, P.PERIODIC), bc_hi=(P.OUTFLOW, P.REFLECT, P.PERIODIC))
+    Ug, _ = gpu_run(pr, H.FP64, steps=8)
+    Uo, _ = oracle_run(pr, steps=8)
+    _check(Ug, Uo, 3, TOL_FP64, "mixed bc")
+
+
+@pytest.mark.parametrize("solver", [H.HLL, H.HLLC])
+def test_sedov_3d_reduced(solver):
+    """Point blast (benchmark setup) at 64^3 for 50 steps."""
+    pr = P.sedov_3d(64, solver=solver)
+    Uo, to = oracle_run(pr, steps=50)
+    for precision, tol in PRECISIONS:
+        Ug, tg = gpu_run(pr, precision, steps=50)
+        assert tg == pytest.approx(to, rel=1e-9 if precision == H.FP64 else 1e-5)
+        _check(Ug, Uo, 3, tol, f"sedov 64^3 prec={precision}")
+
+
+def test_stretched_pulse_reduced():
+    """Centrally refined mesh (ratio 1.01 widths), Gaussian pulse, FP32-mixed
+    HLLC, 80^3 for 20 steps."""
+    pr = P.stretched_pulse_3d(80, steps=20)
+    Ug, _ = gpu_run(pr, H.FP32_MIXED, steps=20)
+    Uo, _ = oracle_run(pr, steps=20)
+    _check(Ug, Uo, 3, TOL_FP32, "stretched 80^3")
+
+
+def test_kelvin_helmholtz_reduced():
+    """Periodic shear layer at 64^2, HLLC, FP32-mixed and FP64, 40 steps."""
+    pr = P.kelvin_helmholtz(64, seed=5)
+    Uo, _ = oracle_run(pr, steps=40)
+    for precision, tol in ((H.FP64, TOL_FP64), (H.FP32_MIXED, TOL_FP32)):
+        Ug, _ = gpu_run(pr, precision, steps=40)
+        _check(Ug, Uo, 2, tol, f"kh prec={precision}")
+
+
+@pytest.mark.parametrize("tile", [0, 1, 2])
+def test_every_tile_shape_identical(tile):
+    """Each compiled tile shape and plane count gives bitwise the same state."""
+    pr = P.random_blocks(3, (70, 34, 41), seed=3, bc=P.REFLECT)
+    ref, _ = gpu_run(pr, H.FP32_MIXED, steps=4, tile=0, kchunk=0)
+    for kc in (0, 7, 41):
+        U, _ = gpu_run(pr, H.FP32_MIXED, steps=4, tile=tile, kchunk=kc)
+        np.testing.assert_array_equal(U, ref)
+
+
+def test_fixed_dt_step_matches_oracle():
+    """genasis_hydro_step with a caller-given dt."""
+    pr = P.random_blocks(2, (64, 50), seed=9, bc=P.OUTFLOW)
+    g = O.Grid(pr)
+    Uo = O.initial_state(pr, g)
+    h = H.Hydro.from_problem(pr, precision=H.FP64)
+    for dt in (1e-3, 2e-3, 5e-4):
+        h.step(dt)
+        Uo = O.step(g, Uo, dt)
+    _check(h.get_conserved(), Uo, 2, TOL_FP64, "fixed dt")
+    h.close()
+
+
+def test_compute_dt_and_totals_match_oracle():
+    pr = P.random_blocks(3, (33, 29, 17), seed=12, bc=P.PERIODIC)
+    g = O.Grid(pr)
+    U0 = O.initial_state(pr, g)
+    for precision, tol in ((H.FP64, 1e-14), (H.FP32_MIXED, 1e-6)):
+        h = H.Hydro.from_problem(pr, precision=precision)
+        assert h.compute_dt(0.4) == pytest.approx(0.4 * O.cfl_dt(g, U0), rel=tol)
+        np.testing.assert_allclose(h.totals(), O.totals(g, U0), rtol=tol, atol=tol * np.abs(O.totals(g, U0)).max())
+        h.close()
+
+
+def test_conservation_periodic_gpu():
+    """Totals stay constant to roundoff on a periodic box (FP64 and FP32)."""
+    pr = P.smooth_periodic(3, 48, seed=4, nonuniform=True)
+    for precision, tol in ((H.FP64, 1e-13), (H.FP32_MIXED, 2e-6)):
+        h = H.Hydro.from_problem(pr, precision=precision)
+        t0 = h.totals()
+        h.advance(30, 0.4)
+        t1 = h.totals()
+        np.testing.assert_allclose(t1, t0, rtol=0, atol=tol * np.abs(t0).max())
+        h.close()
+
+
+def test_device_and_host_pointers_agree():
+    """set/get through torch CUDA tensors equals the host-pointer path."""
+    import torch
+    pr = P.random_blocks(2, (40, 30), seed=1)
+    a = H.Hydro.from_problem(pr, precision=H.FP32_MIXED)
+    b = H.Hydro(pr.ndim, pr.n, pr.widths, pr.bc_lo, pr.bc_hi, pr.gamma, pr.solver, pr.theta, H.FP32_MIXED)
+    dev = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    b.set_primitive(dev(pr.rho), dev(pr.vel), dev(pr.p))
+    for h in (a, b):
+        h.advance(5, 0.4)
+    Ua = a.get_conserved()
+    Ub = torch.empty((4, 30, 40), dtype=torch.float32, device="cuda")
+    b.get_conserved(Ub)
+    np.testing.assert_array_equal(Ua, Ub.cpu().numpy())
+    # resume: set_conserved of a saved state continues bitwise identically
+    c = H.Hydro(pr.ndim, pr.n, pr.widths, pr.bc_lo, pr.bc_hi, pr.gamma, pr.solver, pr.theta, H.FP32_MIXED)
+    c.set_conserved(Ua)
+    a.advance(3, 0.4)
+    c.advance(3, 0.4)
+    np.testing.assert_array_equal(a.get_conserved(), c.get_conserved())
+    for h in (a, b, c):
+        h.close()
+
+
+def test_nonphysical_state_sets_status():
+    pr = P.sod(64)
+    pr.p[10] = -1.0
+    h = H.Hydro.from_problem(pr, precision=H.FP64)
+    with pytest.raises(H.NonPhysicalState):
+        h.advance(1, 0.5, sync=True)
+    h.clear_status()
+    h.close()
+
+
+# ----------------------------------------------------------- full-size workloads
+
+def _one_step_full(prob, precisions):
+    """One device-CFL step at full size, in the benchmark's launch
+    configuration, against one oracle step with the oracle's dt."""
+    g = O.Grid(prob)
+    U0 = O.initial_state(prob, g)
+    dt = prob.cfl * O.cfl_dt(g, U0)
+    Uo = O.step(g, U0, dt)
+    del U0
+    for precision, tol in precisions:
+        h = H.Hydro.from_problem(prob, precision=precision)
+        t = h.advance(1, prob.cfl)
+        assert t == pytest.approx(dt, rel=1e-12 if precision == H.FP64 else 1e-6)
+        Ug = h.get_conserved(precision=H.FP64)
+        h.close()
+        _check(Ug, Uo, prob.ndim, tol, f"{prob.name} prec={precision}")
+
+
+def test_sedov_full_size_one_step():
+    """256^3 point blast, one step, both precisions."""
+    _one_step_full(P.sedov_3d(256), PRECISIONS)
+
+
+def test_stretched_pulse_full_size_one_step():
+    """320^3 centrally refined mesh, one FP32-mixed step."""
+    _one_step_full(P.stretched_pulse_3d(320), ((H.FP32_MIXED, TOL_FP32),))
+
+
+def test_sedov_full_size_symmetry_and_mass():
+    """256^3, 20 FP64 steps: octant mirror symmetry and mass/energy totals."""
+    pr = P.sedov_3d(256)
+    h = H.Hydro.from_problem(pr, precision=H.FP64)
+    t0 = h.totals()
+    h.advance(20, pr.cfl)
+    t1 = h.totals()
+    U = h.get_conserved()
+    h.close()
+    assert t1[0] == pytest.approx(t0[0], rel=1e-12)
+    assert t1[4] == pytest.approx(t0[4], rel=1e-12)
+    np.testing.assert_allclose(U[0], U[0][::-1, ::-1, ::-1], rtol=1e-12)
+    np.testing.assert_allclose(U[0], np.transpose(U[0], (2, 1, 0)), rtol=1e-12)
