@@ -161,6 +161,68 @@ int genasis_hydro_profile_step(genasis_hydro_t h, double cfl, float *ms);
 /* Text of the last error of the calling thread (never NULL). */
 const char *genasis_hydro_last_error(void);
 
+/* ---------------------------------------------------------------------------
+ * Batches: many independent 1D and 2D problems of uneven size advanced
+ * together.  Every problem follows the same update as a single handle (same
+ * equations and passages as above) with its own mesh, boundaries, gamma, time
+ * and CFL time step; all problems of a batch share solver, theta and
+ * precision.  Each RK stage of the whole batch is one persistent kernel launch
+ * whose CTAs take (problem, tile, chunk) work items largest first from a
+ * device counter; genasis_batch_run captures nsteps steps as one CUDA graph.
+ * Arrays of problem i use the single-handle layout for that problem's ndim
+ * and n.  Ownership, pointer kinds, synchronisation and error codes follow the
+ * conventions at the top of this file.
+ * ------------------------------------------------------------------------- */
+typedef struct genasis_batch *genasis_batch_t;
+
+/* One problem: ndim 1 or 2, n[q] >= 2 cells, widths[q] host arrays of n[q]
+ * positive widths, bc codes as for genasis_hydro_desc, gamma > 1. */
+typedef struct {
+  int ndim;
+  int n[2];
+  const double *widths[2];
+  int bc_lo[2];
+  int bc_hi[2];
+  double gamma;
+} genasis_batch_problem;
+
+/* Create a batch of nprob problems (copied); allocates one state arena for
+ * all problems and builds the work list.  stream as in genasis_hydro_desc. */
+int genasis_batch_create(int nprob, const genasis_batch_problem *probs, int solver, double theta, int precision,
+                         void *stream, genasis_batch_t *out);
+int genasis_batch_destroy(genasis_batch_t b);
+
+/* Initial state of problem iprob from FP64 primitives (host or device),
+ * rho[ncell], vel[ndim * ncell], p[ncell]; resets that problem's time. */
+int genasis_batch_set_primitive(genasis_batch_t b, int iprob, const double *rho, const double *vel, const double *p);
+/* Conserved state of problem iprob, (ndim + 2) * ncell values in `precision`
+ * (host or device); synchronises. */
+int genasis_batch_get_conserved(genasis_batch_t b, int iprob, void *U, int precision);
+
+/* nsteps RK2 steps of every problem, each with its own dt = cfl * dt_CFL (taken
+ * on the device per problem); t_end > 0 stops each problem exactly at t_end.
+ * Asynchronous; one CUDA-graph launch. */
+int genasis_batch_run(genasis_batch_t b, int nsteps, double cfl, double t_end);
+
+/* Per-problem times (nprob doubles); synchronises. */
+int genasis_batch_get_times(genasis_batch_t b, double *t);
+/* Synchronise; GENASIS_ENONPHYS if any problem met a non-physical state, with
+ * *first_bad (if non-NULL) set to the lowest such problem index, else -1. */
+int genasis_batch_status(genasis_batch_t b, int *first_bad);
+
+/* Tile index (0 .. count-1: 128 or 256 threads per CTA) and rows per 2D work
+ * item (0 = automatic).  info[0..6] = (tile, threads, rows per item, work
+ * items, persistent CTAs, tile count, total cells / 2^20). */
+int genasis_batch_set_tile(genasis_batch_t b, int tile, int chunk);
+int genasis_batch_get_tile(genasis_batch_t b, int *info);
+/* Time each tile and a few chunk sizes for trial_steps steps on the current
+ * state, keep the fastest, restore state and times; cache file as for
+ * genasis_hydro_autotune (keyed by problem count, cells, precision, solver). */
+int genasis_batch_autotune(genasis_batch_t b, int trial_steps, const char *cache_path);
+/* Device durations of the last step's two persistent stage launches and the
+ * per-problem dt kernel (ms[0..2]) from one extra profiled step; synchronises. */
+int genasis_batch_profile_step(genasis_batch_t b, double cfl, float *ms);
+
 #ifdef __cplusplus
 }
 #endif

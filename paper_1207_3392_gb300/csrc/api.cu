@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "genasis_hydro.h"
+#include "common.h"
 #include "aux_kernels.h"
 #include "hydro_device.cuh"
 #include "registry.h"
@@ -29,14 +30,6 @@ int fail(int code, const char* fmt, ...) {
   va_end(ap);
   return code;
 }
-
-#define GH_CK(call)                                                                          \
-  do {                                                                                       \
-    cudaError_t e_ = (call);                                                                 \
-    if (e_ != cudaSuccess)                                                                   \
-      return fail(e_ == cudaErrorMemoryAllocation ? GENASIS_ENOMEM : GENASIS_ECUDA, "%s: %s", \
-                  #call, cudaGetErrorString(e_));                                            \
-  } while (0)
 
 bool is_device_ptr(const void* p) {
   cudaPointerAttributes at;

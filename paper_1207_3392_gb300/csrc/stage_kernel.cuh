@@ -110,8 +110,8 @@ struct StageKernel {
     for (int v = 0; v < NV; ++v) {
       const T w0 = S.w[v][srow][sl - 1], w1 = S.w[v][srow][sl], w2 = S.w[v][srow][sl + 1],
               w3 = S.w[v][srow][sl + 2];
-      wl[v] = w1 + limited_slope(w0, w1, w2, gl, A.theta) * gl.h;
-      wr[v] = w2 - limited_slope(w1, w2, w3, gr, A.theta) * gr.h;
+      wl[v] = fma(limited_slope(w0, w1, w2, gl, A.theta), gl.h, w1);
+      wr[v] = fma(-limited_slope(w1, w2, w3, gr, A.theta), gr.h, w2);
     }
     face_flux<T, NDIM, 0, SOLVER>(wl, wr, A.gamma, A.gm1, f);
 #pragma unroll
@@ -126,8 +126,8 @@ struct StageKernel {
     for (int v = 0; v < NV; ++v) {
       const T w0 = S.w[v][sl - 1][scol], w1 = S.w[v][sl][scol], w2 = S.w[v][sl + 1][scol],
               w3 = S.w[v][sl + 2][scol];
-      wl[v] = w1 + limited_slope(w0, w1, w2, gl, A.theta) * gl.h;
-      wr[v] = w2 - limited_slope(w1, w2, w3, gr, A.theta) * gr.h;
+      wl[v] = fma(limited_slope(w0, w1, w2, gl, A.theta), gl.h, w1);
+      wr[v] = fma(-limited_slope(w1, w2, w3, gr, A.theta), gr.h, w2);
     }
     face_flux<T, NDIM, 1, SOLVER>(wl, wr, A.gamma, A.gm1, f);
 #pragma unroll
@@ -142,8 +142,8 @@ struct StageKernel {
     T wl[NV], wr[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      wl[v] = wa[v] + sa[v] * ha;
-      wr[v] = wb[v] - sb[v] * hb;
+      wl[v] = fma(sa[v], ha, wa[v]);
+      wr[v] = fma(-sb[v], hb, wb[v]);
     }
     face_flux<T, NDIM, AM, SOLVER>(wl, wr, A.gamma, A.gm1, f);
   }
@@ -161,48 +161,52 @@ struct StageKernel {
     return bad;
   }
 
-  static __device__ void run(const StageArgs<T>& A) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    Smem& S = *reinterpret_cast<Smem*>(smem_raw);
+  // One tile (bx, by) and march chunk bz of the stage.  Accumulates the
+  // thread's CFL speed (stage 1), its share of the totals (stage 1) and the
+  // non-physical flag; the caller reduces them.  All threads of the block must
+  // call it together (it synchronises).
+  static __device__ void tile(const StageArgs<T>& A, Smem& S, int bx, int by, int bz, double& speed_max,
+                              double (&tot)[NV], bool& bad) {
     const int tid = threadIdx.x;
     const int tx = tid % TX, ty = tid / TX;
     const int nx = A.n[0];
     const int ny = HAS_Y ? A.n[1] : 1;
     const int nm = MARCH ? A.n[AM] : 1;
     const size_t vs = (size_t)A.n[0] * A.n[1] * A.n[2];
-    const int a0 = blockIdx.x * TX;
-    const int b0 = HAS_Y ? blockIdx.y * TY : 0;
+    const int a0 = bx * TX;
+    const int b0 = HAS_Y ? by * TY : 0;
     const int ca = a0 + tx, cb = b0 + ty;
     const bool own_valid = ca < nx && cb < ny;
-    const int m0 = MARCH ? blockIdx.z * A.kchunk : 0;
+    const int m0 = MARCH ? bz * A.kchunk : 0;
     const int m1 = MARCH ? min(nm, m0 + A.kchunk) : 1;
     const T dt = STAGE == 2 ? (T)(*A.dt) : T(0);
 
     const T iwx = A.iw[0][min(ca, nx + 1) + 2];
     const T iwy = HAS_Y ? A.iw[1][min(cb, ny + 1) + 2] : T(0);
 
-    // per-thread reductions (stage 1)
-    double speed_max = 0.0;
-    double tot[NV];
+    double tcol[NV];  // this column's sum of U dq along the march axis
 #pragma unroll
-    for (int v = 0; v < NV; ++v) tot[v] = 0.0;
-    bool bad = false;
+    for (int v = 0; v < NV; ++v) tcol[v] = 0.0;
 
-    // march-axis register ring: W at planes m and m+1, slope at m, flux at m-1/2
+    // March-axis register ring.  At the top of iteration m: wk = W(m),
+    // wk1 = W(m+1), sk = slope(m), flo = flux(m-1/2).  The loop starts two
+    // planes early so that every march-axis slope and face flux of the chunk
+    // comes from the same code (bitwise the same values as the neighbouring
+    // chunk computes for the shared face).
     T wk[NV], wk1[NV], sk[NV], flo[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      sk[v] = T(0);
+      flo[v] = T(0);
+    }
+    int mstart = m0;
     if constexpr (MARCH) {
-      T wa[NV], wb[NV], sa[NV];
-      load_prim(A, ca, cb, m0 - 2, dt, vs, wa);
-      load_prim(A, ca, cb, m0 - 1, dt, vs, wb);
-      load_prim(A, ca, cb, m0, dt, vs, wk);
-      load_prim(A, ca, cb, m0 + 1, dt, vs, wk1);
-      const Geo<T> ga = geo(A, AM, m0 - 1), g0 = geo(A, AM, m0);
-      slopes(A, wa, wb, wk, ga, sa);
-      slopes(A, wb, wk, wk1, g0, sk);
-      m_face(A, wb, sa, ga.h, wk, sk, g0.h, flo);
+      load_prim(A, ca, cb, m0 - 2, dt, vs, wk);
+      load_prim(A, ca, cb, m0 - 1, dt, vs, wk1);
+      mstart = m0 - 2;
     }
 
-    for (int m = m0; m < m1; ++m) {
+    for (int m = mstart; m < m1; ++m) {
       T fhi[NV], wk2[NV], sk1[NV];
       T wown[NV];
       if constexpr (MARCH) {
@@ -210,6 +214,16 @@ struct StageKernel {
         const Geo<T> g0 = geo(A, AM, m), g1 = geo(A, AM, m + 1);
         slopes(A, wk, wk1, wk2, g1, sk1);
         m_face(A, wk, sk, g0.h, wk1, sk1, g1.h, fhi);
+        if (m < m0) {  // warm-up planes: advance the ring only
+#pragma unroll
+          for (int v = 0; v < NV; ++v) {
+            flo[v] = fhi[v];
+            wk[v] = wk1[v];
+            wk1[v] = wk2[v];
+            sk[v] = sk1[v];
+          }
+          continue;
+        }
 #pragma unroll
         for (int v = 0; v < NV; ++v) wown[v] = wk[v];
       } else {
@@ -238,18 +252,23 @@ struct StageKernel {
       }
       __syncthreads();
 
-      // in-plane faces, each computed once
-      const int srow = HAS_Y ? ty + 2 : 0;
-      x_face(A, S, a0, tx, srow, ty);
-      if constexpr (HAS_Y) y_face(A, S, b0, ty, tx + 2);
+      // in-plane faces, each computed once, one call site per axis
       {
-        const int extra = tid - (NT - (HAS_Y ? TY + TX : 32));
-        // last x face of each row (TY items) and last y face of each column (TX items)
-        if constexpr (HAS_Y) {
-          if (extra >= 0 && extra < TY) x_face(A, S, a0, TX, extra + 2, extra);
-          else if (extra >= TY && extra < TY + TX) y_face(A, S, b0, TY, extra - TY + 2);
-        } else {
-          if (extra == 0) x_face(A, S, a0, TX, 0, 0);
+        constexpr int NXF = (TX + 1) * TY;
+        constexpr int NYF = HAS_Y ? TX * (TY + 1) : 0;
+        for (int f = tid; f < NXF + NYF; f += NT) {
+          if (f < NXF) {
+            const int row = f / (TX + 1);
+            const int face = f - row * (TX + 1);
+            x_face(A, S, a0, face, HAS_Y ? row + 2 : 0, row);
+          } else {
+            if constexpr (HAS_Y) {
+              const int g = f - NXF;
+              const int face = g / TX;
+              const int col = g - face * TX;
+              y_face(A, S, b0, face, col + 2);
+            }
+          }
         }
       }
       __syncthreads();
@@ -278,7 +297,7 @@ struct StageKernel {
           if (A.want_totals) {
             const double dm = MARCH ? A.wd[AM][m] : 1.0;
 #pragma unroll
-            for (int v = 0; v < NV; ++v) tot[v] = fma((double)__ldg(A.un + v * vs + c), dm, tot[v]);
+            for (int v = 0; v < NV; ++v) tcol[v] = fma((double)__ldg(A.un + v * vs + c), dm, tcol[v]);
           }
         } else {
           const T hdt = T(0.5) * dt;
@@ -300,31 +319,49 @@ struct StageKernel {
       }
     }
 
+    if (STAGE == 1 && own_valid && A.want_totals) {
+      double area = A.wd[0][ca];
+      if constexpr (HAS_Y) area *= A.wd[1][cb];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) tot[v] = fma(tcol[v], area, tot[v]);
+    }
+  }
+
+  // Fixed-order block reduction of (max speed, totals) into per-CTA partials.
+  static __device__ void write_partials(const StageArgs<T>& A, Smem& S, size_t blk, double speed_max,
+                                        const double (&tot)[NV]) {
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    double r[NV + 1];
+    r[0] = warp_max(speed_max);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) r[1 + v] = warp_sum(tot[v]);
+    if (lane == 0) {
+#pragma unroll
+      for (int v = 0; v <= NV; ++v) S.red[warp][v] = r[v];
+    }
+    __syncthreads();
+    if (tid <= NV) {
+      double acc = S.red[0][tid];
+      for (int wi = 1; wi < NT / 32; ++wi) acc = tid == 0 ? fmax(acc, S.red[wi][0]) : acc + S.red[wi][tid];
+      if (tid == 0) A.part_speed[blk] = acc;
+      else A.part_tot[blk * NV + (tid - 1)] = acc;
+    }
+  }
+
+  static __device__ void run(const StageArgs<T>& A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem& S = *reinterpret_cast<Smem*>(smem_raw);
+    double speed_max = 0.0;
+    double tot[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) tot[v] = 0.0;
+    bool bad = false;
+    tile(A, S, blockIdx.x, blockIdx.y, blockIdx.z, speed_max, tot, bad);
     if (bad) atomicOr(A.status, STATUS_NONPHYS);
     if (STAGE == 1) {
-      // per-CTA partials, fixed-order reduction
-      const int warp = tid >> 5, lane = tid & 31;
-      double area = 0.0;
-      if (own_valid && A.want_totals) {
-        area = A.wd[0][ca];
-        if constexpr (HAS_Y) area *= A.wd[1][cb];
-      }
-      double r[NV + 1];
-      r[0] = warp_max(speed_max);
-#pragma unroll
-      for (int v = 0; v < NV; ++v) r[1 + v] = warp_sum(tot[v] * area);
-      if (lane == 0) {
-#pragma unroll
-        for (int v = 0; v <= NV; ++v) S.red[warp][v] = r[v];
-      }
-      __syncthreads();
-      if (tid <= NV) {
-        double acc = S.red[0][tid];
-        for (int wi = 1; wi < NT / 32; ++wi) acc = tid == 0 ? fmax(acc, S.red[wi][0]) : acc + S.red[wi][tid];
-        const size_t blk = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-        if (tid == 0) A.part_speed[blk] = acc;
-        else A.part_tot[blk * NV + (tid - 1)] = acc;
-      }
+      const size_t blk = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+      write_partials(A, S, blk, speed_max, tot);
     }
   }
 };

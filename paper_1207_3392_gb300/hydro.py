@@ -66,6 +66,17 @@ SIGNATURES = {
     "genasis_hydro_autotune": [_P, _I, ctypes.c_char_p],
     "genasis_hydro_launches_per_step": [_P],
     "genasis_hydro_profile_step": [_P, _D, _P],
+    "genasis_batch_create": [_I, _P, _I, _D, _I, _P, ctypes.POINTER(_P)],
+    "genasis_batch_destroy": [_P],
+    "genasis_batch_set_primitive": [_P, _I, _P, _P, _P],
+    "genasis_batch_get_conserved": [_P, _I, _P, _I],
+    "genasis_batch_run": [_P, _I, _D, _D],
+    "genasis_batch_get_times": [_P, _P],
+    "genasis_batch_status": [_P, _P],
+    "genasis_batch_set_tile": [_P, _I, _I],
+    "genasis_batch_get_tile": [_P, _P],
+    "genasis_batch_autotune": [_P, _I, ctypes.c_char_p],
+    "genasis_batch_profile_step": [_P, _D, _P],
 }
 
 
@@ -131,6 +142,8 @@ class Hydro:
             d.bc_lo[q] = int(bc_lo[q]) if q < self.ndim else 0
             d.bc_hi[q] = int(bc_hi[q]) if q < self.ndim else 0
         d.gamma, d.solver, d.theta, d.precision = float(gamma), int(solver), float(theta), self.precision
+        # stream: a cudaStream_t handle (int) or torch.cuda.Stream; None or 0
+        # (the legacy default stream) gives the handle a stream of its own
         if stream is not None:
             d.stream = stream if isinstance(stream, int) else int(getattr(stream, "cuda_stream", stream))
         self._h = ctypes.c_void_p()
@@ -257,3 +270,101 @@ class Hydro:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class BatchProblemDesc(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int), ("n", ctypes.c_int * 2), ("widths", ctypes.c_void_p * 2),
+                ("bc_lo", ctypes.c_int * 2), ("bc_hi", ctypes.c_int * 2), ("gamma", ctypes.c_double)]
+
+
+class Batch:
+    """Many independent 1D/2D problems advanced together (genasis_batch_t)."""
+
+    def __init__(self, problems, solver=HLLC, theta=1.4, precision=FP64, stream=None):
+        lib = load()
+        self.precision = int(precision)
+        self.nprob = len(problems)
+        self._keep = []
+        arr = (BatchProblemDesc * self.nprob)()
+        self.meta = []
+        for i, pr in enumerate(problems):
+            d = arr[i]
+            d.ndim = pr.ndim
+            ws = []
+            for q in range(2):
+                active = q < pr.ndim
+                d.n[q] = int(pr.n[q]) if active else 1
+                if active:
+                    w = np.ascontiguousarray(pr.widths[q], dtype=np.float64)
+                    ws.append(w)
+                    d.widths[q] = w.ctypes.data
+                d.bc_lo[q] = int(pr.bc_lo[q]) if active else 2
+                d.bc_hi[q] = int(pr.bc_hi[q]) if active else 2
+            d.gamma = float(pr.gamma)
+            self._keep.append(ws)
+            shape = tuple(reversed([int(pr.n[q]) for q in range(pr.ndim)]))
+            self.meta.append((pr.ndim, shape, int(np.prod(shape))))
+        s = 0
+        if stream is not None:
+            s = stream if isinstance(stream, int) else int(getattr(stream, "cuda_stream", stream))
+        self._h = ctypes.c_void_p()
+        check(lib.genasis_batch_create(self.nprob, ctypes.cast(arr, ctypes.c_void_p), int(solver), float(theta),
+                                       self.precision, s or None, ctypes.byref(self._h)))
+        self._keep = None
+
+    def set_primitive(self, i, rho, vel, p):
+        ndim, shape, nc = self.meta[i]
+        pr, a = _ptr(rho, np.float64, nc, "rho")
+        pv, b = _ptr(vel, np.float64, nc * ndim, "vel")
+        pp, c = _ptr(p, np.float64, nc, "p")
+        check(load().genasis_batch_set_primitive(self._h, int(i), pr, pv, pp))
+
+    def get_conserved(self, i, precision=FP64):
+        ndim, shape, nc = self.meta[i]
+        dt = np.float64 if precision == FP64 else np.float32
+        out = np.empty((ndim + 2,) + shape, dtype=dt)
+        check(load().genasis_batch_get_conserved(self._h, int(i), out.ctypes.data, int(precision)))
+        return out
+
+    def run(self, nsteps, cfl, t_end=0.0):
+        check(load().genasis_batch_run(self._h, int(nsteps), float(cfl), float(t_end)))
+
+    def times(self):
+        t = np.zeros(self.nprob)
+        check(load().genasis_batch_get_times(self._h, t.ctypes.data))
+        return t
+
+    def status(self):
+        bad = ctypes.c_int(-1)
+        rc = load().genasis_batch_status(self._h, ctypes.byref(bad))
+        if rc != OK:
+            check(rc)
+        return bad.value
+
+    def set_tile(self, tile, chunk=0):
+        check(load().genasis_batch_set_tile(self._h, int(tile), int(chunk)))
+
+    def tile_info(self):
+        info = (ctypes.c_int * 7)()
+        check(load().genasis_batch_get_tile(self._h, info))
+        return dict(zip(("tile", "threads", "chunk", "items", "ctas", "tile_count", "mcells"), list(info)))
+
+    def autotune(self, trial_steps=2, cache_path=None):
+        check(load().genasis_batch_autotune(self._h, int(trial_steps), cache_path.encode() if cache_path else None))
+        return self.tile_info()
+
+    def profile_step(self, cfl):
+        ms = (ctypes.c_float * 3)()
+        check(load().genasis_batch_profile_step(self._h, float(cfl), ms))
+        return tuple(ms)
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load().genasis_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
