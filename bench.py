@@ -46,7 +46,7 @@ def _args():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="sedov", choices=["sedov", "batch"])
-    ap.add_argument("--autotune", action="store_true", help="autotune tiles before timing")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default tile instead of autotuning")
     return ap.parse_args()
 
 
@@ -203,6 +203,9 @@ def run_ours(args):
     del prob
     cells = h.ncell
     cfl = 0.3
+    if not args.no_autotune:
+        h.autotune(trial_steps=3)
+    tile = h.tile_info()
 
     def barrier():
         if world > 1:
@@ -256,7 +259,7 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if prec == H.FP32_MIXED else "f64", "data": "synthetic",
-            "config": _config(args, n), "roofline": roofline, "clocks": clocks,
+            "config": dict(_config(args, n), tile=tile), "roofline": roofline, "clocks": clocks,
             "gpu_launches": args.steps * h.launches_per_step()}
 
     # end to end through the C ABI with host buffers: set_conserved (pinned
@@ -285,12 +288,14 @@ def run_ours(args):
     # other precision / solver combinations of the same workload (context)
     if not args.no_variants and rank == 0:
         variants = {}
-        for pname, pc in (("fp32", H.FP32_MIXED), ("fp64", H.FP64)):
-            for sname in ("hllc", "hll"):
-                if (pname, sname) == (args.precision, args.solver):
+        for pname, pc, sname, totals in (("fp32", H.FP32_MIXED, args.solver, False),
+                                         ("fp32", H.FP32_MIXED, "hllc", True), ("fp32", H.FP32_MIXED, "hll", True),
+                                         ("fp64", H.FP64, "hllc", True), ("fp64", H.FP64, "hll", True)):
+                if (pname, sname, totals) == (args.precision, args.solver, True):
                     continue
                 pr = _workload(n, sname)
                 hv = H.Hydro.from_problem(pr, precision=pc, stream=stream.cuda_stream)
+                hv.set_step_totals(totals)
                 del pr
                 kv = 3 if pc == H.FP64 else 5
                 for _ in range(2):
@@ -303,7 +308,8 @@ def run_ours(args):
                 z.record(stream)
                 torch.cuda.synchronize()
                 mv = a.elapsed_time(z) / kv
-                variants[f"{sname}_{pname}"] = {"value": cells * 2 / (mv * 1e-3), "ms_per_step": mv}
+                key = f"{sname}_{pname}" + ("" if totals else "_no_step_totals")
+                variants[key] = {"value": cells * 2 / (mv * 1e-3), "ms_per_step": mv}
                 hv.close()
         line["variants"] = variants
 
@@ -345,7 +351,7 @@ def run_batch(args):
         b.set_primitive(i, pr.rho, pr.vel, pr.p)
     cells = sum(sp.n ** sp.ndim for sp in specs)
     cells_nv = sum(sp.n ** sp.ndim * (sp.ndim + 2) for sp in specs)
-    if args.autotune:
+    if not args.no_autotune:
         b.autotune(trial_steps=2)
     for _ in range(max(args.warmup, 3)):
         b.run(1, 0.5)

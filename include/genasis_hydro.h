@@ -149,6 +149,16 @@ int genasis_hydro_get_tile(genasis_hydro_t h, int *info);
  * file, keyed by (ndim, n, precision, solver).  Synchronises. */
 int genasis_hydro_autotune(genasis_hydro_t h, int trial_steps, const char *cache_path);
 
+/* Handle options.  GENASIS_OPT_STEP_TOTALS: 1 (default) folds the FP64
+ * conserved totals of U^n into stage 1 of every step (readable after the step
+ * with genasis_hydro_get_step_totals); 0 skips that work.  Returns EINVAL for
+ * an unknown option or value. */
+#define GENASIS_OPT_STEP_TOTALS 1
+int genasis_hydro_set_option(genasis_hydro_t h, int option, int value);
+/* Totals of U^n of the last step taken with GENASIS_OPT_STEP_TOTALS = 1
+ * (totals[0 .. ndim + 1]); synchronises. */
+int genasis_hydro_get_step_totals(genasis_hydro_t h, double *totals);
+
 /* Number of kernel launches one step enqueues. */
 int genasis_hydro_launches_per_step(genasis_hydro_t h);
 
@@ -160,6 +170,7 @@ int genasis_hydro_profile_step(genasis_hydro_t h, double cfl, float *ms);
 
 /* Text of the last error of the calling thread (never NULL). */
 const char *genasis_hydro_last_error(void);
+
 
 /* ---------------------------------------------------------------------------
  * Batches: many independent 1D and 2D problems of uneven size advanced

@@ -628,6 +628,29 @@ int genasis_hydro_get_tile(genasis_hydro_t h, int* info) {
   return GENASIS_OK;
 }
 
+int genasis_hydro_set_option(genasis_hydro_t h, int option, int value) {
+  if (!h) return fail(GENASIS_EINVAL, "NULL handle");
+  if (option == GENASIS_OPT_STEP_TOTALS) {
+    if (value != 0 && value != 1) return fail(GENASIS_EINVAL, "GENASIS_OPT_STEP_TOTALS takes 0 or 1");
+    if (h->want_totals != value) {
+      h->want_totals = value;
+      for (int b = 0; b < 2; ++b)
+        if (h->graph[b]) {
+          cudaGraphExecDestroy(h->graph[b]);
+          h->graph[b] = nullptr;
+        }
+    }
+    return GENASIS_OK;
+  }
+  return fail(GENASIS_EINVAL, "unknown option %d", option);
+}
+
+int genasis_hydro_get_step_totals(genasis_hydro_t h, double* totals) {
+  if (!h || !totals) return fail(GENASIS_EINVAL, "NULL argument");
+  GH_CK(cudaMemcpyAsync(totals, h->scal + SCAL_TOT, h->nv * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  return sync_status(h);
+}
+
 int genasis_hydro_launches_per_step(genasis_hydro_t h) {
   if (!h) return fail(GENASIS_EINVAL, "NULL handle");
   return 3;

@@ -57,14 +57,27 @@ __device__ __forceinline__ T limited_slope(T wm, T wc, T wp, const Geo<T>& g, T 
   return minmod3(theta * ((wc - wm) * g.icm), (wp - wm) * g.ipm, theta * ((wp - wc) * g.ipc));
 }
 
+// Division, reciprocal and square root used by the flux arithmetic.  FP64
+// keeps IEEE operations (its parity bar is 1e-10); FP32 uses the hardware
+// approximations (a few ulp, far inside its 1e-5 bar).
+__device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double frcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ float frcp(float x) { return __fdividef(1.0f, x); }
+// sqrt of a positive argument
+__device__ __forceinline__ double fsqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float fsqrt(float x) { return x * rsqrtf(x); }
+
 // ---------------------------------------------------------------------------
 // Conserved -> primitive recovery.
 //
 // FP64 path: plain double arithmetic.
-// Mixed path (FP32 storage): the cancelling difference G - |S|^2 / (2 D) is
-// formed in FP64 as e D = G D - |S|^2 / 2, where every product of two FP32
-// values is exact in FP64, so the cancellation loses nothing; the
-// well-conditioned divisions v = S / D and e = (e D) / D then run in FP32.
+// Mixed path (FP32 storage): e = G - |S|^2 / (2 D) cancels when the kinetic
+// energy density is a large part of G.  Where the kinetic part is at most
+// half of G the FP32 difference loses at most one bit and is used as is;
+// elsewhere the difference is formed in FP64 as e D = G D - |S|^2 / 2, where
+// every product of two FP32 values is exact, so the cancellation loses
+// nothing, and the well-conditioned division by D runs in FP32.
 // ---------------------------------------------------------------------------
 template <int NDIM>
 __device__ __forceinline__ void recover(const double (&u)[NDIM + 2], double (&w)[NDIM + 2]) {
@@ -80,18 +93,31 @@ __device__ __forceinline__ void recover(const double (&u)[NDIM + 2], double (&w)
   w[NV - 1] = u[NV - 1] - 0.5 * u[0] * v2;
 }
 
+// e D = G D - |S|^2 / 2 in FP64 (products of FP32 values are exact in FP64).
+// Kept out of line so that only lanes that need it execute FP64 instructions.
+static __device__ __noinline__ float energy_density_times_n_fp64(float n, float s1, float s2, float s3, float G) {
+  const double s2d = fma((double)s1, (double)s1, fma((double)s2, (double)s2, (double)s3 * (double)s3));
+  return (float)fma(-0.5, s2d, (double)G * (double)n);
+}
+
 template <int NDIM>
 __device__ __forceinline__ void recover(const float (&u)[NDIM + 2], float (&w)[NDIM + 2]) {
   constexpr int NV = NDIM + 2;
-  double s2 = 0.0;
+  const float rn = frcp(u[0]);
+  float s2 = 0.0f;
 #pragma unroll
-  for (int q = 0; q < NDIM; ++q) s2 = fma((double)u[1 + q], (double)u[1 + q], s2);
-  const double eD = fma(-0.5, s2, (double)u[NV - 1] * (double)u[0]);
-  const float rn = 1.0f / u[0];
+  for (int q = 0; q < NDIM; ++q) s2 = fmaf(u[1 + q], u[1 + q], s2);
+  const float ke = 0.5f * s2 * rn;
+  float e = u[NV - 1] - ke;
+  if (__builtin_expect(!(ke <= 0.5f * u[NV - 1]), 0)) {
+    const float eD = energy_density_times_n_fp64(u[0], u[1], NDIM > 1 ? u[2] : 0.0f, NDIM > 2 ? u[3] : 0.0f,
+                                                 u[NV - 1]);
+    e = eD * rn;
+  }
   w[0] = u[0];
 #pragma unroll
   for (int q = 0; q < NDIM; ++q) w[1 + q] = u[1 + q] * rn;
-  w[NV - 1] = (float)eD * rn;
+  w[NV - 1] = e;
 }
 
 // ---------------------------------------------------------------------------
@@ -148,13 +174,13 @@ __device__ __forceinline__ void face_flux(const T (&wl)[NDIM + 2], const T (&wr)
   fl[NV - 1] = (ul[NV - 1] + pl) * vl;
   fr[NV - 1] = (ur[NV - 1] + pr) * vr;
 
-  const T cl = sqrt(gamma * pl / nl);
-  const T cr = sqrt(gamma * pr / nr);
+  const T cl = fsqrt(gamma * fdiv(pl, nl));
+  const T cr = fsqrt(gamma * fdiv(pr, nr));
   const T ap = fmax(T(0), fmax(vl + cl, vr + cr));
   const T am = fmax(T(0), fmax(cl - vl, cr - vr));
 
   if (SOLVER == SOLVER_HLL) {
-    const T inv = T(1) / (ap + am);
+    const T inv = frcp(ap + am);
     const T apam = ap * am;
 #pragma unroll
     for (int v = 0; v < NV; ++v) F[v] = (ap * fl[v] + am * fr[v] - apam * (ur[v] - ul[v])) * inv;
@@ -164,14 +190,14 @@ __device__ __forceinline__ void face_flux(const T (&wl)[NDIM + 2], const T (&wr)
   // HLLC
   const T sl = am + vl;  // = -(S_L - v_L) > 0
   const T sr = ap - vr;  // =   S_R - v_R  > 0
-  const T alpha_m = (ur[1 + Q] * sr + ul[1 + Q] * sl - (pr - pl)) / (nr * sr + nl * sl);
+  const T alpha_m = fdiv(ur[1 + Q] * sr + ul[1 + Q] * sl - (pr - pl), nr * sr + nl * sl);
   const bool left = alpha_m >= T(0);
   const T SK = left ? -am : ap;
   const T nK = left ? nl : nr;
   const T vK = left ? vl : vr;
   const T pK = left ? pl : pr;
   const T dK = SK - vK;                       // S_K - v_K
-  const T rden = T(1) / (SK - alpha_m);
+  const T rden = frcp(SK - alpha_m);
   const T Ds = nK * dK * rden;
   const T ps = pK + nK * dK * (alpha_m - vK);
   T us[NV];
@@ -190,6 +216,36 @@ __device__ __forceinline__ void face_flux(const T (&wl)[NDIM + 2], const T (&wr)
     F[v] = f;
   }
 }
+
+// Column sums of the conserved totals.  FP64 state: plain FP64 FMA.  FP32
+// state: a compensated pair of floats (Knuth's TwoSum plus the exact rounding
+// error of each product from an FMA), about 48 significant bits, so no FP64
+// instruction runs per cell; the pair is folded into FP64 once per column.
+template <class T>
+struct ColumnSum;
+
+template <>
+struct ColumnSum<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add_product(double u, double dz_hi, double) { s = fma(u, dz_hi, s); }
+  __device__ __forceinline__ double value() const { return s; }
+};
+
+template <>
+struct ColumnSum<float> {
+  float hi = 0.0f, lo = 0.0f;
+  // add u * (dz_hi + dz_lo)
+  __device__ __forceinline__ void add_product(float u, float dz_hi, float dz_lo) {
+    const float p = u * dz_hi;
+    const float pe = fmaf(u, dz_hi, -p) + u * dz_lo;
+    const float t = hi + p;
+    const float bp = t - hi;
+    const float err = (hi - (t - bp)) + (p - bp);
+    hi = t;
+    lo += err + pe;
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
 
 // Deterministic block reductions (fixed shuffle tree, then warps in order).
 template <class T>

@@ -8,21 +8,21 @@
 
 namespace gh {
 
-template <int NDIM, class T, int SOLVER, int STAGE, int TX, int TY>
+template <int NDIM, class T, int SOLVER, int STAGE, int TX, int TY, int MINB>
 inline void fill_variant(StageVariant* out) {
   using K = StageKernel<NDIM, T, SOLVER, STAGE, TX, TY>;
-  out->fn = reinterpret_cast<const void*>(&hydro_stage_kernel<NDIM, T, SOLVER, STAGE, TX, TY>);
+  out->fn = reinterpret_cast<const void*>(&hydro_stage_kernel<NDIM, T, SOLVER, STAGE, TX, TY, MINB>);
   out->smem = sizeof(typename K::Smem);
   out->tx = TX;
   out->ty = TY;
 }
 
-template <int NDIM, class T, int TX, int TY>
+template <int NDIM, class T, int TX, int TY, int MINB = 1>
 inline bool pick_variant(int solver, int stage, StageVariant* out) {
-  if (solver == SOLVER_HLL && stage == 1) fill_variant<NDIM, T, SOLVER_HLL, 1, TX, TY>(out);
-  else if (solver == SOLVER_HLL && stage == 2) fill_variant<NDIM, T, SOLVER_HLL, 2, TX, TY>(out);
-  else if (solver == SOLVER_HLLC && stage == 1) fill_variant<NDIM, T, SOLVER_HLLC, 1, TX, TY>(out);
-  else if (solver == SOLVER_HLLC && stage == 2) fill_variant<NDIM, T, SOLVER_HLLC, 2, TX, TY>(out);
+  if (solver == SOLVER_HLL && stage == 1) fill_variant<NDIM, T, SOLVER_HLL, 1, TX, TY, MINB>(out);
+  else if (solver == SOLVER_HLL && stage == 2) fill_variant<NDIM, T, SOLVER_HLL, 2, TX, TY, MINB>(out);
+  else if (solver == SOLVER_HLLC && stage == 1) fill_variant<NDIM, T, SOLVER_HLLC, 1, TX, TY, MINB>(out);
+  else if (solver == SOLVER_HLLC && stage == 2) fill_variant<NDIM, T, SOLVER_HLLC, 2, TX, TY, MINB>(out);
   else return false;
   return true;
 }

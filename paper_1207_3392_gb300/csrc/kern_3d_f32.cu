@@ -3,13 +3,16 @@
 
 namespace gh {
 
-int tile_count_3d() { return 3; }
+int tile_count_3d() { return 4; }
 
+// Register caps: 256-thread tiles at 3 CTAs per SM and 128-thread tiles at 6
+// (80 registers, 24 resident warps); tile 3 keeps the uncapped allocation.
 bool stage_variant_3d_f32(int solver, int stage, int tile, StageVariant* out) {
   switch (tile) {
-    case 0: return pick_variant<3, float, 32, 8>(solver, stage, out);
-    case 1: return pick_variant<3, float, 32, 4>(solver, stage, out);
-    case 2: return pick_variant<3, float, 64, 4>(solver, stage, out);
+    case 0: return pick_variant<3, float, 32, 8, 3>(solver, stage, out);
+    case 1: return pick_variant<3, float, 32, 4, 6>(solver, stage, out);
+    case 2: return pick_variant<3, float, 64, 4, 3>(solver, stage, out);
+    case 3: return pick_variant<3, float, 32, 8, 2>(solver, stage, out);
   }
   return false;
 }

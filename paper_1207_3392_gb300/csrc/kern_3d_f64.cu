@@ -8,6 +8,7 @@ bool stage_variant_3d_f64(int solver, int stage, int tile, StageVariant* out) {
     case 0: return pick_variant<3, double, 32, 8>(solver, stage, out);
     case 1: return pick_variant<3, double, 32, 4>(solver, stage, out);
     case 2: return pick_variant<3, double, 64, 4>(solver, stage, out);
+    case 3: return pick_variant<3, double, 32, 4, 2>(solver, stage, out);
   }
   return false;
 }

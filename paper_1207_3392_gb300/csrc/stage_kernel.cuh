@@ -165,7 +165,7 @@ struct StageKernel {
   // thread's CFL speed (stage 1), its share of the totals (stage 1) and the
   // non-physical flag; the caller reduces them.  All threads of the block must
   // call it together (it synchronises).
-  static __device__ void tile(const StageArgs<T>& A, Smem& S, int bx, int by, int bz, double& speed_max,
+  static __device__ void tile(const StageArgs<T>& A, Smem& S, int bx, int by, int bz, double& speed_out,
                               double (&tot)[NV], bool& bad) {
     const int tid = threadIdx.x;
     const int tx = tid % TX, ty = tid / TX;
@@ -184,9 +184,8 @@ struct StageKernel {
     const T iwx = A.iw[0][min(ca, nx + 1) + 2];
     const T iwy = HAS_Y ? A.iw[1][min(cb, ny + 1) + 2] : T(0);
 
-    double tcol[NV];  // this column's sum of U dq along the march axis
-#pragma unroll
-    for (int v = 0; v < NV; ++v) tcol[v] = 0.0;
+    ColumnSum<T> tcol[NV];  // this column's sum of U dq along the march axis
+    T speed_max = T(0);
 
     // March-axis register ring.  At the top of iteration m: wk = W(m),
     // wk1 = W(m+1), sk = slope(m), flo = flux(m-1/2).  The loop starts two
@@ -289,15 +288,16 @@ struct StageKernel {
 #pragma unroll
           for (int v = 0; v < NV; ++v) A.out[v * vs + c] = L[v];
           // CFL speed (Eq. courantTimeStep) on U^n at the cell centre
-          const T cs = sqrt(A.gamma * (A.gm1 * wown[NV - 1]) / wown[0]);
+          const T cs = fsqrt(A.gamma * fdiv(A.gm1 * wown[NV - 1], wown[0]));
           T s = (fabs(wown[1]) + cs) * iwx;
           if constexpr (HAS_Y) s = fmax(s, (fabs(wown[2]) + cs) * iwy);
           if constexpr (MARCH) s = fmax(s, (fabs(wown[1 + AM]) + cs) * iwm);
-          speed_max = fmax(speed_max, (double)s);
+          speed_max = fmax(speed_max, s);
           if (A.want_totals) {
             const double dm = MARCH ? A.wd[AM][m] : 1.0;
+            const T dm_hi = (T)dm, dm_lo = (T)(dm - (double)dm_hi);
 #pragma unroll
-            for (int v = 0; v < NV; ++v) tcol[v] = fma((double)__ldg(A.un + v * vs + c), dm, tcol[v]);
+            for (int v = 0; v < NV; ++v) tcol[v].add_product(__ldg(A.un + v * vs + c), dm_hi, dm_lo);
           }
         } else {
           const T hdt = T(0.5) * dt;
@@ -323,8 +323,9 @@ struct StageKernel {
       double area = A.wd[0][ca];
       if constexpr (HAS_Y) area *= A.wd[1][cb];
 #pragma unroll
-      for (int v = 0; v < NV; ++v) tot[v] = fma(tcol[v], area, tot[v]);
+      for (int v = 0; v < NV; ++v) tot[v] = fma(tcol[v].value(), area, tot[v]);
     }
+    speed_out = fmax(speed_out, (double)speed_max);
   }
 
   // Fixed-order block reduction of (max speed, totals) into per-CTA partials.
@@ -366,8 +367,9 @@ struct StageKernel {
   }
 };
 
-template <int NDIM, class T, int SOLVER, int STAGE, int TX, int TY>
-__global__ void __launch_bounds__(TX * TY) hydro_stage_kernel(const StageArgs<T> A) {
+// MINB: CTAs per SM the register allocation must allow (__launch_bounds__).
+template <int NDIM, class T, int SOLVER, int STAGE, int TX, int TY, int MINB>
+__global__ void __launch_bounds__(TX * TY, MINB) hydro_stage_kernel(const StageArgs<T> A) {
   StageKernel<NDIM, T, SOLVER, STAGE, TX, TY>::run(A);
 }
 

@@ -22,6 +22,7 @@ OK, EINVAL, ENOMEM, ECUDA, ENONPHYS, ETIMEOUT = 0, -1, -2, -3, -4, -5
 HLL, HLLC = 0, 1
 BC_PERIODIC, BC_REFLECT, BC_OUTFLOW = 0, 1, 2
 FP64, FP32_MIXED = 0, 1
+OPT_STEP_TOTALS = 1
 
 
 class HydroError(RuntimeError):
@@ -66,6 +67,8 @@ SIGNATURES = {
     "genasis_hydro_autotune": [_P, _I, ctypes.c_char_p],
     "genasis_hydro_launches_per_step": [_P],
     "genasis_hydro_profile_step": [_P, _D, _P],
+    "genasis_hydro_set_option": [_P, _I, _I],
+    "genasis_hydro_get_step_totals": [_P, _P],
     "genasis_batch_create": [_I, _P, _I, _D, _I, _P, ctypes.POINTER(_P)],
     "genasis_batch_destroy": [_P],
     "genasis_batch_set_primitive": [_P, _I, _P, _P, _P],
@@ -223,6 +226,15 @@ class Hydro:
         check(load().genasis_hydro_get_totals(self._h, out.ctypes.data))
         return out[: self.nvar]
 
+    def step_totals(self):
+        """Totals of U^n folded into the last step (GENASIS_OPT_STEP_TOTALS)."""
+        out = np.zeros(5)
+        check(load().genasis_hydro_get_step_totals(self._h, out.ctypes.data))
+        return out[: self.nvar]
+
+    def set_step_totals(self, enabled):
+        check(load().genasis_hydro_set_option(self._h, OPT_STEP_TOTALS, int(bool(enabled))))
+
     def status(self):
         return check(load().genasis_hydro_status(self._h))
 
@@ -368,3 +380,4 @@ class Batch:
             self.close()
         except Exception:
             pass
+

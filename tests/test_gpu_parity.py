@@ -101,14 +101,19 @@ def test_kelvin_helmholtz_reduced():
         _check(Ug, Uo, 2, tol, f"kh prec={precision}")
 
 
-@pytest.mark.parametrize("tile", [0, 1, 2])
-def test_every_tile_shape_identical(tile):
+@pytest.mark.parametrize("ndim,precision", [(3, H.FP32_MIXED), (3, H.FP64), (2, H.FP32_MIXED), (1, H.FP32_MIXED)])
+def test_every_tile_shape_identical(ndim, precision):
     """Each compiled tile shape and plane count gives bitwise the same state."""
-    pr = P.random_blocks(3, (70, 34, 41), seed=3, bc=P.REFLECT)
-    ref, _ = gpu_run(pr, H.FP32_MIXED, steps=4, tile=0, kchunk=0)
-    for kc in (0, 7, 41):
-        U, _ = gpu_run(pr, H.FP32_MIXED, steps=4, tile=tile, kchunk=kc)
-        np.testing.assert_array_equal(U, ref)
+    shape = {3: (70, 34, 41), 2: (150, 97), 1: (700,)}[ndim]
+    pr = P.random_blocks(ndim, shape, seed=3, bc=P.REFLECT)
+    ref, _ = gpu_run(pr, precision, steps=4, tile=0, kchunk=0)
+    h = H.Hydro.from_problem(pr, precision=precision)
+    count = h.tile_info()["tile_count"]
+    h.close()
+    for tile in range(count):
+        for kc in ((0, 7, shape[-1]) if ndim > 1 else (0,)):
+            U, _ = gpu_run(pr, precision, steps=4, tile=tile, kchunk=kc)
+            np.testing.assert_array_equal(U, ref, err_msg=f"tile {tile} kchunk {kc}")
 
 
 def test_fixed_dt_step_matches_oracle():
