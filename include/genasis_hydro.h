@@ -171,6 +171,31 @@ int genasis_hydro_profile_step(genasis_hydro_t h, double cfl, float *ms);
 /* Text of the last error of the calling thread (never NULL). */
 const char *genasis_hydro_last_error(void);
 
+/* One RK2 step with a caller-given dt, like genasis_hydro_step, for callers
+ * that cannot allocate device memory: code whose device memory belongs to a
+ * pooling allocator that has already reserved it (a cudaMalloc there fails or
+ * fragments the pool), and latency-critical loops that must not allocate after
+ * initialisation.  The paper has no counterpart: this is an interface choice.
+ *   desc   mesh and solver as for genasis_hydro_create (widths are host
+ *          pointers); desc->stream is the stream to run on (NULL = the legacy
+ *          default stream).
+ *   U_in   device pointer, conserved state U^n in desc->precision
+ *          ((ndim + 2) * ncell values, layout as above); not modified.
+ *   U_out  device pointer receiving U^{n+1}; must not overlap U_in.
+ * No handle is needed and nothing is allocated (no cudaMalloc, cudaFree or
+ * allocating library call): the stage buffer, reduction partials, device
+ * scalars and geometry tables live in one static 32 MiB device array that
+ * every GPU loading the library holds until the process exits.  Limits: at
+ * most 4096 cells per axis, (ndim + 2) * ncell * sizeof(element) at most about
+ * 31 MiB (for example 1.5 M cells in 3D FP32, 0.78 M in 3D FP64), at most
+ * 4096 CTAs per stage; larger sizes return GENASIS_EINVAL with a message.
+ * The first call on a device looks up the device address of the static array
+ * (cudaGetSymbolAddress) with that device current, so make the first call
+ * before any stream capture.  All calls share the array and it keeps the last
+ * call's contents: calls that overlap on the GPU (other streams, other host
+ * threads) race on it.  Synchronises the stream; returns GENASIS_ENONPHYS if
+ * the step met a non-physical state. */
+int genasis_hydro_step_noalloc(const genasis_hydro_desc *desc, const void *U_in, void *U_out, double dt);
 
 /* ---------------------------------------------------------------------------
  * Batches: many independent 1D and 2D problems of uneven size advanced

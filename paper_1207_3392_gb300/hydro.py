@@ -69,6 +69,7 @@ SIGNATURES = {
     "genasis_hydro_profile_step": [_P, _D, _P],
     "genasis_hydro_set_option": [_P, _I, _I],
     "genasis_hydro_get_step_totals": [_P, _P],
+    "genasis_hydro_step_noalloc": [ctypes.POINTER(Desc), _P, _P, _D],
     "genasis_batch_create": [_I, _P, _I, _D, _I, _P, ctypes.POINTER(_P)],
     "genasis_batch_destroy": [_P],
     "genasis_batch_set_primitive": [_P, _I, _P, _P, _P],
@@ -381,3 +382,28 @@ class Batch:
         except Exception:
             pass
 
+
+def step_noalloc(prob, U_in, U_out, dt, precision=FP64, solver=None, stream=None):
+    """One RK2 step through genasis_hydro_step_noalloc, which allocates no
+    device memory (for callers whose device memory is owned by a pooling
+    allocator, or that must not allocate after initialisation).  U_in and
+    U_out are CUDA tensors of the conserved state in `precision`; prob gives
+    the mesh (ndim, n, widths, bc_lo, bc_hi, gamma, theta, solver)."""
+    d = Desc()
+    d.ndim = int(prob.ndim)
+    widths = [np.ascontiguousarray(prob.widths[q], dtype=np.float64) for q in range(prob.ndim)]
+    for q in range(3):
+        d.n[q] = int(prob.n[q]) if q < prob.ndim else 1
+        d.widths[q] = widths[q].ctypes.data if q < prob.ndim else None
+        d.bc_lo[q] = int(prob.bc_lo[q]) if q < prob.ndim else 0
+        d.bc_hi[q] = int(prob.bc_hi[q]) if q < prob.ndim else 0
+    d.gamma = float(prob.gamma)
+    d.solver = int(prob.solver if solver is None else solver)
+    d.theta = float(prob.theta)
+    d.precision = int(precision)
+    if stream is not None:
+        d.stream = stream if isinstance(stream, int) else int(getattr(stream, "cuda_stream", stream))
+    dt_ = np.float64 if precision == FP64 else np.float32
+    pin, a = _ptr(U_in, dt_, None, "U_in")
+    pout, b = _ptr(U_out, dt_, None, "U_out")
+    check(load().genasis_hydro_step_noalloc(ctypes.byref(d), pin, pout, float(dt)))
