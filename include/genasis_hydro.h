@@ -171,6 +171,96 @@ int genasis_hydro_profile_step(genasis_hydro_t h, double cfl, float *ms);
 /* Text of the last error of the calling thread (never NULL). */
 const char *genasis_hydro_last_error(void);
 
+/* ---------------------------------------------------------------------------
+ * Learned flux correction (2D).  Not in the paper: the benchmark adds to the
+ * face flux of Sec. 3.2 (HLL or HLLC) a correction predicted by a small network
+ * from the six-cell primitive stencil across each face:
+ *   features (24): for cells i-3 .. i+2 along the face normal, rho/rho_bar - 1,
+ *     v_n/c_bar, v_t/c_bar, p/p_bar - 1 (rho_bar, p_bar: stencil means,
+ *     c_bar = sqrt(gamma p_bar / rho_bar), v_n / v_t: normal / transverse
+ *     velocity);
+ *   network: 24 -> 64 -> 64 -> 4, SiLU activations, BF16 weights and
+ *     activations, FP32 accumulation (tensor cores);
+ *   correction: output k times the flux scale (rho_bar c_bar, rho_bar c_bar^2,
+ *     rho_bar c_bar^2, rho_bar c_bar^3) for (mass, normal momentum, transverse
+ *     momentum, energy), added to the face flux, so the update stays in
+ *     conservation form (every face flux is shared by its two cells);
+ *   limiter: flux-corrected transport keeps every conserved variable within
+ *     local bounds of the plain update (genasis_learned_set_fct);
+ *   fallback: after each RK stage, a cell whose corrected update has rho <= 0
+ *     or p <= 0 makes every face it touches use the plain flux, and the cells
+ *     around it are recomputed (one a-posteriori pass).
+ * Parameters are one FP32 vector of genasis_mlp_param_count() values:
+ * W1 [64][24], b1 [64], W2 [64][64], b2 [64], W3 [4][64], b3 [4].
+ * ------------------------------------------------------------------------- */
+typedef struct genasis_learned *genasis_learned_t;
+typedef struct genasis_mlp_opt *genasis_mlp_opt_t;
+
+/* Number of network parameters (6020). */
+int genasis_mlp_param_count(void);
+
+/* Corrected 2D solver: desc as for genasis_hydro_create with ndim = 2,
+ * precision GENASIS_FP32_MIXED, n[q] >= 6.  Without parameters (or after
+ * set_params(NULL)) it runs the plain scheme. */
+int genasis_learned_create(const genasis_hydro_desc *desc, genasis_learned_t *out);
+int genasis_learned_destroy(genasis_learned_t l);
+/* params: host or device pointer to the FP32 parameter vector, copied. */
+int genasis_learned_set_params(genasis_learned_t l, const float *params);
+/* Flux-corrected transport (Zalesak 1979) on the correction, on by default:
+ * the plain flux is the low-order flux and the correction the antidiffusive
+ * flux; each face's correction is scaled by C in [0, 1] so that no conserved
+ * variable of a cell leaves the range, over the cell and its face neighbours,
+ * of the plain-flux update and of the stage input (enabled = 1 or 0). */
+int genasis_learned_set_fct(genasis_learned_t l, int enabled);
+/* Bound on the network outputs (face frame, before scaling): each output is
+ * clamped to [-ylim, ylim]; INFINITY (the default) means no bound. */
+int genasis_learned_set_limit(genasis_learned_t l, float ylim);
+/* State in FP32 conserved form (4 planes) or from FP64 primitives, host or
+ * device; get_conserved synchronises. */
+int genasis_learned_set_primitive(genasis_learned_t l, const double *rho, const double *vel, const double *p);
+int genasis_learned_set_conserved(genasis_learned_t l, const float *U);
+int genasis_learned_get_conserved(genasis_learned_t l, float *U);
+/* nsteps RK2 steps with the device CFL step (as genasis_hydro_advance). */
+int genasis_learned_advance(genasis_learned_t l, int nsteps, double cfl, double t_end, double *t_out);
+/* One corrected TVD RK2 step with the given dt (> 0, no CFL check), enqueued
+ * on the handle's stream without synchronising. */
+int genasis_learned_step(genasis_learned_t l, double dt);
+/* Cells whose corrected update fell back to the plain flux, cumulative. */
+int genasis_learned_fallbacks(genasis_learned_t l, long long *cells);
+/* Training support on a periodic mesh, device pointers, compact face order
+ * f = (axis * ny + j) * nx + i (face (i, j) of axis 0 lies between cells
+ * (i-1, j) and (i, j)):
+ *   features: X [2 nx ny][32] BF16 (24 features + zeros), scale [2 nx ny][4];
+ *   targets:  T [2 nx ny][4] = face-frame (f_target - f_plain) / scale, with
+ *             f_target, f_plain [2][4][ny][nx] FP64 in conserved order. */
+int genasis_learned_features(genasis_learned_t l, void *X, float *scale);
+int genasis_learned_targets(genasis_learned_t l, const double *f_target, const double *f_plain, const float *scale,
+                            float *T);
+
+/* Add weight * (F(U^n) + F(U^n + dt K)) / 2 of the step just taken (the
+ * effective RK2 face flux), averaged over the `stride` fine faces of each
+ * coarse face, to F [2][4][ny/stride][nx/stride] (FP64, device).  2D
+ * GENASIS_FP32_MIXED handles only; call right after a step. */
+int genasis_hydro_accumulate_face_flux(genasis_hydro_t h, int stride, double weight, double *F);
+/* Conservative restriction of a uniform 2D FP32 state by `factor` into
+ * U_coarse [4][ny/factor][nx/factor] (device); synchronises. */
+int genasis_hydro_restrict(genasis_hydro_t h, int factor, float *U_coarse);
+
+/* Network on tensor cores (device pointers; stream may be NULL):
+ *   forward:  Y [n][4] from X [n][32] BF16;
+ *   gradient: grad [param_count] of mean((y - T)^2) over n samples x 4
+ *             outputs, and optionally the sum of squared errors (*loss). */
+int genasis_mlp_forward(const float *params, const void *X, long long n, float *Y, void *stream);
+int genasis_mlp_gradient(const float *params, const void *X, const float *T, long long n, float *grad, float *loss,
+                         void *stream);
+/* Adam (beta 0.9 / 0.999, eps 1e-8) on a device copy of the parameters. */
+int genasis_mlp_opt_create(const float *params, void *stream, genasis_mlp_opt_t *out);
+int genasis_mlp_opt_destroy(genasis_mlp_opt_t o);
+/* One gradient step on the batch (X, T device pointers); *loss_out (host, may
+ * be NULL) receives the batch mean squared error before the step. */
+int genasis_mlp_opt_step(genasis_mlp_opt_t o, const void *X, const float *T, long long n, float lr, float *loss_out);
+int genasis_mlp_opt_get_params(genasis_mlp_opt_t o, float *params);
+
 /* One RK2 step with a caller-given dt, like genasis_hydro_step, for callers
  * that cannot allocate device memory: code whose device memory belongs to a
  * pooling allocator that has already reserved it (a cudaMalloc there fails or

@@ -59,7 +59,8 @@ def _load():
                            ("og_evolve", [D, P, ctypes.c_double, ctypes.c_double, ctypes.c_int, P, P]),
                            ("og_prim_to_cons", [D, P, P, P, P]), ("og_cons_to_prim", [D, P, P, P, P]),
                            ("og_riemann_flux", [ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, P, P, P, P]),
-                           ("og_physical_flux", [ctypes.c_double, ctypes.c_int, ctypes.c_int, P, P])]:
+                           ("og_physical_flux", [ctypes.c_double, ctypes.c_int, ctypes.c_int, P, P]),
+                           ("og_face_fluxes_2d", [D, P, P, P])]:
             f = getattr(lib, name)
             f.argtypes = args
             f.restype = ctypes.c_int
@@ -209,6 +210,17 @@ def physical_flux(gamma, ndim, axis, prim):
     F = np.zeros(5)
     _check(lib.og_physical_flux(float(gamma), int(ndim), int(axis), pa, F.ctypes.data), "physical_flux")
     return F[: ndim + 2]
+
+
+def face_fluxes_2d(g: Grid, U):
+    """Plain face fluxes of a 2D state: Fx [4][ny][nx+1], Fy [4][ny+1][nx]."""
+    lib = _load()
+    U, pu = _arr(U)
+    ny, nx = g.shape
+    Fx = np.empty((4, ny, nx + 1))
+    Fy = np.empty((4, ny + 1, nx))
+    _check(lib.og_face_fluxes_2d(g._ptr(), pu, Fx.ctypes.data, Fy.ctypes.data), "face_fluxes_2d")
+    return Fx, Fy
 
 
 def minmod(a, b, c):

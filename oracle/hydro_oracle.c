@@ -532,5 +532,71 @@ int og_physical_flux(double gamma, int nd, int q, const double *prim, double *F)
   return OG_OK;
 }
 
+/* Plain face fluxes of a 2D state (the fluxes og_rhs differences), for the
+ * learned-correction reference: Fx [nv][ny][nx+1] (face i between cells i-1
+ * and i of row j), Fy [nv][ny+1][nx].  Same ghost filling, recovery,
+ * reconstruction and Riemann solver as og_rhs_grid. */
+int og_face_fluxes_2d(const og_desc *d, const double *U, double *Fx, double *Fy) {
+  if (d->ndim != 2) return OG_EINVAL;
+  og_grid G;
+  int rc = og_grid_init(&G, d);
+  if (rc != OG_OK) { og_grid_free(&G); return rc; }
+  int nv = G.nvar;
+  size_t ne = G.next, nin = (size_t)G.n[0] * G.n[1];
+  double *Ue = (double *)malloc(sizeof(double) * nv * ne);
+  double *We = (double *)malloc(sizeof(double) * nv * ne);
+  double *Win = (double *)malloc(sizeof(double) * nv * ne);
+  double *Wout = (double *)malloc(sizeof(double) * nv * ne);
+  if (!Ue || !We || !Win || !Wout) { rc = OG_ENOMEM; goto out; }
+  for (size_t t = 0; t < nv * ne; ++t) Ue[t] = NAN;
+  for (int j = 0; j < G.n[1]; ++j)
+    for (int i = 0; i < G.n[0]; ++i)
+      for (int v = 0; v < nv; ++v) Ue[(size_t)v * ne + og_at(&G, i, j, 0)] = U[(size_t)v * nin + (size_t)j * G.n[0] + i];
+  og_fill_ghosts(&G, d, Ue);
+  for (size_t t = 0; t < ne; ++t) {
+    double u[5] = {0, 0, 0, 0, 0}, w[5];
+    for (int v = 0; v < nv; ++v) u[v] = Ue[(size_t)v * ne + t];
+    og_prim_from_cons(2, u, w);
+    for (int v = 0; v < nv; ++v) We[(size_t)v * ne + t] = w[v];
+  }
+  for (int q = 0; q < 2; ++q) {
+    const double *wq = G.w[q];
+    int lo[2] = {0, 0}, hi[2] = {G.n[0], G.n[1]};
+    lo[q] = -1; hi[q] = G.n[q] + 1;
+    for (int j = lo[1]; j < hi[1]; ++j)
+      for (int i = lo[0]; i < hi[0]; ++i) {
+        int c[2] = {i, j}, cm[2] = {i, j}, cp[2] = {i, j};
+        cm[q] -= 1; cp[q] += 1;
+        size_t tc = og_at(&G, i, j, 0), tm = og_at(&G, cm[0], cm[1], 0), tp = og_at(&G, cp[0], cp[1], 0);
+        double dm = wq[c[q] - 1 + OG_NG], dc = wq[c[q] + OG_NG], dp = wq[c[q] + 1 + OG_NG];
+        double dist_cm = 0.5 * (dm + dc), dist_pm = 0.5 * dm + dc + 0.5 * dp, dist_pc = 0.5 * (dc + dp);
+        for (int v = 0; v < nv; ++v) {
+          double Wc = We[(size_t)v * ne + tc], Wm = We[(size_t)v * ne + tm], Wp = We[(size_t)v * ne + tp];
+          double D = og_minmod3(d->theta * ((Wc - Wm) / dist_cm), (Wp - Wm) / dist_pm, d->theta * ((Wp - Wc) / dist_pc));
+          Win[(size_t)v * ne + tc] = Wc - D * (0.5 * dc);
+          Wout[(size_t)v * ne + tc] = Wc + D * (0.5 * dc);
+        }
+      }
+    int nfx = q == 0 ? G.n[0] + 1 : G.n[0], nfy = q == 0 ? G.n[1] : G.n[1] + 1;
+    double *Fo = q == 0 ? Fx : Fy;
+    for (int j = 0; j < nfy; ++j)
+      for (int i = 0; i < nfx; ++i) {
+        int cr[2] = {i, j}, cl[2] = {i, j};
+        cl[q] -= 1;
+        double WL[5], WR[5], F[5];
+        for (int v = 0; v < nv; ++v) {
+          WL[v] = Wout[(size_t)v * ne + og_at(&G, cl[0], cl[1], 0)];
+          WR[v] = Win[(size_t)v * ne + og_at(&G, cr[0], cr[1], 0)];
+        }
+        og_face_flux(d->solver, d->gamma, 2, q, WL, WR, F, NULL);
+        for (int v = 0; v < nv; ++v) Fo[((size_t)v * nfy + j) * nfx + i] = F[v];
+      }
+  }
+out:
+  free(Ue); free(We); free(Win); free(Wout);
+  og_grid_free(&G);
+  return rc;
+}
+
 /* Exposed for the limiter unit test. */
 double og_minmod(double a, double b, double c) { return og_minmod3(a, b, c); }

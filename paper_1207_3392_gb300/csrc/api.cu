@@ -14,7 +14,9 @@
 
 #include "genasis_hydro.h"
 #include "common.h"
+#include "geometry.h"
 #include "aux_kernels.h"
+#include "learned_internal.h"
 #include "hydro_device.cuh"
 #include "registry.h"
 #include "stage_kernel.cuh"
@@ -68,6 +70,7 @@ struct genasis_hydro {
   void* geo[3] = {nullptr, nullptr, nullptr};
   void* iw[3] = {nullptr, nullptr, nullptr};
   double* wd[3] = {nullptr, nullptr, nullptr};
+  float* wpair[3] = {nullptr, nullptr, nullptr};  // FP32 state: widths as hi[n] then lo[n]
   double* part_speed = nullptr;
   double* part_tot = nullptr;
   size_t part_cap = 0;  // blocks the partial buffers hold
@@ -115,37 +118,6 @@ int validate(const genasis_hydro_desc* d) {
   return GENASIS_OK;
 }
 
-// Widths including two ghost cells on each side, by the boundary rule.
-std::vector<double> extended_widths(const double* w, int n, int lo, int hi) {
-  std::vector<double> e(n + 4);
-  for (int c = -2; c < n + 2; ++c) {
-    int s = c;
-    if (c < 0) s = lo == GENASIS_BC_PERIODIC ? c + n : lo == GENASIS_BC_REFLECT ? -1 - c : 0;
-    else if (c >= n) s = hi == GENASIS_BC_PERIODIC ? c - n : hi == GENASIS_BC_REFLECT ? 2 * n - 1 - c : n - 1;
-    e[c + 2] = w[s];
-  }
-  return e;
-}
-
-// Reconstruction geometry (Eq. MinMod with centre distances of a non-uniform
-// Cartesian mesh): q_c - q_- = (d_{c-1} + d_c)/2, q_+ - q_- = d_{c-1}/2 + d_c +
-// d_{c+1}/2, q_+ - q_c = (d_c + d_{c+1})/2, face offset d_c / 2.
-template <class T>
-void build_geometry(const std::vector<double>& e, std::vector<Geo<T>>& geo, std::vector<T>& iw) {
-  const int m = (int)e.size();
-  geo.resize(m);
-  iw.resize(m);
-  for (int k = 0; k < m; ++k) {
-    const double dc = e[k];
-    const double dm = e[k > 0 ? k - 1 : 0], dp = e[k + 1 < m ? k + 1 : m - 1];
-    geo[k].icm = (T)(1.0 / (0.5 * (dm + dc)));
-    geo[k].ipm = (T)(1.0 / (0.5 * dm + dc + 0.5 * dp));
-    geo[k].ipc = (T)(1.0 / (0.5 * (dc + dp)));
-    geo[k].h = (T)(0.5 * dc);
-    iw[k] = (T)(1.0 / dc);
-  }
-}
-
 template <class T>
 int upload_geometry(genasis_hydro* h, const genasis_hydro_desc* d) {
   for (int q = 0; q < 3; ++q) {
@@ -156,13 +128,23 @@ int upload_geometry(genasis_hydro* h, const genasis_hydro_desc* d) {
     std::vector<double> e = extended_widths(w.data(), n < 2 ? 2 : n, h->bc_lo[q], h->bc_hi[q]);
     std::vector<Geo<T>> geo;
     std::vector<T> iw;
-    build_geometry<T>(e, geo, iw);
+    append_geometry<T>(e, geo, iw);
     GH_CK(cudaMalloc(&h->geo[q], geo.size() * sizeof(Geo<T>)));
     GH_CK(cudaMalloc(&h->iw[q], iw.size() * sizeof(T)));
     GH_CK(cudaMalloc(&h->wd[q], w.size() * sizeof(double)));
     GH_CK(cudaMemcpy(h->geo[q], geo.data(), geo.size() * sizeof(Geo<T>), cudaMemcpyHostToDevice));
     GH_CK(cudaMemcpy(h->iw[q], iw.data(), iw.size() * sizeof(T), cudaMemcpyHostToDevice));
     GH_CK(cudaMemcpy(h->wd[q], w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice));
+    if (sizeof(T) == 4) {
+      // each FP64 width as a float pair hi + lo (for the compensated column sums)
+      std::vector<float> pair(2 * w.size());
+      for (size_t i = 0; i < w.size(); ++i) {
+        pair[i] = (float)w[i];
+        pair[w.size() + i] = (float)(w[i] - (double)pair[i]);
+      }
+      GH_CK(cudaMalloc(&h->wpair[q], pair.size() * sizeof(float)));
+      GH_CK(cudaMemcpy(h->wpair[q], pair.data(), pair.size() * sizeof(float), cudaMemcpyHostToDevice));
+    }
   }
   return GENASIS_OK;
 }
@@ -233,6 +215,14 @@ StageArgs<T> stage_args(genasis_hydro* h, int stage) {
     A.geo[q] = (const Geo<T>*)h->geo[q];
     A.iw[q] = (const T*)h->iw[q];
     A.wd[q] = h->wd[q];
+    if (sizeof(T) == 4) {
+      const size_t nq = q < h->ndim ? (size_t)h->n[q] : 2;
+      A.wdh[q] = (const T*)h->wpair[q];
+      A.wdl[q] = (const T*)(h->wpair[q] + nq);
+    } else {
+      A.wdh[q] = (const T*)h->wd[q];
+      A.wdl[q] = (const T*)h->wd[q];
+    }
   }
   A.gamma = (T)h->gamma;
   A.gm1 = (T)(h->gamma - 1.0);
@@ -371,6 +361,7 @@ int free_all(genasis_hydro* h) {
     cudaFree(h->geo[q]);
     cudaFree(h->iw[q]);
     cudaFree(h->wd[q]);
+    cudaFree(h->wpair[q]);
   }
   cudaFree(h->part_speed);
   cudaFree(h->part_tot);
@@ -651,6 +642,48 @@ int genasis_hydro_get_step_totals(genasis_hydro_t h, double* totals) {
   return sync_status(h);
 }
 
+static int mesh2_of(genasis_hydro* h, Mesh2* M) {
+  if (h->ndim != 2 || h->prec != GENASIS_FP32_MIXED)
+    return fail(GENASIS_EINVAL, "needs a 2D GENASIS_FP32_MIXED handle");
+  M->nx = h->n[0];
+  M->ny = h->n[1];
+  for (int q = 0; q < 2; ++q) {
+    M->bc_lo[q] = h->bc_lo[q];
+    M->bc_hi[q] = h->bc_hi[q];
+    M->geo[q] = (const Geo<float>*)h->geo[q];
+    M->iw[q] = (const float*)h->iw[q];
+  }
+  M->gamma = (float)h->gamma;
+  M->gm1 = (float)(h->gamma - 1.0);
+  M->theta = (float)h->theta;
+  return GENASIS_OK;
+}
+
+int genasis_hydro_accumulate_face_flux(genasis_hydro_t h, int stride, double weight, double* F) {
+  if (!h || !F) return fail(GENASIS_EINVAL, "NULL argument");
+  Mesh2 M;
+  int rc = mesh2_of(h, &M);
+  if (rc) return rc;
+  if (stride < 1 || M.nx % stride || M.ny % stride) return fail(GENASIS_EINVAL, "stride must divide nx and ny");
+  if (!is_device_ptr(F)) return fail(GENASIS_EINVAL, "F must be a device pointer");
+  // the last step read U^n from the other state buffer and left its K
+  GH_CK(launch_face_flux_accumulate(M, h->solver, (const float*)h->U[1 - h->cur], (const float*)h->K, h->scal + SCAL_DT,
+                                    stride, weight, F, h->stream));
+  return GENASIS_OK;
+}
+
+int genasis_hydro_restrict(genasis_hydro_t h, int factor, float* U_coarse) {
+  if (!h || !U_coarse) return fail(GENASIS_EINVAL, "NULL argument");
+  Mesh2 M;
+  int rc = mesh2_of(h, &M);
+  if (rc) return rc;
+  if (factor < 1 || M.nx % factor || M.ny % factor) return fail(GENASIS_EINVAL, "factor must divide nx and ny");
+  if (!is_device_ptr(U_coarse)) return fail(GENASIS_EINVAL, "U_coarse must be a device pointer");
+  GH_CK(launch_restrict(M.nx, M.ny, factor, (const float*)h->U[h->cur], U_coarse, h->stream));
+  GH_CK(cudaStreamSynchronize(h->stream));
+  return GENASIS_OK;
+}
+
 int genasis_hydro_launches_per_step(genasis_hydro_t h) {
   if (!h) return fail(GENASIS_EINVAL, "NULL handle");
   return 3;
@@ -718,7 +751,7 @@ int genasis_hydro_autotune(genasis_hydro_t h, int trial_steps, const char* cache
   for (int tile = 0; tile < tile_count(h->ndim) && !rc; ++tile) {
     std::vector<int> kcs = {0};
     if (h->ndim >= 2)
-      for (int kc : {16, 32, 64})
+      for (int kc : {12, 16, 24, 32, 48, 64})
         if (kc < nm) kcs.push_back(kc);
     for (int kc : kcs) {
       rc = configure(h, tile, kc);

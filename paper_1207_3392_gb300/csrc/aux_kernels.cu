@@ -104,25 +104,39 @@ __global__ void totals_kernel(ReduceArgs<T> A) {
   }
 }
 
-// One CTA: fold the per-CTA partials in a fixed order, then set dt and t.
+// One CTA of 256 threads: fold the per-CTA partials in a fixed order (strided
+// per-thread sums, then a fixed tree), then set dt and t.
 //   mode FIN_FIXED : dt = fixed_dt
 //   mode FIN_CFL   : dt = cfl / max speed            (Eq. courantTimeStep x C_CFL)
 //   mode FIN_REDUCE: only store dt_CFL and totals
 // With t_end > 0 the step is clamped so that t never passes t_end.
-__global__ void finalize_kernel(FinalizeArgs A) {
+__global__ void __launch_bounds__(256) finalize_kernel(FinalizeArgs A) {
   __shared__ double red[32];
+  __shared__ double tsum[5][256];
+  const int tid = threadIdx.x;
   double best = 0.0;
   if (A.part_speed)
-    for (int i = threadIdx.x; i < A.nblk; i += blockDim.x) best = fmax(best, A.part_speed[i]);
+    for (int i = tid; i < A.nblk; i += blockDim.x) best = fmax(best, A.part_speed[i]);
   best = warp_max(best);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = best;
-  __syncthreads();
-  if (A.part_tot && threadIdx.x < A.nv) {
-    double s = 0.0;
-    for (int i = 0; i < A.nblk; ++i) s += A.part_tot[(size_t)i * A.nv + threadIdx.x];
-    A.scal[SCAL_TOT + threadIdx.x] = s;
+  if ((tid & 31) == 0) red[tid >> 5] = best;
+  if (A.part_tot) {
+    // thread t sums partials t, t + 256, ... in order; then a fixed tree
+    for (int v = 0; v < A.nv; ++v) {
+      double s = 0.0;
+      for (int i = tid; i < A.nblk; i += blockDim.x) s += A.part_tot[(size_t)i * A.nv + v];
+      tsum[v][tid] = s;
+    }
   }
-  if (threadIdx.x == 0) {
+  __syncthreads();
+  if (A.part_tot) {
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+      if (tid < w)
+        for (int v = 0; v < A.nv; ++v) tsum[v][tid] += tsum[v][tid + w];
+      __syncthreads();
+    }
+    if (tid < A.nv) A.scal[SCAL_TOT + tid] = tsum[tid][0];
+  }
+  if (tid == 0) {
     double m = red[0];
     for (int i = 1; i < (int)(blockDim.x >> 5); ++i) m = fmax(m, red[i]);
     if (A.part_speed) A.scal[SCAL_DTCFL] = 1.0 / m;

@@ -15,6 +15,7 @@
 #include "batch_registry.h"
 #include "common.h"
 #include "genasis_hydro.h"
+#include "geometry.h"
 
 namespace gh {
 
@@ -89,29 +90,6 @@ struct genasis_batch {
 namespace {
 
 template <class T>
-void geometry_tables(const double* w, int n, int lo, int hi, std::vector<Geo<T>>& geo, std::vector<T>& iw) {
-  // widths with two ghosts each side by the boundary rule; reconstruction
-  // distances of Eq. MinMod on a non-uniform Cartesian mesh
-  std::vector<double> e(n + 4);
-  for (int c = -2; c < n + 2; ++c) {
-    int s = c;
-    if (c < 0) s = lo == GENASIS_BC_PERIODIC ? c + n : lo == GENASIS_BC_REFLECT ? -1 - c : 0;
-    else if (c >= n) s = hi == GENASIS_BC_PERIODIC ? c - n : hi == GENASIS_BC_REFLECT ? 2 * n - 1 - c : n - 1;
-    e[c + 2] = w[s];
-  }
-  for (int k = 0; k < n + 4; ++k) {
-    const double dc = e[k], dm = e[k > 0 ? k - 1 : 0], dp = e[k + 1 < n + 4 ? k + 1 : n + 3];
-    Geo<T> g;
-    g.icm = (T)(1.0 / (0.5 * (dm + dc)));
-    g.ipm = (T)(1.0 / (0.5 * dm + dc + 0.5 * dp));
-    g.ipc = (T)(1.0 / (0.5 * (dc + dp)));
-    g.h = (T)(0.5 * dc);
-    geo.push_back(g);
-    iw.push_back((T)(1.0 / dc));
-  }
-}
-
-template <class T>
 int upload_tables(genasis_batch* b, const genasis_batch_problem* probs) {
   std::vector<Geo<T>> geo;
   std::vector<T> iw;
@@ -135,7 +113,7 @@ int upload_tables(genasis_batch* b, const genasis_batch_problem* probs) {
       d.goff[q] = h.goff[q];
       d.woff[q] = h.woff[q];
       if (q < h.ndim) {
-        geometry_tables<T>(probs[p].widths[q], h.n[q], h.bc_lo[q], h.bc_hi[q], geo, iw);
+        append_geometry<T>(extended_widths(probs[p].widths[q], h.n[q], h.bc_lo[q], h.bc_hi[q]), geo, iw);
         wd.insert(wd.end(), probs[p].widths[q], probs[p].widths[q] + h.n[q]);
       }
     }

@@ -68,6 +68,10 @@ struct BatchKernel {
     A.geo[2] = nullptr;
     A.iw[2] = nullptr;
     A.wd[2] = nullptr;
+    for (int q = 0; q < 3; ++q) {
+      A.wdh[q] = nullptr;
+      A.wdl[q] = nullptr;
+    }
     A.gamma = P.gamma;
     A.gm1 = P.gm1;
     A.theta = B.theta;

@@ -1,0 +1,1186 @@
+// learned.cu -- the learned flux correction (2D, FP32 state): the corrected
+// solver handle genasis_learned_*, the BF16 tensor-core MLP kernels
+// (inference, gradients, Adam) behind genasis_mlp_*, and the kernels that turn
+// fine runs into training targets.  The correction is the benchmark's
+// addition to the HLLC flux of Sec. 3.2; the paper has no counterpart.
+#include <cuda_runtime.h>
+
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
+#include "aux_kernels.h"
+#include "common.h"
+#include "genasis_hydro.h"
+#include "geometry.h"
+#include "learned_kernels.cuh"
+#include "learned_internal.h"
+
+namespace gh {
+
+// ============================================================== MLP kernels
+
+// Y[n][4] = net(X[n][32]); one warp per 16 samples, weights in shared memory.
+__global__ void __launch_bounds__(256) mlp_infer_kernel(const float* __restrict__ P, const __nv_bfloat16* __restrict__ X,
+                                                        long long n, float* __restrict__ Y) {
+  __shared__ mlp::Weights W;
+  mlp::load_weights(W, P);
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const long long ntile = (n + 15) / 16;
+  for (long long tile = (long long)blockIdx.x * 8 + warp; tile < ntile; tile += (long long)gridDim.x * 8) {
+    const long long s0 = tile * 16;
+    const int rows = (int)(n - s0 < 16 ? n - s0 : 16);
+    mlp::Forward F;
+    mlp::load_x(F, X + s0 * mlp::KIN, rows);
+    mlp::forward(F, W);
+    if (t < 2) {
+      if (g < rows) {
+        Y[(s0 + g) * 4 + 2 * t] = F.y[0];
+        Y[(s0 + g) * 4 + 2 * t + 1] = F.y[1];
+      }
+      if (g + 8 < rows) {
+        Y[(s0 + g + 8) * 4 + 2 * t] = F.y[2];
+        Y[(s0 + g + 8) * 4 + 2 * t + 1] = F.y[3];
+      }
+    }
+  }
+}
+
+constexpr int TS = 128;            // samples per CTA iteration in training (8 warps x 16)
+constexpr int TSP = TS + mlp::PAD;
+
+struct TrainSmem {
+  mlp::Weights W;
+  __nv_bfloat16 xt[mlp::KIN][TSP];   // X^T
+  __nv_bfloat16 h1t[mlp::NH][TSP];   // h1^T
+  __nv_bfloat16 h2t[mlp::NH][TSP];   // h2^T
+  __nv_bfloat16 d1t[mlp::NH][TSP];   // (dL/dz1)^T
+  __nv_bfloat16 d2t[mlp::NH][TSP];   // (dL/dz2)^T
+  __nv_bfloat16 dyt[16][TSP];        // (dL/dy)^T, rows >= 4 zero
+  float red[256];
+};
+
+// Scatter a 16 x 16 A fragment (rows = samples s0 + g / + 8, columns c0 + ...)
+// into a transposed [column][sample] array.
+__device__ __forceinline__ void store_afrag_t(__nv_bfloat16 (*dst)[TSP], const uint32_t (&a)[4], int c0, int s0) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const __nv_bfloat162* v = reinterpret_cast<const __nv_bfloat162*>(a);
+  dst[c0 + 2 * t][s0 + g] = v[0].x;
+  dst[c0 + 2 * t + 1][s0 + g] = v[0].y;
+  dst[c0 + 2 * t][s0 + g + 8] = v[1].x;
+  dst[c0 + 2 * t + 1][s0 + g + 8] = v[1].y;
+  dst[c0 + 2 * t + 8][s0 + g] = v[2].x;
+  dst[c0 + 2 * t + 9][s0 + g] = v[2].y;
+  dst[c0 + 2 * t + 8][s0 + g + 8] = v[3].x;
+  dst[c0 + 2 * t + 9][s0 + g + 8] = v[3].y;
+}
+
+// One accumulator tile (16 x 8) of A^T B where A^T rows come from `a` ([row][sample])
+// and B columns from `b` ([col][sample]), K = TS samples.
+__device__ __forceinline__ void grad_tile(float (&acc)[4], const __nv_bfloat16 (*a)[TSP], int r0,
+                                          const __nv_bfloat16 (*b)[TSP], int c0) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+#pragma unroll 4
+  for (int kk = 0; kk < TS / 16; ++kk) {
+    const int k = 16 * kk + 2 * t;
+    uint32_t af[4] = {mlp::ld32(&a[r0 + g][k]), mlp::ld32(&a[r0 + g + 8][k]), mlp::ld32(&a[r0 + g][k + 8]),
+                      mlp::ld32(&a[r0 + g + 8][k + 8])};
+    mlp::mma16816(acc, af, mlp::ld32(&b[c0 + g][k]), mlp::ld32(&b[c0 + g][k + 8]));
+  }
+}
+
+// Gradient of mean((y - T)^2) (over n samples x 4 outputs) with respect to the
+// parameters, summed per CTA into part[blockIdx.x][NPARAM]; loss sums into
+// part_loss[blockIdx.x].  Deterministic: fixed sample-to-CTA assignment.
+__global__ void __launch_bounds__(256) mlp_train_kernel(const float* __restrict__ P, const __nv_bfloat16* __restrict__ X,
+                                                        const float* __restrict__ T, long long n, float inv_count,
+                                                        float* __restrict__ part, float* __restrict__ part_loss) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TrainSmem& S = *reinterpret_cast<TrainSmem*>(smem_raw);
+  mlp::load_weights(S.W, P);
+  for (int i = threadIdx.x; i < 16 * TSP; i += blockDim.x) (&S.dyt[0][0])[i] = __float2bfloat16(0.0f);
+  __syncthreads();
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
+  float gw1[2][4] = {}, gw2[4][4] = {}, gw3[4] = {};
+  float gb = 0.0f, loss = 0.0f;
+  for (long long base = (long long)blockIdx.x * TS; base < n; base += (long long)gridDim.x * TS) {
+    const long long s0 = base + 16 * warp;
+    const int rows = (int)(n - s0 <= 0 ? 0 : (n - s0 < 16 ? n - s0 : 16));
+    mlp::Forward F;
+    mlp::load_x(F, X + s0 * mlp::KIN, rows);
+    mlp::forward(F, S.W);
+    // dL/dy
+    float dy[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int r = g + (e >= 2 ? 8 : 0), c = 2 * t + (e & 1);
+      float d = 0.0f;
+      if (c < mlp::NOUT && r < rows) {
+        const float diff = F.y[e] - T[(s0 + r) * 4 + c];
+        loss += diff * diff;
+        d = 2.0f * diff * inv_count;
+      }
+      dy[e] = d;
+    }
+    uint32_t dya[4] = {mlp::pack2(dy[0], dy[1]), mlp::pack2(dy[2], dy[3]), 0u, 0u};
+    // dL/dz2 = (dy W3) * silu'(z2)
+    float d2[8][4];
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
+      mlp::mma16816(acc, dya, mlp::ld32(&S.W.w3t[8 * nt + g][2 * t]), mlp::ld32(&S.W.w3t[8 * nt + g][2 * t + 8]));
+#pragma unroll
+      for (int e = 0; e < 4; ++e) d2[nt][e] = acc[e] * mlp::dsilu(F.z2[nt][e]);
+    }
+    uint32_t d2a[4][4];
+    mlp::to_afrag(d2, d2a, false);
+    // dL/dz1 = (dz2 W2) * silu'(z1)
+    float d1[8][4];
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int kc = 0; kc < 4; ++kc)
+        mlp::mma16816(acc, d2a[kc], mlp::ld32(&S.W.w2t[8 * nt + g][16 * kc + 2 * t]),
+                      mlp::ld32(&S.W.w2t[8 * nt + g][16 * kc + 2 * t + 8]));
+#pragma unroll
+      for (int e = 0; e < 4; ++e) d1[nt][e] = acc[e] * mlp::dsilu(F.z1[nt][e]);
+    }
+    uint32_t d1a[4][4];
+    mlp::to_afrag(d1, d1a, false);
+    // transposed copies for the weight-gradient products
+    const int sl = 16 * warp;
+    store_afrag_t(S.xt, F.xa[0], 0, sl);
+    store_afrag_t(S.xt, F.xa[1], 16, sl);
+#pragma unroll
+    for (int kc = 0; kc < 4; ++kc) {
+      store_afrag_t(S.h1t, F.h1a[kc], 16 * kc, sl);
+      store_afrag_t(S.h2t, F.h2a[kc], 16 * kc, sl);
+      store_afrag_t(S.d1t, d1a[kc], 16 * kc, sl);
+      store_afrag_t(S.d2t, d2a[kc], 16 * kc, sl);
+    }
+    {
+      const __nv_bfloat162* v = reinterpret_cast<const __nv_bfloat162*>(dya);
+      S.dyt[2 * t][sl + g] = v[0].x;
+      S.dyt[2 * t + 1][sl + g] = v[0].y;
+      S.dyt[2 * t][sl + g + 8] = v[1].x;
+      S.dyt[2 * t + 1][sl + g + 8] = v[1].y;
+    }
+    __syncthreads();
+    // weight gradients, K = TS samples: dW1 (4 x 4 tiles), dW2 (4 x 8), dW3 (1 x 8)
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const int tile = warp + 8 * i;
+      grad_tile(gw1[i], S.d1t, 16 * (tile / 4), S.xt, 8 * (tile % 4));
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int tile = 4 * warp + i;
+      grad_tile(gw2[i], S.d2t, 16 * (tile / 8), S.h1t, 8 * (tile % 8));
+    }
+    grad_tile(gw3, S.dyt, 0, S.h2t, 8 * warp);
+    // bias gradients: row sums of the transposed derivative tables
+    {
+      const __nv_bfloat16* row = tid < 64 ? S.d1t[tid] : tid < 128 ? S.d2t[tid - 64] : S.dyt[(tid - 128) & 15];
+      if (tid < 132) {
+        float s = 0.f;
+        for (int k = 0; k < TS; k += 2) {
+          const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162*>(row + k);
+          s += __bfloat162float(v.x) + __bfloat162float(v.y);
+        }
+        gb += s;
+      }
+    }
+    __syncthreads();
+  }
+  // write this CTA's partial gradient
+  float* G = part + (size_t)blockIdx.x * mlp::NPARAM;
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const int tile = warp + 8 * i, r0 = 16 * (tile / 4), c0 = 8 * (tile % 4);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int r = r0 + g + (e >= 2 ? 8 : 0), c = c0 + 2 * t + (e & 1);
+      if (c < mlp::NIN) G[mlp::OW1 + r * mlp::NIN + c] = gw1[i][e];
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int tile = 4 * warp + i, r0 = 16 * (tile / 8), c0 = 8 * (tile % 8);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int r = r0 + g + (e >= 2 ? 8 : 0), c = c0 + 2 * t + (e & 1);
+      G[mlp::OW2 + r * mlp::NH + c] = gw2[i][e];
+    }
+  }
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const int r = g + (e >= 2 ? 8 : 0), c = 8 * warp + 2 * t + (e & 1);
+    if (r < mlp::NOUT) G[mlp::OW3 + r * mlp::NH + c] = gw3[e];
+  }
+  if (tid < 64) G[mlp::OB1 + tid] = gb;
+  else if (tid < 128) G[mlp::OB2 + tid - 64] = gb;
+  else if (tid < 132) G[mlp::OB3 + tid - 128] = gb;
+  // loss: fixed-order block sum
+  S.red[tid] = loss;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (tid < w) S.red[tid] += S.red[tid + w];
+    __syncthreads();
+  }
+  if (tid == 0) part_loss[blockIdx.x] = S.red[0];
+}
+
+// Sum the per-CTA partials in order (gradient, loss); optionally one Adam step
+// on the FP32 parameters (Kingma & Ba, bias-corrected).
+__global__ void mlp_reduce_adam_kernel(const float* __restrict__ part, const float* __restrict__ part_loss, int nblk,
+                                       float* __restrict__ grad_out, float* __restrict__ loss_out, float* P, float* m,
+                                       float* v, int step, float lr, float b1, float b2, float eps) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p == 0 && loss_out) {
+    float s = 0.f;
+    for (int b = 0; b < nblk; ++b) s += part_loss[b];
+    *loss_out = s;
+  }
+  if (p >= mlp::NPARAM) return;
+  float g = 0.f;
+  for (int b = 0; b < nblk; ++b) g += part[(size_t)b * mlp::NPARAM + p];
+  if (grad_out) grad_out[p] = g;
+  if (step > 0) {
+    const float mm = b1 * m[p] + (1.f - b1) * g;
+    const float vv = b2 * v[p] + (1.f - b2) * g * g;
+    m[p] = mm;
+    v[p] = vv;
+    const float mh = mm / (1.f - powf(b1, (float)step));
+    const float vh = vv / (1.f - powf(b2, (float)step));
+    P[p] -= lr * mh / (sqrtf(vh) + eps);
+  }
+}
+
+// ====================================================== learned-solver kernels
+
+// Plain flux of every face (x faces (nx+1) x ny, then y faces nx x (ny+1)) of
+// the state un (+ dt k), and, if X is non-null, the MLP features and scales.
+template <int SOLVER>
+__global__ void lf_faces_kernel(Mesh2 M, const float* __restrict__ un, const float* __restrict__ k,
+                                const double* __restrict__ dtp, float* __restrict__ F, __nv_bfloat16* __restrict__ X,
+                                float* __restrict__ scale) {
+  const long long nxf = (long long)(M.nx + 1) * M.ny, nf = nxf + (long long)M.nx * (M.ny + 1);
+  const float dt = k ? (float)*dtp : 0.f;
+  for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < nf; f += (long long)gridDim.x * blockDim.x) {
+    float s[6][4], Fl[4];
+    if (f < nxf) {
+      const int i = (int)(f % (M.nx + 1)), j = (int)(f / (M.nx + 1));
+#pragma unroll
+      for (int c = 0; c < 6; ++c) cell_prim(M, un, k, dt, i - 3 + c, j, s[c]);
+      const float(&w)[4][4] = *reinterpret_cast<const float(*)[4][4]>(&s[1][0]);
+      plain_face_flux<0, SOLVER>(M, w, i - 1, Fl);
+      if (X) face_features<0>(M, s, X + f * mlp::KIN, scale + f * 4);
+    } else {
+      const long long gidx = f - nxf;
+      const int i = (int)(gidx % M.nx), j = (int)(gidx / M.nx);
+#pragma unroll
+      for (int c = 0; c < 6; ++c) cell_prim(M, un, k, dt, i, j - 3 + c, s[c]);
+      const float(&w)[4][4] = *reinterpret_cast<const float(*)[4][4]>(&s[1][0]);
+      plain_face_flux<1, SOLVER>(M, w, j - 1, Fl);
+      if (X) face_features<1>(M, s, X + f * mlp::KIN, scale + f * 4);
+    }
+#pragma unroll
+    for (int v = 0; v < 4; ++v) F[v * nf + f] = Fl[v];
+  }
+}
+
+struct UpdateArgs {
+  Mesh2 M;
+  const float* un;
+  const float* k1;      // stage 2: K of stage 1
+  const double* dtp;
+  const float* F;       // plain face fluxes [4][nf]
+  const float* dY;      // network outputs [nf][4], or null (no correction)
+  const float* scale;   // [nf][4]
+  float* out;                   // stage 1: K; stage 2: U^{n+1}
+  const unsigned char* flag;    // per cell: keeps the plain flux on all its faces (read)
+  unsigned char* flag_out;      // flags for the next pass (written)
+  unsigned long long* nfallback;
+  unsigned* status;
+  int stage;
+  int fixup;                    // 0: corrected pass; k > 0: k-th widening pass; -1: all-plain pass
+  int last;                     // last widening pass: remaining failures request the all-plain pass
+  unsigned* all_plain;          // device flag: redo the whole stage with plain fluxes
+  float ylim;                   // network outputs are clamped to [-ylim, ylim]
+  const float* R;               // FCT ratios [8][ncell] (R+ then R- per variable), or null
+};
+
+__device__ __forceinline__ bool cell_flagged(const UpdateArgs& A, int i, int j) {
+  const Mesh2& M = A.M;
+  if (i < 0 || i >= M.nx) {
+    if (M.bc_lo[0] != BC_PERIODIC) return false;
+    i = ((i % M.nx) + M.nx) % M.nx;
+  }
+  if (j < 0 || j >= M.ny) {
+    if (M.bc_lo[1] != BC_PERIODIC) return false;
+    j = ((j % M.ny) + M.ny) % M.ny;
+  }
+  return A.flag[(size_t)j * M.nx + i] != 0;
+}
+
+
+// Learned correction of face f in conserved order (network output clamped to
+// [-ylim, ylim], times the face's flux scale, rotated from the face frame).
+__device__ __forceinline__ void face_correction(const float* dY, const float* scale, float ylim, long long f, int axis,
+                                                float (&d)[4]) {
+  const float* yr = dY + f * 4;
+  const float* s = scale + f * 4;
+  float y[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) y[k] = fminf(fmaxf(yr[k], -ylim), ylim);
+  d[0] = s[0] * y[0];
+  d[1 + axis] = s[1] * y[1];
+  d[2 - axis] = s[2] * y[2];
+  d[3] = s[3] * y[3];
+}
+
+// Flux-corrected-transport factor of a face with correction d between cells
+// l and r (linear indices, -1 outside the mesh): the correction may raise a
+// cell by at most its R+ and lower it by at most its R-, for every variable.
+__device__ __forceinline__ float fct_factor(const float* R, size_t ncell, long long l, long long r, const float (&d)[4]) {
+  float C = 1.0f;
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const float rpr = r >= 0 ? R[v * ncell + r] : 1.f, rmr = r >= 0 ? R[(4 + v) * ncell + r] : 1.f;
+    const float rpl = l >= 0 ? R[v * ncell + l] : 1.f, rml = l >= 0 ? R[(4 + v) * ncell + l] : 1.f;
+    if (d[v] > 0.f) C = fminf(C, fminf(rpr, rml));
+    else if (d[v] < 0.f) C = fminf(C, fminf(rmr, rpl));
+  }
+  return C;
+}
+
+// Face flux: plain flux plus the (FCT-limited) learned correction, unless the
+// correction is off or, in a widening pass, either neighbour is flagged.
+__device__ __forceinline__ void face_total(const UpdateArgs& A, long long f, int axis, bool corr, long long nf,
+                                           long long lcell, long long rcell, float (&Fo)[4]) {
+#pragma unroll
+  for (int v = 0; v < 4; ++v) Fo[v] = A.F[v * nf + f];
+  if (!corr || !A.dY) return;
+  float d[4];
+  face_correction(A.dY, A.scale, A.ylim, f, axis, d);
+  const float C = A.R ? fct_factor(A.R, (size_t)A.M.nx * A.M.ny, lcell, rcell, d) : 1.0f;
+#pragma unroll
+  for (int v = 0; v < 4; ++v) Fo[v] = fmaf(C, d[v], Fo[v]);
+}
+
+// Neighbour cell index with periodic wrap, or -1 across a non-periodic wall.
+__device__ __forceinline__ long long neighbour(const Mesh2& M, int i, int j) {
+  if (i < 0 || i >= M.nx) {
+    if (M.bc_lo[0] != BC_PERIODIC) return -1;
+    i = ((i % M.nx) + M.nx) % M.nx;
+  }
+  if (j < 0 || j >= M.ny) {
+    if (M.bc_lo[1] != BC_PERIODIC) return -1;
+    j = ((j % M.ny) + M.ny) % M.ny;
+  }
+  return (long long)j * M.nx + i;
+}
+
+// Zalesak's ratios for the stage U_new = U_b - c dt div(F): with the low-order
+// update U_L = U_b - c dt div(F_plain), bounds over the cell and its face
+// neighbours of U_L and of the stage input, and P+/P- the sums of the
+// positive/negative correction contributions of the cell's faces,
+// R+ = min(1, (U_max - U_L)/P+), R- = min(1, (U_L - U_min)/P-).
+__global__ void lf_fct_kernel(UpdateArgs A, float* __restrict__ R) {
+  const Mesh2& M = A.M;
+  const long long ncell = (long long)M.nx * M.ny;
+  const long long nxf = (long long)(M.nx + 1) * M.ny, nf = nxf + (long long)M.nx * (M.ny + 1);
+  const float dt = (float)*A.dtp;
+  const float cdt = A.stage == 1 ? dt : 0.5f * dt;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell; c += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(c % M.nx), j = (int)(c / M.nx);
+    float umax[4], umin[4], UL[4];
+    const int di[5] = {0, -1, 1, 0, 0}, dj[5] = {0, 0, 0, -1, 1};
+    for (int k = 0; k < 5; ++k) {
+      const long long n = k == 0 ? c : neighbour(M, i + di[k], j + dj[k]);
+      if (n < 0) continue;
+      const int ni = (int)(n % M.nx), nj = (int)(n / M.nx);
+      const long long xl = (long long)nj * (M.nx + 1) + ni, yb = nxf + (long long)nj * M.nx + ni;
+      const float iwx = M.iw[0][ni + 2], iwy = M.iw[1][nj + 2];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const float u0 = A.un[v * ncell + n];
+        const float kk = A.stage == 2 ? A.k1[v * ncell + n] : 0.f;
+        const float ub = fmaf(A.stage == 2 ? 0.5f * dt : 0.f, kk, u0);
+        const float uin = fmaf(A.stage == 2 ? dt : 0.f, kk, u0);
+        const float div = (A.F[v * nf + xl + 1] - A.F[v * nf + xl]) * iwx + (A.F[v * nf + yb + M.nx] - A.F[v * nf + yb]) * iwy;
+        const float ul = fmaf(-cdt, div, ub);
+        if (k == 0) {
+          UL[v] = ul;
+          umax[v] = fmaxf(ul, uin);
+          umin[v] = fminf(ul, uin);
+        } else {
+          umax[v] = fmaxf(umax[v], fmaxf(ul, uin));
+          umin[v] = fminf(umin[v], fminf(ul, uin));
+        }
+      }
+    }
+    const long long xl = (long long)j * (M.nx + 1) + i, yb = nxf + (long long)j * M.nx + i;
+    const float iwx = M.iw[0][i + 2], iwy = M.iw[1][j + 2];
+    float dl[4], dr[4], db[4], dt4[4];
+    face_correction(A.dY, A.scale, A.ylim, xl, 0, dl);
+    face_correction(A.dY, A.scale, A.ylim, xl + 1, 0, dr);
+    face_correction(A.dY, A.scale, A.ylim, yb, 1, db);
+    face_correction(A.dY, A.scale, A.ylim, yb + M.nx, 1, dt4);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const float q[4] = {cdt * dl[v] * iwx, -cdt * dr[v] * iwx, cdt * db[v] * iwy, -cdt * dt4[v] * iwy};
+      float pp = 0.f, pm = 0.f;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        pp += fmaxf(q[k], 0.f);
+        pm += fmaxf(-q[k], 0.f);
+      }
+      R[v * ncell + c] = pp > 0.f ? fminf(1.f, (umax[v] - UL[v]) / pp) : 1.f;
+      R[(4 + v) * ncell + c] = pm > 0.f ? fminf(1.f, (UL[v] - umin[v]) / pm) : 1.f;
+    }
+  }
+}
+
+__global__ void lf_update_kernel(UpdateArgs A) {
+  const Mesh2& M = A.M;
+  const long long ncell = (long long)M.nx * M.ny;
+  const long long nxf = (long long)(M.nx + 1) * M.ny, nf = nxf + (long long)M.nx * (M.ny + 1);
+  const float dt = (float)*A.dtp;
+  if (A.fixup < 0 && *A.all_plain == 0u) return;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell; c += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(c % M.nx), j = (int)(c / M.nx);
+    bool cl = true, cr = true, cb = true, ct = true, me = false;
+    if (A.fixup < 0) {
+      cl = cr = cb = ct = false;
+    } else if (A.fixup) {
+      me = A.flag[c] != 0;
+      const bool fl = cell_flagged(A, i - 1, j), fr = cell_flagged(A, i + 1, j);
+      const bool fb = cell_flagged(A, i, j - 1), ft = cell_flagged(A, i, j + 1);
+      if (!(me || fl || fr || fb || ft)) {
+        A.flag_out[c] = 0;
+        continue;
+      }
+      cl = !(me || fl);
+      cr = !(me || fr);
+      cb = !(me || fb);
+      ct = !(me || ft);
+    }
+    const long long xl = (long long)j * (M.nx + 1) + i, yb = nxf + (long long)j * M.nx + i;
+    float FL[4], FR[4], FB[4], FT[4];
+    face_total(A, xl, 0, cl, nf, neighbour(M, i - 1, j), c, FL);
+    face_total(A, xl + 1, 0, cr, nf, c, neighbour(M, i + 1, j), FR);
+    face_total(A, yb, 1, cb, nf, neighbour(M, i, j - 1), c, FB);
+    face_total(A, yb + M.nx, 1, ct, nf, c, neighbour(M, i, j + 1), FT);
+    const float iwx = M.iw[0][i + 2], iwy = M.iw[1][j + 2];
+    float u[4], w[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const float L = -((FR[v] - FL[v]) * iwx + (FT[v] - FB[v]) * iwy);
+      const float u0 = A.un[v * ncell + c];
+      if (A.stage == 1) {
+        A.out[v * ncell + c] = L;
+        u[v] = fmaf(dt, L, u0);
+      } else {
+        u[v] = fmaf(0.5f * dt, A.k1[v * ncell + c] + L, u0);
+        A.out[v * ncell + c] = u[v];
+      }
+    }
+    recover<2>(u, w);
+    const bool ok = w[0] > 0.f && M.gm1 * w[3] > 0.f && fabsf(w[1]) < INFINITY && fabsf(w[2]) < INFINITY;
+    if (A.fixup == 0) {
+      A.flag_out[c] = ok ? 0 : 1;
+      if (!ok) atomicAdd(A.nfallback, 1ull);
+    } else if (A.fixup > 0) {
+      // flags only grow: a flagged cell stays plain, a newly failing one joins
+      A.flag_out[c] = (me || !ok) ? 1 : 0;
+      if (!ok && me) atomicOr(A.status, STATUS_NONPHYS);  // all its faces are plain already
+      if (!ok && A.last) atomicOr(A.all_plain, 1u);
+    } else if (!ok) {
+      atomicOr(A.status, STATUS_NONPHYS);  // the plain scheme itself fails
+    }
+  }
+}
+
+// Training targets: add weight * (F(U) + F(U + dt K)) / 2, averaged over the
+// `s` fine faces that make up each coarse face, to acc[axis][v][J][I] (double).
+// Coarse x face (I, J) is the face between coarse cells (I - 1, J) and (I, J).
+template <int SOLVER>
+__global__ void face_flux_accumulate_kernel(Mesh2 M, const float* __restrict__ un, const float* __restrict__ k,
+                                            const double* __restrict__ dtp, int s, double weight,
+                                            double* __restrict__ acc) {
+  const int ncx = M.nx / s, ncy = M.ny / s;
+  const long long nc = (long long)ncx * ncy;
+  const float dt = (float)*dtp;
+  for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < 2 * nc; f += (long long)gridDim.x * blockDim.x) {
+    const int axis = (int)(f / nc);
+    const long long r = f - axis * nc;
+    const int I = (int)(r % ncx), J = (int)(r / ncx);
+    double sum[4] = {0, 0, 0, 0};
+    for (int q = 0; q < s; ++q) {
+      for (int st = 0; st < 2; ++st) {
+        const float* kk = st ? k : nullptr;
+        float w[4][4], Fl[4];
+        if (axis == 0) {
+          const int i = s * I, j = s * J + q;
+#pragma unroll
+          for (int c = 0; c < 4; ++c) cell_prim(M, un, kk, dt, i - 2 + c, j, w[c]);
+          plain_face_flux<0, SOLVER>(M, w, i - 1, Fl);
+        } else {
+          const int i = s * I + q, j = s * J;
+#pragma unroll
+          for (int c = 0; c < 4; ++c) cell_prim(M, un, kk, dt, i, j - 2 + c, w[c]);
+          plain_face_flux<1, SOLVER>(M, w, j - 1, Fl);
+        }
+#pragma unroll
+        for (int v = 0; v < 4; ++v) sum[v] += (double)Fl[v];
+      }
+    }
+    const double scale = weight * 0.5 / s;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[((size_t)axis * 4 + v) * nc + r] += scale * sum[v];
+  }
+}
+
+// Conservative restriction of a 2D FP32 state by an integer factor on a
+// uniform mesh: each coarse cell holds the mean of its factor^2 fine cells.
+__global__ void restrict_kernel(int nx, int ny, int s, const float* __restrict__ uf, float* __restrict__ uc) {
+  const int ncx = nx / s, ncy = ny / s;
+  const long long nc = (long long)ncx * ncy, nfc = (long long)nx * ny;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < 4 * nc; c += (long long)gridDim.x * blockDim.x) {
+    const int v = (int)(c / nc);
+    const long long r = c - v * nc;
+    const int I = (int)(r % ncx), J = (int)(r / ncx);
+    double sum = 0.0;
+    for (int b = 0; b < s; ++b)
+      for (int a = 0; a < s; ++a) sum += (double)uf[v * nfc + (long long)(s * J + b) * nx + s * I + a];
+    uc[c] = (float)(sum / ((double)s * s));
+  }
+}
+
+// Features of the distinct faces of a periodic 2D state in compact order
+// (axis, j, i): face (i, j) of axis 0 lies between cells (i-1, j) and (i, j).
+__global__ void train_features_kernel(Mesh2 M, const float* __restrict__ un, __nv_bfloat16* __restrict__ X,
+                                      float* __restrict__ scale) {
+  const long long nc = (long long)M.nx * M.ny;
+  for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < 2 * nc; f += (long long)gridDim.x * blockDim.x) {
+    const int axis = (int)(f / nc);
+    const long long r = f - axis * nc;
+    const int i = (int)(r % M.nx), j = (int)(r / M.nx);
+    float s[6][4];
+    if (axis == 0) {
+#pragma unroll
+      for (int c = 0; c < 6; ++c) cell_prim(M, un, nullptr, 0.f, i - 3 + c, j, s[c]);
+      face_features<0>(M, s, X + f * mlp::KIN, scale + f * 4);
+    } else {
+#pragma unroll
+      for (int c = 0; c < 6; ++c) cell_prim(M, un, nullptr, 0.f, i, j - 3 + c, s[c]);
+      face_features<1>(M, s, X + f * mlp::KIN, scale + f * 4);
+    }
+  }
+}
+
+// Targets in the face frame: T = rot^-1(F_target - F_plain) / scale, in the
+// compact face order of train_features_kernel.
+__global__ void train_targets_kernel(long long nc, const double* __restrict__ ft, const double* __restrict__ fp,
+                                     const float* __restrict__ scale, float* __restrict__ T) {
+  for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < 2 * nc; f += (long long)gridDim.x * blockDim.x) {
+    const int axis = (int)(f / nc);
+    const long long r = f - axis * nc;
+    double d[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const size_t idx = ((size_t)axis * 4 + v) * nc + r;
+      d[v] = ft[idx] - fp[idx];
+    }
+    const double dn = axis == 0 ? d[1] : d[2], dtv = axis == 0 ? d[2] : d[1];
+    const float* s = scale + f * 4;
+    T[f * 4 + 0] = (float)(d[0] / s[0]);
+    T[f * 4 + 1] = (float)(dn / s[1]);
+    T[f * 4 + 2] = (float)(dtv / s[2]);
+    T[f * 4 + 3] = (float)(d[3] / s[3]);
+  }
+}
+
+// ----------------------------------------------------------------- launchers
+
+static int blocks_for(long long n, int block = 256, int cap = 8192) {
+  long long b = (n + block - 1) / block;
+  return (int)(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+cudaError_t launch_face_flux_accumulate(const Mesh2& M, int solver, const float* un, const float* k, const double* dtp,
+                                        int s, double weight, double* acc, cudaStream_t st) {
+  const long long n = 2LL * (M.nx / s) * (M.ny / s);
+  if (solver == SOLVER_HLL) face_flux_accumulate_kernel<SOLVER_HLL><<<blocks_for(n), 256, 0, st>>>(M, un, k, dtp, s, weight, acc);
+  else face_flux_accumulate_kernel<SOLVER_HLLC><<<blocks_for(n), 256, 0, st>>>(M, un, k, dtp, s, weight, acc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_restrict(int nx, int ny, int s, const float* uf, float* uc, cudaStream_t st) {
+  restrict_kernel<<<blocks_for(4LL * (nx / s) * (ny / s)), 256, 0, st>>>(nx, ny, s, uf, uc);
+  return cudaGetLastError();
+}
+
+}  // namespace gh
+
+using namespace gh;
+
+// ================================================================ MLP C API
+
+namespace {
+
+int mlp_grad_impl(const float* P, const void* X, const float* T, long long n, float* grad, float* loss, float* Pupd,
+                  float* m, float* v, int step, float lr, cudaStream_t st) {
+  if (n < 1) return fail(GENASIS_EINVAL, "mlp: n must be >= 1");
+  static bool attr_set = false;
+  if (!attr_set) {
+    GH_CK(cudaFuncSetAttribute(mlp_train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TrainSmem)));
+    attr_set = true;
+  }
+  int dev = 0, sms = 0;
+  GH_CK(cudaGetDevice(&dev));
+  GH_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  long long iters = (n + TS - 1) / TS;
+  int nblk = (int)(iters < (long long)sms ? iters : (long long)sms);
+  float* part = nullptr;
+  float* part_loss = nullptr;
+  GH_CK(cudaMallocAsync((void**)&part, (size_t)nblk * mlp::NPARAM * sizeof(float), st));
+  GH_CK(cudaMallocAsync((void**)&part_loss, (size_t)nblk * sizeof(float), st));
+  const float inv = 1.0f / (float)(4.0 * (double)n);
+  mlp_train_kernel<<<nblk, 256, sizeof(TrainSmem), st>>>(P, (const __nv_bfloat16*)X, T, n, inv, part, part_loss);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) {
+    mlp_reduce_adam_kernel<<<(mlp::NPARAM + 255) / 256, 256, 0, st>>>(part, part_loss, nblk, grad, loss, Pupd, m, v, step,
+                                                                       lr, 0.9f, 0.999f, 1e-8f);
+    e = cudaGetLastError();
+  }
+  cudaFreeAsync(part, st);
+  cudaFreeAsync(part_loss, st);
+  GH_CK(e);
+  return GENASIS_OK;
+}
+
+}  // namespace
+
+struct genasis_mlp_opt {
+  float* P = nullptr;
+  float* m = nullptr;
+  float* v = nullptr;
+  float* loss = nullptr;
+  int step = 0;
+  cudaStream_t stream = nullptr;
+};
+
+extern "C" {
+
+int genasis_mlp_param_count(void) { return mlp::NPARAM; }
+
+int genasis_mlp_forward(const float* params, const void* X, long long n, float* Y, void* stream) {
+  if (!params || !X || !Y || n < 0) return fail(GENASIS_EINVAL, "mlp_forward: bad argument");
+  if (!is_device_ptr(params) || !is_device_ptr(X) || !is_device_ptr(Y))
+    return fail(GENASIS_EINVAL, "mlp_forward: params, X and Y must be device pointers");
+  if (n == 0) return GENASIS_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long tiles = (n + 15) / 16;
+  const int nb = (int)((tiles + 7) / 8 < 4096 ? (tiles + 7) / 8 : 4096);
+  mlp_infer_kernel<<<nb, 256, 0, st>>>(params, (const __nv_bfloat16*)X, n, Y);
+  GH_CK(cudaGetLastError());
+  return GENASIS_OK;
+}
+
+int genasis_mlp_gradient(const float* params, const void* X, const float* T, long long n, float* grad, float* loss,
+                         void* stream) {
+  if (!params || !X || !T || !grad) return fail(GENASIS_EINVAL, "mlp_gradient: NULL argument");
+  if (!is_device_ptr(params) || !is_device_ptr(X) || !is_device_ptr(T) || !is_device_ptr(grad) ||
+      (loss && !is_device_ptr(loss)))
+    return fail(GENASIS_EINVAL, "mlp_gradient: all pointers must be device pointers");
+  return mlp_grad_impl(params, X, T, n, grad, loss, nullptr, nullptr, nullptr, 0, 0.f, (cudaStream_t)stream);
+}
+
+int genasis_mlp_opt_create(const float* params, void* stream, genasis_mlp_opt_t* out) {
+  if (!params || !out) return fail(GENASIS_EINVAL, "mlp_opt_create: NULL argument");
+  genasis_mlp_opt* o = new genasis_mlp_opt();
+  o->stream = (cudaStream_t)stream;
+  const size_t bytes = mlp::NPARAM * sizeof(float);
+  cudaError_t e = cudaMalloc(&o->P, bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&o->m, bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&o->v, bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&o->loss, sizeof(float));
+  if (e == cudaSuccess) e = cudaMemsetAsync(o->m, 0, bytes, o->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(o->v, 0, bytes, o->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(o->P, params, bytes, is_device_ptr(params) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                        o->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(o->stream);
+  if (e != cudaSuccess) {
+    cudaFree(o->P);
+    cudaFree(o->m);
+    cudaFree(o->v);
+    cudaFree(o->loss);
+    delete o;
+    return fail(e == cudaErrorMemoryAllocation ? GENASIS_ENOMEM : GENASIS_ECUDA, "mlp_opt_create: %s",
+                cudaGetErrorString(e));
+  }
+  *out = o;
+  return GENASIS_OK;
+}
+
+int genasis_mlp_opt_destroy(genasis_mlp_opt_t o) {
+  if (!o) return GENASIS_OK;
+  if (o->stream) cudaStreamSynchronize(o->stream);
+  cudaFree(o->P);
+  cudaFree(o->m);
+  cudaFree(o->v);
+  cudaFree(o->loss);
+  delete o;
+  return GENASIS_OK;
+}
+
+int genasis_mlp_opt_step(genasis_mlp_opt_t o, const void* X, const float* T, long long n, float lr, float* loss_out) {
+  if (!o || !X || !T) return fail(GENASIS_EINVAL, "mlp_opt_step: NULL argument");
+  if (!is_device_ptr(X) || !is_device_ptr(T)) return fail(GENASIS_EINVAL, "mlp_opt_step: X and T must be device pointers");
+  if (!(lr > 0.f)) return fail(GENASIS_EINVAL, "mlp_opt_step: lr must be > 0");
+  o->step += 1;
+  int rc = mlp_grad_impl(o->P, X, T, n, nullptr, o->loss, o->P, o->m, o->v, o->step, lr, o->stream);
+  if (rc) return rc;
+  if (loss_out) {
+    float l = 0.f;
+    GH_CK(cudaMemcpyAsync(&l, o->loss, sizeof(float), cudaMemcpyDeviceToHost, o->stream));
+    GH_CK(cudaStreamSynchronize(o->stream));
+    *loss_out = l / (float)(4.0 * (double)n);
+  }
+  return GENASIS_OK;
+}
+
+int genasis_mlp_opt_get_params(genasis_mlp_opt_t o, float* params) {
+  if (!o || !params) return fail(GENASIS_EINVAL, "mlp_opt_get_params: NULL argument");
+  GH_CK(cudaMemcpyAsync(params, o->P, mlp::NPARAM * sizeof(float),
+                        is_device_ptr(params) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, o->stream));
+  GH_CK(cudaStreamSynchronize(o->stream));
+  return GENASIS_OK;
+}
+
+}  // extern "C"
+
+// ===================================================== learned solver handle
+
+struct genasis_learned {
+  Mesh2 M{};
+  int solver = 1;
+  size_t ncell = 0;
+  long long nf = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  void* U[2] = {nullptr, nullptr};
+  int cur = 0;
+  float* K = nullptr;
+  Geo<float>* geo[2] = {nullptr, nullptr};
+  float* iw[2] = {nullptr, nullptr};
+  double* wd[2] = {nullptr, nullptr};
+  float* F = nullptr;
+  __nv_bfloat16* X = nullptr;
+  float* scale = nullptr;
+  float* dY = nullptr;
+  unsigned char* flag[2] = {nullptr, nullptr};
+  float* params = nullptr;
+  bool corrected = false;
+  float ylim = INFINITY;
+  bool fct = true;
+  float* R = nullptr;
+  double* scal = nullptr;
+  double* part_speed = nullptr;
+  unsigned* status = nullptr;
+  unsigned long long* nfallback = nullptr;
+  unsigned* all_plain = nullptr;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  int g_nsteps = -1;
+  double g_cfl = 0, g_tend = 0;
+  bool g_corr = false;
+};
+
+namespace {
+
+constexpr int kFallbackPasses = 3;
+
+int learned_free(genasis_learned* l) {
+  if (l->stream) cudaStreamSynchronize(l->stream);
+  for (int b = 0; b < 2; ++b) {
+    if (l->graph[b]) cudaGraphExecDestroy(l->graph[b]);
+    cudaFree(l->U[b]);
+    cudaFree(l->geo[b]);
+    cudaFree(l->iw[b]);
+    cudaFree(l->wd[b]);
+  }
+  for (void* p : {(void*)l->K, (void*)l->F, (void*)l->X, (void*)l->scale, (void*)l->dY, (void*)l->flag[0],
+                  (void*)l->flag[1], (void*)l->params, (void*)l->scal, (void*)l->part_speed, (void*)l->status,
+                  (void*)l->nfallback, (void*)l->all_plain, (void*)l->R})
+    cudaFree(p);
+  if (l->own_stream && l->stream) cudaStreamDestroy(l->stream);
+  delete l;
+  return GENASIS_OK;
+}
+
+void drop_graphs(genasis_learned* l) {
+  for (int b = 0; b < 2; ++b)
+    if (l->graph[b]) {
+      cudaGraphExecDestroy(l->graph[b]);
+      l->graph[b] = nullptr;
+    }
+}
+
+// One corrected RK2 step: dt = cfl * dt_CFL (clamped at t_end > 0), or the
+// given dt when fixed_dt > 0.
+int learned_enqueue_step(genasis_learned* l, double cfl, double t_end, double fixed_dt = 0.0) {
+  cudaStream_t st = l->stream;
+  // CFL time step from U^n (Eq. courantTimeStep)
+  ReduceArgs<float> R;
+  memset(&R, 0, sizeof(R));
+  R.ncell = l->ncell;
+  R.n[0] = l->M.nx;
+  R.n[1] = l->M.ny;
+  R.n[2] = 1;
+  R.iw[0] = l->iw[0];
+  R.iw[1] = l->iw[1];
+  R.wd[0] = l->wd[0];
+  R.wd[1] = l->wd[1];
+  R.gamma = l->M.gamma;
+  R.U = (const float*)l->U[l->cur];
+  R.part_speed = l->part_speed;
+  R.status = l->status;
+  R.nblk = blocks_for((long long)l->ncell, 256, 1024);
+  GH_CK(launch_speed<float>(2, R, st));
+  FinalizeArgs Fa;
+  memset(&Fa, 0, sizeof(Fa));
+  Fa.part_speed = l->part_speed;
+  Fa.nblk = R.nblk;
+  Fa.nv = 4;
+  Fa.mode = fixed_dt > 0.0 ? FIN_FIXED : FIN_CFL;
+  Fa.cfl = cfl;
+  Fa.fixed_dt = fixed_dt;
+  Fa.t_end = t_end;
+  Fa.scal = l->scal;
+  Fa.status = l->status;
+  GH_CK(launch_finalize(Fa, st));
+  const float* un = (const float*)l->U[l->cur];
+  for (int stage = 1; stage <= 2; ++stage) {
+    const float* kin = stage == 2 ? l->K : nullptr;
+    const int nb = blocks_for(l->nf);
+    if (l->solver == SOLVER_HLL)
+      lf_faces_kernel<SOLVER_HLL><<<nb, 256, 0, st>>>(l->M, un, kin, l->scal + SCAL_DT, l->F, l->corrected ? l->X : nullptr, l->scale);
+    else
+      lf_faces_kernel<SOLVER_HLLC><<<nb, 256, 0, st>>>(l->M, un, kin, l->scal + SCAL_DT, l->F, l->corrected ? l->X : nullptr, l->scale);
+    GH_CK(cudaGetLastError());
+    if (l->corrected) {
+      const long long tiles = (l->nf + 15) / 16;
+      mlp_infer_kernel<<<(int)((tiles + 7) / 8 < 4096 ? (tiles + 7) / 8 : 4096), 256, 0, st>>>(l->params, l->X, l->nf, l->dY);
+      GH_CK(cudaGetLastError());
+    }
+    UpdateArgs A;
+    A.M = l->M;
+    A.un = un;
+    A.k1 = l->K;
+    A.dtp = l->scal + SCAL_DT;
+    A.F = l->F;
+    A.dY = l->corrected ? l->dY : nullptr;
+    A.scale = l->scale;
+    A.out = stage == 1 ? l->K : (float*)l->U[1 - l->cur];
+    A.flag = l->flag[1];
+    A.flag_out = l->flag[0];
+    A.nfallback = l->nfallback;
+    A.status = l->status;
+    A.stage = stage;
+    A.fixup = 0;
+    A.last = 0;
+    A.all_plain = l->all_plain;
+    A.ylim = l->ylim;
+    A.R = nullptr;
+    const int nc = blocks_for((long long)l->ncell);
+    if (l->corrected && l->fct) {
+      lf_fct_kernel<<<nc, 256, 0, st>>>(A, l->R);
+      GH_CK(cudaGetLastError());
+      A.R = l->R;
+    }
+    lf_update_kernel<<<nc, 256, 0, st>>>(A);
+    GH_CK(cudaGetLastError());
+    if (l->corrected) {
+      // widening passes: cells touching flagged cells use the plain flux on
+      // those faces (both sides of a face decide alike, so the update stays
+      // conservative); flags only grow
+      for (int pass = 1; pass <= kFallbackPasses; ++pass) {
+        A.flag = l->flag[(pass + 1) & 1];
+        A.flag_out = l->flag[pass & 1];
+        A.fixup = pass;
+        A.last = pass == kFallbackPasses;
+        lf_update_kernel<<<nc, 256, 0, st>>>(A);
+        GH_CK(cudaGetLastError());
+      }
+      // if widening did not clear every failure, the whole stage takes the plain flux
+      A.fixup = -1;
+      lf_update_kernel<<<nc, 256, 0, st>>>(A);
+      GH_CK(cudaGetLastError());
+      GH_CK(cudaMemsetAsync(l->all_plain, 0, sizeof(unsigned), st));
+    }
+  }
+  l->cur = 1 - l->cur;
+  return GENASIS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int genasis_learned_create(const genasis_hydro_desc* d, genasis_learned_t* out) {
+  if (!d || !out) return fail(GENASIS_EINVAL, "learned_create: NULL argument");
+  *out = nullptr;
+  if (d->ndim != 2) return fail(GENASIS_EINVAL, "learned_create: the learned correction is 2D (ndim = 2)");
+  if (d->precision != GENASIS_FP32_MIXED) return fail(GENASIS_EINVAL, "learned_create: precision must be GENASIS_FP32_MIXED");
+  if (d->solver != GENASIS_HLL && d->solver != GENASIS_HLLC) return fail(GENASIS_EINVAL, "learned_create: bad solver");
+  if (!(d->gamma > 1.0) || !(d->theta >= 1.0 && d->theta <= 2.0)) return fail(GENASIS_EINVAL, "learned_create: bad gamma or theta");
+  for (int q = 0; q < 2; ++q) {
+    if (d->n[q] < 6) return fail(GENASIS_EINVAL, "learned_create: n[%d] must be >= 6", q);
+    if (!d->widths[q]) return fail(GENASIS_EINVAL, "learned_create: widths[%d] is NULL", q);
+    for (int i = 0; i < d->n[q]; ++i)
+      if (!(d->widths[q][i] > 0.0) || !isfinite(d->widths[q][i])) return fail(GENASIS_EINVAL, "learned_create: bad width");
+    if (d->bc_lo[q] < 0 || d->bc_lo[q] > 2 || d->bc_hi[q] < 0 || d->bc_hi[q] > 2) return fail(GENASIS_EINVAL, "learned_create: bad boundary code");
+    if ((d->bc_lo[q] == GENASIS_BC_PERIODIC) != (d->bc_hi[q] == GENASIS_BC_PERIODIC))
+      return fail(GENASIS_EINVAL, "learned_create: periodic must be set on both ends");
+  }
+  genasis_learned* l = new genasis_learned();
+  l->solver = d->solver;
+  l->M.nx = d->n[0];
+  l->M.ny = d->n[1];
+  for (int q = 0; q < 2; ++q) {
+    l->M.bc_lo[q] = d->bc_lo[q];
+    l->M.bc_hi[q] = d->bc_hi[q];
+  }
+  l->M.gamma = (float)d->gamma;
+  l->M.gm1 = (float)(d->gamma - 1.0);
+  l->M.theta = (float)d->theta;
+  l->ncell = (size_t)l->M.nx * l->M.ny;
+  l->nf = (long long)(l->M.nx + 1) * l->M.ny + (long long)l->M.nx * (l->M.ny + 1);
+#define LCK(call)                                                                                   \
+  do {                                                                                              \
+    cudaError_t e_ = (call);                                                                        \
+    if (e_ != cudaSuccess) {                                                                        \
+      int code_ = fail(e_ == cudaErrorMemoryAllocation ? GENASIS_ENOMEM : GENASIS_ECUDA, "%s: %s", #call, \
+                       cudaGetErrorString(e_));                                                     \
+      learned_free(l);                                                                              \
+      return code_;                                                                                 \
+    }                                                                                               \
+  } while (0)
+  if (d->stream) {
+    l->stream = (cudaStream_t)d->stream;
+  } else {
+    LCK(cudaStreamCreateWithFlags(&l->stream, cudaStreamNonBlocking));
+    l->own_stream = true;
+  }
+  const size_t sbytes = l->ncell * 4 * sizeof(float);
+  for (int b = 0; b < 2; ++b) {
+    LCK(cudaMalloc(&l->U[b], sbytes));
+    LCK(cudaMemsetAsync(l->U[b], 0, sbytes, l->stream));
+  }
+  LCK(cudaMalloc((void**)&l->K, sbytes));
+  LCK(cudaMalloc((void**)&l->F, (size_t)l->nf * 4 * sizeof(float)));
+  LCK(cudaMalloc((void**)&l->X, (size_t)l->nf * mlp::KIN * sizeof(__nv_bfloat16)));
+  LCK(cudaMalloc((void**)&l->scale, (size_t)l->nf * 4 * sizeof(float)));
+  LCK(cudaMalloc((void**)&l->dY, (size_t)l->nf * 4 * sizeof(float)));
+  for (int b = 0; b < 2; ++b) {
+    LCK(cudaMalloc((void**)&l->flag[b], l->ncell));
+    LCK(cudaMemsetAsync(l->flag[b], 0, l->ncell, l->stream));
+  }
+  LCK(cudaMalloc((void**)&l->params, mlp::NPARAM * sizeof(float)));
+  LCK(cudaMalloc((void**)&l->scal, SCAL_COUNT * sizeof(double)));
+  LCK(cudaMemsetAsync(l->scal, 0, SCAL_COUNT * sizeof(double), l->stream));
+  LCK(cudaMalloc((void**)&l->part_speed, 1024 * sizeof(double)));
+  LCK(cudaMalloc((void**)&l->status, sizeof(unsigned)));
+  LCK(cudaMemsetAsync(l->status, 0, sizeof(unsigned), l->stream));
+  LCK(cudaMalloc((void**)&l->R, l->ncell * 8 * sizeof(float)));
+  LCK(cudaMalloc((void**)&l->all_plain, sizeof(unsigned)));
+  LCK(cudaMemsetAsync(l->all_plain, 0, sizeof(unsigned), l->stream));
+  LCK(cudaMalloc((void**)&l->nfallback, sizeof(unsigned long long)));
+  LCK(cudaMemsetAsync(l->nfallback, 0, sizeof(unsigned long long), l->stream));
+  for (int q = 0; q < 2; ++q) {
+    std::vector<Geo<float>> geo;
+    std::vector<float> iw;
+    append_geometry<float>(extended_widths(d->widths[q], d->n[q], d->bc_lo[q], d->bc_hi[q]), geo, iw);
+    LCK(cudaMalloc((void**)&l->geo[q], geo.size() * sizeof(Geo<float>)));
+    LCK(cudaMalloc((void**)&l->iw[q], iw.size() * sizeof(float)));
+    LCK(cudaMalloc((void**)&l->wd[q], d->n[q] * sizeof(double)));
+    LCK(cudaMemcpy(l->geo[q], geo.data(), geo.size() * sizeof(Geo<float>), cudaMemcpyHostToDevice));
+    LCK(cudaMemcpy(l->iw[q], iw.data(), iw.size() * sizeof(float), cudaMemcpyHostToDevice));
+    LCK(cudaMemcpy(l->wd[q], d->widths[q], d->n[q] * sizeof(double), cudaMemcpyHostToDevice));
+    l->M.geo[q] = l->geo[q];
+    l->M.iw[q] = l->iw[q];
+  }
+  LCK(cudaStreamSynchronize(l->stream));
+#undef LCK
+  *out = l;
+  return GENASIS_OK;
+}
+
+int genasis_learned_destroy(genasis_learned_t l) {
+  if (!l) return GENASIS_OK;
+  return learned_free(l);
+}
+
+int genasis_learned_set_params(genasis_learned_t l, const float* params) {
+  if (!l) return fail(GENASIS_EINVAL, "NULL handle");
+  drop_graphs(l);
+  if (!params) {
+    l->corrected = false;
+    return GENASIS_OK;
+  }
+  GH_CK(cudaMemcpyAsync(l->params, params, mlp::NPARAM * sizeof(float),
+                        is_device_ptr(params) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, l->stream));
+  GH_CK(cudaStreamSynchronize(l->stream));
+  l->corrected = true;
+  return GENASIS_OK;
+}
+
+int genasis_learned_set_fct(genasis_learned_t l, int enabled) {
+  if (!l || (enabled != 0 && enabled != 1)) return fail(GENASIS_EINVAL, "learned_set_fct: bad argument");
+  l->fct = enabled == 1;
+  drop_graphs(l);
+  return GENASIS_OK;
+}
+
+int genasis_learned_set_limit(genasis_learned_t l, float ylim) {
+  if (!l) return fail(GENASIS_EINVAL, "NULL handle");
+  if (!(ylim >= 0.0f)) return fail(GENASIS_EINVAL, "learned_set_limit: limit must be >= 0 (INFINITY: none)");
+  l->ylim = ylim;
+  drop_graphs(l);
+  return GENASIS_OK;
+}
+
+int genasis_learned_set_primitive(genasis_learned_t l, const double* rho, const double* vel, const double* p) {
+  if (!l || !rho || !vel || !p) return fail(GENASIS_EINVAL, "NULL argument");
+  const double* src[3] = {rho, vel, p};
+  const size_t cnt[3] = {l->ncell, 2 * l->ncell, l->ncell};
+  double* tmp[3] = {nullptr, nullptr, nullptr};
+  const double* use[3];
+  int rc = GENASIS_OK;
+  for (int a = 0; a < 3; ++a) {
+    use[a] = src[a];
+    if (is_device_ptr(src[a])) continue;
+    cudaError_t e = cudaMallocAsync((void**)&tmp[a], cnt[a] * sizeof(double), l->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(tmp[a], src[a], cnt[a] * sizeof(double), cudaMemcpyHostToDevice, l->stream);
+    if (e != cudaSuccess) rc = fail(GENASIS_ECUDA, "staging primitives: %s", cudaGetErrorString(e));
+    use[a] = tmp[a];
+  }
+  if (!rc) {
+    cudaError_t e = launch_init_from_primitive<float>(2, l->ncell, (double)l->M.gamma, use[0], use[1], use[2],
+                                                      (float*)l->U[l->cur], l->stream);
+    if (e != cudaSuccess) rc = fail(GENASIS_ECUDA, "init kernel: %s", cudaGetErrorString(e));
+  }
+  for (int a = 0; a < 3; ++a)
+    if (tmp[a]) cudaFreeAsync(tmp[a], l->stream);
+  if (rc) return rc;
+  GH_CK(cudaMemsetAsync(l->scal + SCAL_T, 0, sizeof(double), l->stream));
+  GH_CK(cudaStreamSynchronize(l->stream));
+  return GENASIS_OK;
+}
+
+int genasis_learned_set_conserved(genasis_learned_t l, const float* U) {
+  if (!l || !U) return fail(GENASIS_EINVAL, "NULL argument");
+  GH_CK(cudaMemcpyAsync(l->U[l->cur], U, l->ncell * 4 * sizeof(float),
+                        is_device_ptr(U) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, l->stream));
+  GH_CK(cudaStreamSynchronize(l->stream));
+  return GENASIS_OK;
+}
+
+int genasis_learned_get_conserved(genasis_learned_t l, float* U) {
+  if (!l || !U) return fail(GENASIS_EINVAL, "NULL argument");
+  GH_CK(cudaMemcpyAsync(U, l->U[l->cur], l->ncell * 4 * sizeof(float),
+                        is_device_ptr(U) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, l->stream));
+  unsigned st = 0;
+  GH_CK(cudaMemcpyAsync(&st, l->status, sizeof(unsigned), cudaMemcpyDeviceToHost, l->stream));
+  GH_CK(cudaStreamSynchronize(l->stream));
+  if (st & STATUS_NONPHYS) return fail(GENASIS_ENONPHYS, "non-physical state (rho <= 0, p <= 0 or NaN) on the device");
+  return GENASIS_OK;
+}
+
+int genasis_learned_advance(genasis_learned_t l, int nsteps, double cfl, double t_end, double* t_out) {
+  if (!l) return fail(GENASIS_EINVAL, "NULL handle");
+  if (nsteps < 0 || !(cfl > 0.0)) return fail(GENASIS_EINVAL, "learned_advance: bad nsteps or cfl");
+  if (nsteps > 0) {
+    if (l->g_nsteps != nsteps || l->g_cfl != cfl || l->g_tend != t_end || l->g_corr != l->corrected) {
+      drop_graphs(l);
+      l->g_nsteps = nsteps;
+      l->g_cfl = cfl;
+      l->g_tend = t_end;
+      l->g_corr = l->corrected;
+    }
+    const int cur0 = l->cur;
+    if (!l->graph[cur0]) {
+      cudaGraph_t g;
+      GH_CK(cudaStreamBeginCapture(l->stream, cudaStreamCaptureModeThreadLocal));
+      int rc = GENASIS_OK;
+      for (int s = 0; s < nsteps && !rc; ++s) rc = learned_enqueue_step(l, cfl, t_end);
+      cudaError_t e = cudaStreamEndCapture(l->stream, &g);
+      l->cur = cur0;
+      if (rc) {
+        if (e == cudaSuccess) cudaGraphDestroy(g);
+        return rc;
+      }
+      GH_CK(e);
+      e = cudaGraphInstantiate(&l->graph[cur0], g, 0);
+      cudaGraphDestroy(g);
+      GH_CK(e);
+    }
+    GH_CK(cudaGraphLaunch(l->graph[cur0], l->stream));
+    l->cur = cur0 ^ (nsteps & 1);
+  }
+  if (t_out) {
+    GH_CK(cudaMemcpyAsync(t_out, l->scal + SCAL_T, sizeof(double), cudaMemcpyDeviceToHost, l->stream));
+    unsigned st = 0;
+    GH_CK(cudaMemcpyAsync(&st, l->status, sizeof(unsigned), cudaMemcpyDeviceToHost, l->stream));
+    GH_CK(cudaStreamSynchronize(l->stream));
+    if (st & STATUS_NONPHYS) return fail(GENASIS_ENONPHYS, "non-physical state even with the plain flux");
+  }
+  return GENASIS_OK;
+}
+
+int genasis_learned_step(genasis_learned_t l, double dt) {
+  if (!l) return fail(GENASIS_EINVAL, "NULL handle");
+  if (!(dt > 0.0) || !(dt < INFINITY)) return fail(GENASIS_EINVAL, "learned_step: dt must be finite and > 0");
+  return learned_enqueue_step(l, 1.0, 0.0, dt);
+}
+
+int genasis_learned_fallbacks(genasis_learned_t l, long long* cells) {
+  if (!l || !cells) return fail(GENASIS_EINVAL, "NULL argument");
+  unsigned long long v = 0;
+  GH_CK(cudaMemcpyAsync(&v, l->nfallback, sizeof(v), cudaMemcpyDeviceToHost, l->stream));
+  GH_CK(cudaStreamSynchronize(l->stream));
+  *cells = (long long)v;
+  return GENASIS_OK;
+}
+
+int genasis_learned_features(genasis_learned_t l, void* X, float* scale) {
+  if (!l || !X || !scale) return fail(GENASIS_EINVAL, "NULL argument");
+  if (!is_device_ptr(X) || !is_device_ptr(scale)) return fail(GENASIS_EINVAL, "learned_features: device pointers required");
+  if (l->M.bc_lo[0] != GENASIS_BC_PERIODIC || l->M.bc_lo[1] != GENASIS_BC_PERIODIC)
+    return fail(GENASIS_EINVAL, "learned_features: training features need a periodic mesh");
+  train_features_kernel<<<blocks_for(2LL * l->ncell), 256, 0, l->stream>>>(l->M, (const float*)l->U[l->cur],
+                                                                           (__nv_bfloat16*)X, scale);
+  GH_CK(cudaGetLastError());
+  GH_CK(cudaStreamSynchronize(l->stream));
+  return GENASIS_OK;
+}
+
+int genasis_learned_targets(genasis_learned_t l, const double* f_target, const double* f_plain, const float* scale,
+                            float* T) {
+  if (!l || !f_target || !f_plain || !scale || !T) return fail(GENASIS_EINVAL, "NULL argument");
+  if (!is_device_ptr(f_target) || !is_device_ptr(f_plain) || !is_device_ptr(scale) || !is_device_ptr(T))
+    return fail(GENASIS_EINVAL, "learned_targets: device pointers required");
+  const long long nc = (long long)l->ncell;
+  train_targets_kernel<<<blocks_for(2 * nc), 256, 0, l->stream>>>(nc, f_target, f_plain, scale, T);
+  GH_CK(cudaGetLastError());
+  GH_CK(cudaStreamSynchronize(l->stream));
+  return GENASIS_OK;
+}
+
+}  // extern "C"

@@ -32,6 +32,8 @@ struct StageArgs {
   const Geo<T>* geo[3];   // per axis, index c + 2 for c in [-2, n + 2)
   const T* iw[3];         // inverse widths, index c + 2
   const double* wd[3];    // widths in FP64, index c (totals)
+  const T* wdh[3];        // widths split as wdh + wdl (FP32 state: both floats; FP64 state: wdh = wd)
+  const T* wdl[3];
   const T* __restrict__ un;   // U^n      [NV][n2][n1][n0]
   const T* __restrict__ k1;   // K of stage 1 (stage 2 only)
   T* __restrict__ out;        // stage 1: K; stage 2: U^{n+1}
@@ -55,8 +57,11 @@ struct StageKernel {
   static constexpr int NHALO = HAS_Y ? 4 * TX + 4 * TY : 4;
   static_assert(HAS_Y || TY == 1, "tiles of 1D/2D runs are one row high");
   static_assert(NT % 32 == 0, "whole warps");
+  static constexpr int HSLOTS = (NHALO + NT - 1) / NT;  // halo slots per thread
 
   struct Smem {
+    Geo<T> gx[TX + 4];                 // geometry of cells a0 - 2 .. a0 + TX + 1
+    Geo<T> gy[HAS_Y ? TY + 4 : 1];     // geometry of cells b0 - 2 .. b0 + TY + 1
     T w[NV][SY][SX];
     T fx[NV][TY][TX + 1];
     T fy[HAS_Y ? NV : 1][HAS_Y ? TY + 1 : 1][TX];
@@ -71,16 +76,33 @@ struct StageKernel {
     return (size_t)a;
   }
 
-  // Load the conserved state of (possibly ghost) cell (a, b, m) -- for stage 2
-  // the provisional U1 = U^n + dt K -- and recover primitives.
-  static __device__ __forceinline__ void load_prim(const StageArgs<T>& A, int a, int b, int m, T dt,
-                                                   size_t vs, T (&w)[NV]) {
-    bool fa, fb = false, fm = false;
-    const int sa = bc_map(a, A.n[0], A.bc_lo[0], A.bc_hi[0], fa);
-    int sb = 0, sm = 0;
+  // Boundary-mapped in-plane part of a cell address (fixed for a tile): the
+  // march coordinate is mapped per plane by load_col.
+  struct ColRef {
+    size_t off;
+    bool fa, fb;
+  };
+
+  static __device__ __forceinline__ ColRef col_ref(const StageArgs<T>& A, int a, int b) {
+    ColRef r;
+    bool fb = false;
+    const int sa = bc_map(a, A.n[0], A.bc_lo[0], A.bc_hi[0], r.fa);
+    int sb = 0;
     if constexpr (HAS_Y) sb = bc_map(b, A.n[1], A.bc_lo[1], A.bc_hi[1], fb);
-    if constexpr (MARCH) sm = bc_map(m, A.n[AM], A.bc_lo[AM], A.bc_hi[AM], fm);
-    const size_t c = cell(A, sa, sb, sm);
+    r.fb = fb;
+    r.off = HAS_Y ? (size_t)sb * A.n[0] + sa : (size_t)sa;
+    return r;
+  }
+
+  // Primitives of the (possibly ghost) cell (ref, m); see load_prim.
+  static __device__ __forceinline__ void load_col(const StageArgs<T>& A, const ColRef& r, int m, T dt, size_t vs,
+                                                  T (&w)[NV]) {
+    bool fm = false;
+    size_t c = r.off;
+    if constexpr (MARCH) {
+      const int sm = bc_map(m, A.n[AM], A.bc_lo[AM], A.bc_hi[AM], fm);
+      c += (size_t)sm * (HAS_Y ? (size_t)A.n[0] * A.n[1] : (size_t)A.n[0]);
+    }
     T u[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
@@ -88,8 +110,8 @@ struct StageKernel {
       if (STAGE == 2) x = fma(dt, __ldg(A.k1 + v * vs + c), x);
       u[v] = x;
     }
-    if (fa) u[1] = -u[1];
-    if constexpr (HAS_Y) { if (fb) u[2] = -u[2]; }
+    if (r.fa) u[1] = -u[1];
+    if constexpr (HAS_Y) { if (r.fb) u[2] = -u[2]; }
     if constexpr (MARCH) { if (fm) u[1 + AM] = -u[1 + AM]; }
     recover<NDIM>(u, w);
   }
@@ -104,7 +126,7 @@ struct StageKernel {
   static __device__ __forceinline__ void x_face(const StageArgs<T>& A, Smem& S, int a0, int face, int srow,
                                                 int frow) {
     const int sl = face + 1;  // slot of the left cell
-    const Geo<T> gl = geo(A, 0, a0 + face - 1), gr = geo(A, 0, a0 + face);
+    const Geo<T> gl = S.gx[face + 1], gr = S.gx[face + 2];
     T wl[NV], wr[NV], f[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
@@ -120,7 +142,7 @@ struct StageKernel {
 
   static __device__ __forceinline__ void y_face(const StageArgs<T>& A, Smem& S, int b0, int face, int scol) {
     const int sl = face + 1;
-    const Geo<T> gl = geo(A, 1, b0 + face - 1), gr = geo(A, 1, b0 + face);
+    const Geo<T> gl = S.gy[face + 1], gr = S.gy[face + 2];
     T wl[NV], wr[NV], f[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
@@ -184,6 +206,37 @@ struct StageKernel {
     const T iwx = A.iw[0][min(ca, nx + 1) + 2];
     const T iwy = HAS_Y ? A.iw[1][min(cb, ny + 1) + 2] : T(0);
 
+    // per-tile tables: in-plane geometry in shared memory (made visible by the
+    // first barrier of the plane loop), boundary-mapped column addresses
+    for (int k = tid; k < TX + 4; k += NT) S.gx[k] = geo(A, 0, a0 + k - 2);
+    if constexpr (HAS_Y)
+      for (int k = tid; k < TY + 4; k += NT) S.gy[k] = geo(A, 1, b0 + k - 2);
+    const ColRef own = col_ref(A, ca, cb);
+    // this thread's halo slots h = tid + k NT: rows -2, -1, TY, TY+1 of the
+    // tile (3D), then columns -2, -1, TX, TX+1 of every row
+    int hsx[HSLOTS], hsy[HSLOTS];
+    ColRef halo[HSLOTS];
+#pragma unroll
+    for (int k = 0; k < HSLOTS; ++k) {
+      const int h = tid + k * NT;
+      int sx = 0, sy = 0;
+      if (h < NHALO) {
+        if (HAS_Y && h < 4 * TX) {
+          const int r = h / TX;
+          sx = h % TX + 2;
+          sy = r < 2 ? r : TY + r;
+        } else {
+          const int hh = HAS_Y ? h - 4 * TX : h;
+          const int c = hh & 3;
+          sy = HAS_Y ? (hh >> 2) + 2 : 0;
+          sx = c < 2 ? c : TX + c;
+        }
+      }
+      hsx[k] = sx;
+      hsy[k] = sy;
+      halo[k] = col_ref(A, a0 + sx - 2, HAS_Y ? b0 + sy - 2 : 0);
+    }
+
     ColumnSum<T> tcol[NV];  // this column's sum of U dq along the march axis
     T speed_max = T(0);
 
@@ -200,8 +253,8 @@ struct StageKernel {
     }
     int mstart = m0;
     if constexpr (MARCH) {
-      load_prim(A, ca, cb, m0 - 2, dt, vs, wk);
-      load_prim(A, ca, cb, m0 - 1, dt, vs, wk1);
+      load_col(A, own, m0 - 2, dt, vs, wk);
+      load_col(A, own, m0 - 1, dt, vs, wk1);
       mstart = m0 - 2;
     }
 
@@ -209,7 +262,7 @@ struct StageKernel {
       T fhi[NV], wk2[NV], sk1[NV];
       T wown[NV];
       if constexpr (MARCH) {
-        load_prim(A, ca, cb, m + 2, dt, vs, wk2);
+        load_col(A, own, m + 2, dt, vs, wk2);
         const Geo<T> g0 = geo(A, AM, m), g1 = geo(A, AM, m + 1);
         slopes(A, wk, wk1, wk2, g1, sk1);
         m_face(A, wk, sk, g0.h, wk1, sk1, g1.h, fhi);
@@ -226,28 +279,20 @@ struct StageKernel {
 #pragma unroll
         for (int v = 0; v < NV; ++v) wown[v] = wk[v];
       } else {
-        load_prim(A, ca, 0, 0, dt, vs, wown);
+        load_col(A, own, 0, dt, vs, wown);
       }
       // own cell into the shared plane
 #pragma unroll
       for (int v = 0; v < NV; ++v) S.w[v][HAS_Y ? ty + 2 : 0][tx + 2] = wown[v];
       // cross-shaped in-plane halo
-      for (int h = tid; h < NHALO; h += NT) {
-        int sx, sy;
-        if (HAS_Y && h < 4 * TX) {
-          const int r = h / TX;
-          sx = h % TX + 2;
-          sy = r < 2 ? r : TY + r;
-        } else {
-          const int hh = HAS_Y ? h - 4 * TX : h;
-          const int c = hh & 3;
-          sy = HAS_Y ? (hh >> 2) + 2 : 0;
-          sx = c < 2 ? c : TX + c;
-        }
-        T wh[NV];
-        load_prim(A, a0 + sx - 2, HAS_Y ? b0 + sy - 2 : 0, m, dt, vs, wh);
 #pragma unroll
-        for (int v = 0; v < NV; ++v) S.w[v][sy][sx] = wh[v];
+      for (int k = 0; k < HSLOTS; ++k) {
+        if (tid + k * NT < NHALO) {
+          T wh[NV];
+          load_col(A, halo[k], m, dt, vs, wh);
+#pragma unroll
+          for (int v = 0; v < NV; ++v) S.w[v][hsy[k]][hsx[k]] = wh[v];
+        }
       }
       __syncthreads();
 
@@ -294,8 +339,7 @@ struct StageKernel {
           if constexpr (MARCH) s = fmax(s, (fabs(wown[1 + AM]) + cs) * iwm);
           speed_max = fmax(speed_max, s);
           if (A.want_totals) {
-            const double dm = MARCH ? A.wd[AM][m] : 1.0;
-            const T dm_hi = (T)dm, dm_lo = (T)(dm - (double)dm_hi);
+            const T dm_hi = MARCH ? A.wdh[AM][m] : T(1), dm_lo = MARCH ? A.wdl[AM][m] : T(0);
 #pragma unroll
             for (int v = 0; v < NV; ++v) tcol[v].add_product(__ldg(A.un + v * vs + c), dm_hi, dm_lo);
           }

@@ -70,6 +70,28 @@ SIGNATURES = {
     "genasis_hydro_set_option": [_P, _I, _I],
     "genasis_hydro_get_step_totals": [_P, _P],
     "genasis_hydro_step_noalloc": [ctypes.POINTER(Desc), _P, _P, _D],
+    "genasis_hydro_accumulate_face_flux": [_P, _I, _D, _P],
+    "genasis_hydro_restrict": [_P, _I, _P],
+    "genasis_learned_create": [ctypes.POINTER(Desc), ctypes.POINTER(_P)],
+    "genasis_learned_destroy": [_P],
+    "genasis_learned_set_params": [_P, _P],
+    "genasis_learned_set_limit": [_P, ctypes.c_float],
+    "genasis_learned_set_fct": [_P, _I],
+    "genasis_learned_step": [_P, ctypes.c_double],
+    "genasis_learned_set_primitive": [_P, _P, _P, _P],
+    "genasis_learned_set_conserved": [_P, _P],
+    "genasis_learned_get_conserved": [_P, _P],
+    "genasis_learned_advance": [_P, _I, _D, _D, _P],
+    "genasis_learned_fallbacks": [_P, _P],
+    "genasis_learned_features": [_P, _P, _P],
+    "genasis_learned_targets": [_P, _P, _P, _P, _P],
+    "genasis_mlp_param_count": [],
+    "genasis_mlp_forward": [_P, _P, ctypes.c_longlong, _P, _P],
+    "genasis_mlp_gradient": [_P, _P, _P, ctypes.c_longlong, _P, _P, _P],
+    "genasis_mlp_opt_create": [_P, _P, ctypes.POINTER(_P)],
+    "genasis_mlp_opt_destroy": [_P],
+    "genasis_mlp_opt_step": [_P, _P, _P, ctypes.c_longlong, ctypes.c_float, _P],
+    "genasis_mlp_opt_get_params": [_P, _P],
     "genasis_batch_create": [_I, _P, _I, _D, _I, _P, ctypes.POINTER(_P)],
     "genasis_batch_destroy": [_P],
     "genasis_batch_set_primitive": [_P, _I, _P, _P, _P],
@@ -264,6 +286,20 @@ class Hydro:
         check(load().genasis_hydro_profile_step(self._h, float(cfl), ms))
         return tuple(ms)
 
+    def accumulate_face_flux(self, F, stride=1, weight=1.0):
+        """Add the last step's effective RK2 face flux (averaged over `stride`
+        fine faces per coarse face) times `weight` into the CUDA float64
+        tensor F of shape (2, 4, ny/stride, nx/stride)."""
+        pf, _ = _ptr(F, np.float64, None, "F")
+        check(load().genasis_hydro_accumulate_face_flux(self._h, int(stride), float(weight), pf))
+
+    def restrict(self, out, factor):
+        """Conservative restriction of the state by `factor` into the CUDA
+        float32 tensor out of shape (4, ny/factor, nx/factor)."""
+        po, _ = _ptr(out, np.float32, None, "out")
+        check(load().genasis_hydro_restrict(self._h, int(factor), po))
+        return out
+
     def launches_per_step(self):
         return check(load().genasis_hydro_launches_per_step(self._h))
 
@@ -407,3 +443,166 @@ def step_noalloc(prob, U_in, U_out, dt, precision=FP64, solver=None, stream=None
     pin, a = _ptr(U_in, dt_, None, "U_in")
     pout, b = _ptr(U_out, dt_, None, "U_out")
     check(load().genasis_hydro_step_noalloc(ctypes.byref(d), pin, pout, float(dt)))
+
+
+def _desc(prob, precision, solver=None, stream=None):
+    d = Desc()
+    d.ndim = int(prob.ndim)
+    keep = [np.ascontiguousarray(prob.widths[q], dtype=np.float64) for q in range(prob.ndim)]
+    for q in range(3):
+        d.n[q] = int(prob.n[q]) if q < prob.ndim else 1
+        d.widths[q] = keep[q].ctypes.data if q < prob.ndim else None
+        d.bc_lo[q] = int(prob.bc_lo[q]) if q < prob.ndim else 0
+        d.bc_hi[q] = int(prob.bc_hi[q]) if q < prob.ndim else 0
+    d.gamma = float(prob.gamma)
+    d.solver = int(prob.solver if solver is None else solver)
+    d.theta = float(prob.theta)
+    d.precision = int(precision)
+    if stream is not None:
+        d.stream = stream if isinstance(stream, int) else int(getattr(stream, "cuda_stream", stream))
+    return d, keep
+
+
+def mlp_param_count():
+    return load().genasis_mlp_param_count()
+
+
+def mlp_forward(params, X, Y, stream=None):
+    """Y[n, 4] = network(X[n, 32] bf16); CUDA tensors."""
+    n = X.shape[0]
+    check(load().genasis_mlp_forward(params.data_ptr(), X.data_ptr(), int(n), Y.data_ptr(),
+                                     None if stream is None else int(getattr(stream, "cuda_stream", stream))))
+    return Y
+
+
+def mlp_gradient(params, X, T, grad, loss=None, stream=None):
+    n = X.shape[0]
+    check(load().genasis_mlp_gradient(params.data_ptr(), X.data_ptr(), T.data_ptr(), int(n), grad.data_ptr(),
+                                      None if loss is None else loss.data_ptr(),
+                                      None if stream is None else int(getattr(stream, "cuda_stream", stream))))
+    return grad
+
+
+class MlpOptimizer:
+    """Adam on a device copy of the network parameters (genasis_mlp_opt_t)."""
+
+    def __init__(self, params, stream=None):
+        p = np.ascontiguousarray(params, dtype=np.float32) if not hasattr(params, "data_ptr") else params
+        ptr = p.ctypes.data if isinstance(p, np.ndarray) else p.data_ptr()
+        self._h = ctypes.c_void_p()
+        check(load().genasis_mlp_opt_create(ptr, None if stream is None else int(getattr(stream, "cuda_stream", stream)),
+                                            ctypes.byref(self._h)))
+
+    def step(self, X, T, lr, want_loss=True):
+        loss = ctypes.c_float()
+        check(load().genasis_mlp_opt_step(self._h, X.data_ptr(), T.data_ptr(), int(X.shape[0]), float(lr),
+                                          ctypes.byref(loss) if want_loss else None))
+        return loss.value if want_loss else None
+
+    def params(self):
+        out = np.empty(mlp_param_count(), dtype=np.float32)
+        check(load().genasis_mlp_opt_get_params(self._h, out.ctypes.data))
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load().genasis_mlp_opt_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Learned:
+    """2D FP32 solver with the learned flux correction (genasis_learned_t)."""
+
+    def __init__(self, prob, params=None, solver=None, stream=None):
+        lib = load()
+        d, keep = _desc(prob, FP32_MIXED, solver, stream)
+        self._h = ctypes.c_void_p()
+        check(lib.genasis_learned_create(ctypes.byref(d), ctypes.byref(self._h)))
+        self.n = (int(prob.n[0]), int(prob.n[1]))
+        self.ncell = self.n[0] * self.n[1]
+        self.shape = (self.n[1], self.n[0])
+        self.set_params(params)
+
+    def set_params(self, params):
+        if params is None:
+            check(load().genasis_learned_set_params(self._h, None))
+            return
+        if hasattr(params, "data_ptr"):
+            check(load().genasis_learned_set_params(self._h, params.data_ptr()))
+        else:
+            p = np.ascontiguousarray(params, dtype=np.float32)
+            check(load().genasis_learned_set_params(self._h, p.ctypes.data))
+
+    def set_fct(self, enabled):
+        """Flux-corrected-transport limiting of the correction (default on)."""
+        check(load().genasis_learned_set_fct(self._h, int(bool(enabled))))
+
+    def set_limit(self, ylim):
+        """Clamp network outputs to [-ylim, ylim] (math.inf: no bound)."""
+        check(load().genasis_learned_set_limit(self._h, float(ylim)))
+
+    def set_primitive(self, rho, vel, p):
+        pr, a = _ptr(rho, np.float64, self.ncell, "rho")
+        pv, b = _ptr(vel, np.float64, 2 * self.ncell, "vel")
+        pp, c = _ptr(p, np.float64, self.ncell, "p")
+        check(load().genasis_learned_set_primitive(self._h, pr, pv, pp))
+
+    def set_conserved(self, U):
+        pu, keep = _ptr(U, np.float32, 4 * self.ncell, "U")
+        check(load().genasis_learned_set_conserved(self._h, pu))
+
+    def get_conserved(self, out=None):
+        if out is None:
+            out = np.empty((4,) + self.shape, dtype=np.float32)
+        po, _ = _ptr(out, np.float32, 4 * self.ncell, "out")
+        check(load().genasis_learned_get_conserved(self._h, po))
+        return out
+
+    def advance(self, nsteps, cfl, t_end=0.0, sync=True):
+        t = ctypes.c_double()
+        check(load().genasis_learned_advance(self._h, int(nsteps), float(cfl), float(t_end),
+                                             ctypes.byref(t) if sync else None))
+        return t.value if sync else None
+
+    def step(self, dt):
+        """One corrected RK2 step with a given dt (asynchronous)."""
+        check(load().genasis_learned_step(self._h, float(dt)))
+
+    def evolve(self, cfl, t_end, chunk=64, max_chunks=1 << 30):
+        """Advance to t_end (the last step clamped); stops early after
+        max_chunks calls of `chunk` steps and returns the time reached."""
+        t = 0.0
+        for _ in range(max_chunks):
+            if t >= t_end:
+                break
+            t = self.advance(chunk, cfl, t_end)
+        return t
+
+    def fallbacks(self):
+        v = ctypes.c_longlong()
+        check(load().genasis_learned_fallbacks(self._h, ctypes.byref(v)))
+        return v.value
+
+    def features(self, X, scale):
+        check(load().genasis_learned_features(self._h, X.data_ptr(), scale.data_ptr()))
+
+    def targets(self, f_target, f_plain, scale, T):
+        check(load().genasis_learned_targets(self._h, f_target.data_ptr(), f_plain.data_ptr(), scale.data_ptr(),
+                                             T.data_ptr()))
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load().genasis_learned_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

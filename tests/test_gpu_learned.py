@@ -1,0 +1,318 @@
+"""Learned flux correction on the GPU: tensor-core MLP forward and gradients
+against the FP64 reference (exactly emulating the BF16 rounding the kernels
+store, and against plain FP64), Adam training that fits a teacher network, the
+corrected solver against the reference corrected step, its conservation and
+positivity fallback, and the exactness of the training-target construction
+(the accumulated effective fluxes reproduce the state change)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import mlp as M
+from paper_1207_3392_gb300 import hydro as H
+from paper_1207_3392_gb300 import problems as P
+from parity_util import TOL_FP32, oracle_run, rel_l1
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1207_3392_gb300 import build
+    build.build()
+
+
+def _dev(x, dtype):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x)).to(dtype=dtype, device="cuda")
+
+
+def _x_bf16(X):
+    import torch
+    Xp = np.zeros((X.shape[0], 32))
+    Xp[:, :24] = X
+    return _dev(Xp, torch.float32).to(torch.bfloat16).contiguous()
+
+
+def _random_net(seed, last=0.3):
+    rng = np.random.default_rng(seed)
+    th = M.init_params(seed)
+    th[-(M.NOUT * M.NH + M.NOUT):] = rng.normal(0, last, M.NOUT * M.NH + M.NOUT)
+    th[M.NH * M.NIN:M.NH * M.NIN + M.NH] = rng.normal(0, 0.1, M.NH)
+    return th.astype(np.float32).astype(np.float64)
+
+
+def _rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b))
+
+
+def test_mlp_forward_matches_reference():
+    import torch
+    rng = np.random.default_rng(1)
+    th = _random_net(2)
+    n = 1003  # not a multiple of 16
+    X = M.bf16(rng.normal(0, 0.7, (n, 24)))
+    Y = torch.empty((n, 4), device="cuda")
+    H.mlp_forward(_dev(th, torch.float32), _x_bf16(X), Y)
+    Yg = Y.cpu().numpy().astype(np.float64)
+    Ye, _ = M.forward(th, X, emulate_bf16=True)
+    Yf, _ = M.forward(th, X)
+    assert _rel(Yg, Ye) < 3e-3
+    assert _rel(Yg, Yf) < 3e-2
+
+
+def _emulated_grad(th, X, T):
+    """Gradient with the kernels' BF16 storage points emulated in FP64."""
+    P_ = M.unpack(th)
+    r = M.bf16
+    Xb = r(X)
+    z1 = Xb @ r(P_["W1"]).T + P_["b1"]
+    h1 = r(M.silu(z1))
+    z2 = h1 @ r(P_["W2"]).T + P_["b2"]
+    h2 = r(M.silu(z2))
+    Y = h2 @ r(P_["W3"]).T + P_["b3"]
+    n = X.shape[0]
+    dy = r(2.0 * (Y - T) / (4 * n))
+    dz2 = r((dy @ r(P_["W3"])) * M.dsilu(z2))
+    dz1 = r((dz2 @ r(P_["W2"])) * M.dsilu(z1))
+    g = {"W3": dy.T @ h2, "b3": dy.sum(0), "W2": dz2.T @ h1, "b2": dz2.sum(0), "W1": dz1.T @ Xb, "b1": dz1.sum(0)}
+    return M.pack(g), float(np.sum((Y - T) ** 2))
+
+
+def test_mlp_gradient_matches_reference():
+    import torch
+    rng = np.random.default_rng(3)
+    th = _random_net(4)
+    n = 517
+    X = M.bf16(rng.normal(0, 0.7, (n, 24)))
+    T = rng.normal(0, 0.3, (n, 4))
+    g = torch.empty(M.NPARAM, device="cuda")
+    loss = torch.empty(1, device="cuda")
+    H.mlp_gradient(_dev(th, torch.float32), _x_bf16(X), _dev(T, torch.float32), g, loss)
+    gg = g.cpu().numpy().astype(np.float64)
+    ge, le = _emulated_grad(th, X, T)
+    gf = M.grad(th, X, T)
+    o = 0
+    for name, shp in M.SHAPES:
+        k = int(np.prod(shp))
+        assert _rel(gg[o:o + k], ge[o:o + k]) < 2e-2, name
+        assert _rel(gg[o:o + k], gf[o:o + k]) < 8e-2, name
+        o += k
+    assert _rel(gg, ge) < 1e-2
+    assert float(loss.item()) == pytest.approx(le, rel=2e-3)
+
+
+def test_adam_training_fits_a_teacher():
+    import torch
+    rng = np.random.default_rng(5)
+    teacher = _random_net(6, last=0.5)
+    n = 8192
+    X = M.bf16(rng.normal(0, 0.7, (n, 24)))
+    T, _ = M.forward(teacher, X)
+    Xd, Td = _x_bf16(X), _dev(T, torch.float32)
+    opt = H.MlpOptimizer(M.init_params(7).astype(np.float32))
+    first = opt.step(Xd, Td, 3e-3)
+    for _ in range(400):
+        last = opt.step(Xd, Td, 3e-3)
+    opt.close()
+    assert last < 0.05 * first
+
+
+def test_learned_solver_without_network_matches_oracle():
+    pr = P.kelvin_helmholtz(64, seed=5)
+    L = H.Learned(pr)
+    L.set_primitive(pr.rho, pr.vel, pr.p)
+    L.advance(30, 0.5)
+    Ug = L.get_conserved().astype(np.float64)
+    L.close()
+    Uo, _ = oracle_run(pr, steps=30)
+    assert np.all(rel_l1(Ug, Uo, 2) <= TOL_FP32)
+
+
+def test_learned_solver_matches_reference_corrected_step():
+    pr = P.kelvin_helmholtz(48, seed=2)
+    th = _random_net(8, last=0.02)
+    L = H.Learned(pr, params=th.astype(np.float32))
+    L.set_fct(False)
+    L.set_primitive(pr.rho, pr.vel, pr.p)
+    g = O.Grid(pr)
+    U = O.initial_state(pr, g)
+    for _ in range(3):
+        dt = 0.5 * O.cfl_dt(g, U)
+        U, _ = M.corrected_step(O, g, U, dt, th, emulate_bf16=True)
+    L.advance(3, 0.5)
+    Ug = L.get_conserved().astype(np.float64)
+    assert L.fallbacks() == 0
+    L.close()
+    assert np.all(rel_l1(Ug, U, 2) <= 1e-4), rel_l1(Ug, U, 2)
+    # and it differs from the plain scheme by much more than that
+    Up, _ = oracle_run(pr, steps=3)
+    assert np.max(rel_l1(Ug, Up, 2)) > 1e-3
+
+
+def test_learned_solver_output_limit_matches_reference():
+    """The output bound clamps the network before scaling, on the GPU as in
+    the reference corrected step."""
+    pr = P.kelvin_helmholtz(48, seed=7)
+    th = _random_net(10, last=0.2)
+    lim = 0.004
+    L = H.Learned(pr, params=th.astype(np.float32))
+    L.set_fct(False)
+    L.set_limit(lim)
+    L.set_primitive(pr.rho, pr.vel, pr.p)
+    g = O.Grid(pr)
+    U = O.initial_state(pr, g)
+    for _ in range(3):
+        dt = 0.5 * O.cfl_dt(g, U)
+        U, _ = M.corrected_step(O, g, U, dt, th, emulate_bf16=True, ylim=lim)
+    L.advance(3, 0.5)
+    Ug = L.get_conserved().astype(np.float64)
+    L.close()
+    assert np.all(rel_l1(Ug, U, 2) <= 1e-4), rel_l1(Ug, U, 2)
+
+
+def test_learned_solver_conserves_and_falls_back():
+    pr = P.kelvin_helmholtz(64, seed=3)
+    th = _random_net(9, last=0.0)
+    th[M.NPARAM - 4] = 40.0   # b3[0]: a huge mass-flux correction on every face
+    L = H.Learned(pr, params=th.astype(np.float32))
+    L.set_fct(False)          # the limiter alone would keep every cell valid
+    L.set_primitive(pr.rho, pr.vel, pr.p)
+    U0 = L.get_conserved().astype(np.float64)
+    L.advance(5, 0.5)
+    U1 = L.get_conserved().astype(np.float64)
+    assert L.fallbacks() > 0
+    rho = U1[0]
+    e = U1[3] - 0.5 * (U1[1] ** 2 + U1[2] ** 2) / rho
+    assert rho.min() > 0 and e.min() > 0
+    np.testing.assert_allclose(U1.sum(axis=(1, 2)), U0.sum(axis=(1, 2)), rtol=2e-6, atol=1e-3)
+    L.close()
+
+
+def test_fct_limited_solver_matches_reference():
+    """Flux-corrected transport on the correction: the GPU step against the
+    reference FCT step, for a network whose raw correction is large."""
+    pr = P.kelvin_helmholtz(48, seed=11)
+    th = _random_net(12, last=0.3)
+    L = H.Learned(pr, params=th.astype(np.float32))
+    L.set_primitive(pr.rho, pr.vel, pr.p)
+    g = O.Grid(pr)
+    U = O.initial_state(pr, g)
+    for _ in range(3):
+        dt = 0.5 * O.cfl_dt(g, U)
+        U = M.fct_step(O, g, U, dt, th, emulate_bf16=True)
+    L.advance(3, 0.5)
+    Ug = L.get_conserved().astype(np.float64)
+    assert L.fallbacks() == 0
+    L.close()
+    err = rel_l1(Ug, U, 2)
+    assert np.all(err <= 1e-4), err
+    # the limited correction still moves the state, by far more than the error
+    Up, _ = oracle_run(pr, steps=3)
+    diff = rel_l1(U, Up, 2)
+    assert np.max(diff) > 3e-4 and np.max(err) < 0.1 * np.max(diff), (err, diff)
+
+
+def test_fixed_dt_step_matches_reference():
+    """genasis_learned_step takes the caller's dt."""
+    pr = P.kelvin_helmholtz(32, seed=13)
+    th = _random_net(14, last=0.3)
+    L = H.Learned(pr, params=th.astype(np.float32))
+    L.set_primitive(pr.rho, pr.vel, pr.p)
+    g = O.Grid(pr)
+    U = O.initial_state(pr, g)
+    dt = 0.4 * O.cfl_dt(g, U)
+    for _ in range(2):
+        L.step(dt)
+        U = M.fct_step(O, g, U, dt, th, emulate_bf16=True)
+    Ug = L.get_conserved().astype(np.float64)
+    L.close()
+    err = rel_l1(Ug, U, 2)
+    assert np.all(err <= 1e-4), err
+
+
+def test_fct_keeps_an_aggressive_network_valid():
+    """With the limiter on, a huge constant mass-flux correction is cut back so
+    that no cell needs the fallback, totals are conserved and the state stays
+    physical."""
+    pr = P.kelvin_helmholtz(64, seed=3)
+    th = _random_net(9, last=0.0)
+    th[M.NPARAM - 4] = 40.0
+    L = H.Learned(pr, params=th.astype(np.float32))
+    L.set_primitive(pr.rho, pr.vel, pr.p)
+    U0 = L.get_conserved().astype(np.float64)
+    L.advance(5, 0.5)
+    U1 = L.get_conserved().astype(np.float64)
+    assert L.fallbacks() == 0
+    rho = U1[0]
+    e = U1[3] - 0.5 * (U1[1] ** 2 + U1[2] ** 2) / rho
+    assert rho.min() > 0 and e.min() > 0
+    np.testing.assert_allclose(U1.sum(axis=(1, 2)), U0.sum(axis=(1, 2)), rtol=2e-6, atol=1e-3)
+    L.close()
+
+
+def test_features_and_targets_match_reference():
+    import torch
+    pr = P.kelvin_helmholtz(32, seed=4)
+    L = H.Learned(pr)
+    L.set_primitive(pr.rho, pr.vel, pr.p)
+    nc = 32 * 32
+    X = torch.empty((2 * nc, 32), dtype=torch.bfloat16, device="cuda")
+    sc = torch.empty((2 * nc, 4), device="cuda")
+    L.features(X, sc)
+    Xg = X.float().cpu().numpy()[:, :24].reshape(2, 32, 32, 24)
+    for axis in (0, 1):
+        Xo, so = M.face_features(pr.rho, pr.vel[0], pr.vel[1], pr.p, pr.gamma, axis)
+        assert np.max(np.abs(Xg[axis] - Xo)) < 1.5e-2 * max(1.0, np.abs(Xo).max())
+        np.testing.assert_allclose(sc.cpu().numpy().reshape(2, 32, 32, 4)[axis], so, rtol=2e-6)
+    rng = np.random.default_rng(0)
+    ft = rng.normal(size=(2, 4, 32, 32))
+    fp = rng.normal(size=(2, 4, 32, 32))
+    T = torch.empty((2 * nc, 4), device="cuda")
+    L.targets(_dev(ft, torch.float64), _dev(fp, torch.float64), sc, T)
+    Tg = T.cpu().numpy().reshape(2, 32, 32, 4)
+    s = sc.cpu().numpy().reshape(2, 32, 32, 4).astype(np.float64)
+    d = np.moveaxis(ft - fp, 1, -1)          # [axis, j, i, conserved var]
+    want = np.empty_like(d)
+    want[0] = d[0] / s[0]                    # x faces: normal momentum is S_x
+    want[1] = d[1][..., [0, 2, 1, 3]] / s[1]  # y faces: normal momentum is S_y
+    np.testing.assert_allclose(Tg, want, rtol=1e-6, atol=1e-6)
+    L.close()
+
+
+@pytest.mark.parametrize("stride", [1, 4])
+def test_accumulated_fluxes_reproduce_the_state_change(stride):
+    """Sum over steps of the accumulated effective face fluxes, differenced,
+    equals the (restricted) state change: interior fine faces cancel."""
+    import torch
+    n = 64
+    pr = P.kelvin_helmholtz(n, seed=6)
+    h = H.Hydro.from_problem(pr, precision=H.FP32_MIXED)
+    nc = n // stride
+    U0 = torch.empty((4, nc, nc), device="cuda")
+    h.restrict(U0, stride)
+    F = torch.zeros((2, 4, nc, nc), dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()  # the handle runs on its own stream
+    dt = 0.5 * h.compute_dt(0.5)
+    for _ in range(stride):
+        h.step(dt)
+        h.accumulate_face_flux(F, stride, 1.0)
+    U1 = torch.empty((4, nc, nc), device="cuda")
+    h.restrict(U1, stride)
+    h.close()
+    Fx, Fy = F[0].cpu().numpy(), F[1].cpu().numpy()
+    dxc = 1.0 / nc
+    div = (np.roll(Fx, -1, axis=2) - Fx) / dxc + (np.roll(Fy, -1, axis=1) - Fy) / dxc
+    dU = (U1.double() - U0.double()).cpu().numpy()
+    np.testing.assert_allclose(dU, -dt * div, rtol=0, atol=2e-5 * np.abs(U0.cpu().numpy()).max())
+
+
+def test_targets_vanish_when_fine_equals_coarse():
+    """With a 'fine' run at the coarse resolution (factor 1) the target flux is
+    the plain flux itself, so every training target is zero up to rounding."""
+    from paper_1207_3392_gb300 import learned_flux as LF
+    X, T = LF.generate([0], n_coarse=64, factor=1, t_end=0.02, snap_every=1, keep_fraction=1.0)
+    assert T.shape[0] > 0
+    assert float(T.abs().max()) < 1e-5

@@ -68,3 +68,61 @@ def test_face_features_symmetry_and_scaling():
     # the stencil of face (j, i) along x is cells i-3 .. i+2 of row j
     j, i = 5, 7
     np.testing.assert_allclose(Xx[j, i, 0::4] + 1.0, rho[j, i - 3:i + 3] / rho[j, i - 3:i + 3].mean(), rtol=1e-14)
+
+
+def _kh_state(n=16, seed=1):
+    import oracle as O
+    from paper_1207_3392_gb300 import problems as P
+    pr = P.kelvin_helmholtz(n, seed=seed)
+    g = O.Grid(pr)
+    return O, pr, g, O.initial_state(pr, g)
+
+
+def test_corrected_step_with_zero_network_is_the_plain_step():
+    O, pr, g, U = _kh_state()
+    theta = M.init_params(5)  # last layer zero: the network outputs 0
+    dt = 0.4 * O.cfl_dt(g, U)
+    Uc, flagged = M.corrected_step(O, g, U, dt, theta)
+    np.testing.assert_allclose(Uc, O.step(g, U, dt), rtol=0, atol=1e-14 * np.abs(U).max())
+    assert flagged == 0
+
+
+def test_corrected_step_conserves_totals():
+    O, pr, g, U = _kh_state()
+    rng = np.random.default_rng(9)
+    theta = M.init_params(6)
+    theta[-(M.NOUT * M.NH + M.NOUT):] = rng.normal(0, 0.05, M.NOUT * M.NH + M.NOUT)
+    dt = 0.4 * O.cfl_dt(g, U)
+    Uc, _ = M.corrected_step(O, g, U, dt, theta)
+    np.testing.assert_allclose(O.totals(g, Uc), O.totals(g, U), rtol=0, atol=1e-13)
+    assert np.abs(Uc - O.step(g, U, dt)).max() > 1e-6  # the correction does something
+
+
+def test_fct_step_keeps_local_bounds_and_conserves():
+    """With an aggressive correction the FCT-limited step keeps every conserved
+    variable within the stage bounds (so density stays positive) and is
+    conservative; with a zero network it is the plain step."""
+    O, pr, g, U = _kh_state(24, seed=3)
+    dt = 0.4 * O.cfl_dt(g, U)
+    theta = M.init_params(5)
+    np.testing.assert_allclose(M.fct_step(O, g, U, dt, theta), O.step(g, U, dt), rtol=0, atol=1e-13)
+    rng = np.random.default_rng(1)
+    theta[-(M.NOUT * M.NH + M.NOUT):] = rng.normal(0, 2.0, M.NOUT * M.NH + M.NOUT)
+    Un = M.fct_step(O, g, U, dt, theta)
+    np.testing.assert_allclose(O.totals(g, Un), O.totals(g, U), rtol=0, atol=1e-12)
+    assert Un[0].min() > 0
+    # the unlimited corrected step with the same network leaves the bounds
+    Uu, _ = M.corrected_step(O, g, U, dt, theta)
+    assert Uu[0].min() < U[0].min() - 1e-3 or Uu[0].max() > U[0].max() + 1e-3
+    # first stage alone: every variable inside [min, max] of U_L and U over neighbours
+    wx, wy = np.asarray(g.widths[0]), np.asarray(g.widths[1])
+    Fx, Fy, dfx, dfy = M._corrections(O, g, U, theta, False, np.inf)
+    Cx, Cy = M.fct_factors(U, U, Fx, Fy, dfx, dfy, dt, wx, wy)
+    assert Cx.min() >= 0 and Cx.max() <= 1 and Cy.min() >= 0 and Cy.max() <= 1
+    div = lambda a, b: (a[:, :, 1:] - a[:, :, :-1]) / wx[None, None, :] + (b[:, 1:, :] - b[:, :-1, :]) / wy[None, :, None]
+    UL = U - dt * div(Fx, Fy)
+    U1 = U - dt * div(Fx + Cx[None] * dfx, Fy + Cy[None] * dfy)
+    hi, _ = M._neighbour_extrema(np.maximum(UL, U))
+    _, lo = M._neighbour_extrema(np.minimum(UL, U))
+    tol = 1e-12 * np.abs(U).max()
+    assert np.all(U1 <= hi + tol) and np.all(U1 >= lo - tol)
