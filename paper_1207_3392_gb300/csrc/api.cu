@@ -42,7 +42,9 @@ bool is_device_ptr(const void* p) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
-int tile_count(int ndim) { return ndim == 1 ? tile_count_1d() : ndim == 2 ? tile_count_2d() : tile_count_3d(); }
+int tile_count(int ndim, bool fp64) {
+  return ndim == 1 ? tile_count_1d() : ndim == 2 ? tile_count_2d() : fp64 ? tile_count_3d_f64() : tile_count_3d_f32();
+}
 
 bool stage_variant(int ndim, bool fp64, int solver, int stage, int tile, StageVariant* out) {
   if (ndim == 1) return stage_variant_1d(fp64, solver, stage, tile, out);
@@ -50,7 +52,7 @@ bool stage_variant(int ndim, bool fp64, int solver, int stage, int tile, StageVa
   return fp64 ? stage_variant_3d_f64(solver, stage, tile, out) : stage_variant_3d_f32(solver, stage, tile, out);
 }
 
-int stage_tile_count(int ndim) { return tile_count(ndim); }
+int stage_tile_count(int ndim, bool fp64) { return tile_count(ndim, fp64); }
 
 }  // namespace gh
 
@@ -128,7 +130,7 @@ int upload_geometry(genasis_hydro* h, const genasis_hydro_desc* d) {
     std::vector<double> e = extended_widths(w.data(), n < 2 ? 2 : n, h->bc_lo[q], h->bc_hi[q]);
     std::vector<Geo<T>> geo;
     std::vector<T> iw;
-    append_geometry<T>(e, geo, iw);
+    append_geometry<T>(e, h->theta, geo, iw);
     GH_CK(cudaMalloc(&h->geo[q], geo.size() * sizeof(Geo<T>)));
     GH_CK(cudaMalloc(&h->iw[q], iw.size() * sizeof(T)));
     GH_CK(cudaMalloc(&h->wd[q], w.size() * sizeof(double)));
@@ -150,7 +152,7 @@ int upload_geometry(genasis_hydro* h, const genasis_hydro_desc* d) {
 }
 
 int configure(genasis_hydro* h, int tile, int kchunk_req) {
-  if (tile < 0 || tile >= tile_count(h->ndim)) return fail(GENASIS_EINVAL, "tile %d out of range", tile);
+  if (tile < 0 || tile >= tile_count(h->ndim, h->prec == GENASIS_FP64)) return fail(GENASIS_EINVAL, "tile %d out of range", tile);
   StageVariant v1, v2;
   const bool fp64 = h->prec == GENASIS_FP64;
   if (!stage_variant(h->ndim, fp64, h->solver, 1, tile, &v1) || !stage_variant(h->ndim, fp64, h->solver, 2, tile, &v2))
@@ -226,7 +228,6 @@ StageArgs<T> stage_args(genasis_hydro* h, int stage) {
   }
   A.gamma = (T)h->gamma;
   A.gm1 = (T)(h->gamma - 1.0);
-  A.theta = (T)h->theta;
   A.un = (const T*)h->U[h->cur];
   A.k1 = (const T*)h->K;
   A.out = stage == 1 ? (T*)h->K : (T*)h->U[1 - h->cur];
@@ -615,7 +616,7 @@ int genasis_hydro_get_tile(genasis_hydro_t h, int* info) {
   info[2] = h->v1.ty;
   info[3] = h->kchunk;
   info[4] = (int)(h->grid.x * h->grid.y * h->grid.z);
-  info[5] = tile_count(h->ndim);
+  info[5] = tile_count(h->ndim, h->prec == GENASIS_FP64);
   return GENASIS_OK;
 }
 
@@ -655,7 +656,6 @@ static int mesh2_of(genasis_hydro* h, Mesh2* M) {
   }
   M->gamma = (float)h->gamma;
   M->gm1 = (float)(h->gamma - 1.0);
-  M->theta = (float)h->theta;
   return GENASIS_OK;
 }
 
@@ -730,7 +730,7 @@ int genasis_hydro_autotune(genasis_hydro_t h, int trial_steps, const char* cache
         }
       }
       fclose(f);
-      if (tile >= 0 && tile < tile_count(h->ndim)) return configure(h, tile, kc);
+      if (tile >= 0 && tile < tile_count(h->ndim, h->prec == GENASIS_FP64)) return configure(h, tile, kc);
     }
   }
   // save state, time, status
@@ -748,7 +748,7 @@ int genasis_hydro_autotune(genasis_hydro_t h, int trial_steps, const char* cache
   int best_tile = 0, best_kc = 0;
   int rc = GENASIS_OK;
   const int nm = h->ndim >= 2 ? h->n[h->ndim - 1] : 1;
-  for (int tile = 0; tile < tile_count(h->ndim) && !rc; ++tile) {
+  for (int tile = 0; tile < tile_count(h->ndim, h->prec == GENASIS_FP64) && !rc; ++tile) {
     std::vector<int> kcs = {0};
     if (h->ndim >= 2)
       for (int kc : {12, 16, 24, 32, 48, 64})

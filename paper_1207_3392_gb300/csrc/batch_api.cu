@@ -113,7 +113,7 @@ int upload_tables(genasis_batch* b, const genasis_batch_problem* probs) {
       d.goff[q] = h.goff[q];
       d.woff[q] = h.woff[q];
       if (q < h.ndim) {
-        append_geometry<T>(extended_widths(probs[p].widths[q], h.n[q], h.bc_lo[q], h.bc_hi[q]), geo, iw);
+        append_geometry<T>(extended_widths(probs[p].widths[q], h.n[q], h.bc_lo[q], h.bc_hi[q]), b->theta, geo, iw);
         wd.insert(wd.end(), probs[p].widths[q], probs[p].widths[q] + h.n[q]);
       }
     }
@@ -200,7 +200,6 @@ BatchArgs<T> batch_args(genasis_batch* b, int stage, unsigned* counter) {
   A.dt = b->dt;
   A.speed = b->speed;
   A.status = b->status;
-  A.theta = (T)b->theta;
   A.kchunk = b->chunk;
   return A;
 }

@@ -40,7 +40,6 @@ struct BatchArgs {
   const double* dt;         // per-problem dt
   unsigned long long* speed;  // per-problem max CFL speed (FP64 bit pattern; stage 1)
   unsigned* status;         // per-problem status
-  T theta;
   int kchunk;               // planes (rows) per 2D item
 };
 
@@ -74,7 +73,6 @@ struct BatchKernel {
     }
     A.gamma = P.gamma;
     A.gm1 = P.gm1;
-    A.theta = B.theta;
     A.un = B.un + P.off;
     A.k1 = B.k1 + P.off;
     A.out = B.out + P.off;

@@ -24,18 +24,20 @@ inline std::vector<double> extended_widths(const double* w, int n, int lo, int h
 
 // Reconstruction geometry (Eq. MinMod with centre distances of a non-uniform
 // Cartesian mesh): q_c - q_- = (d_{c-1} + d_c)/2, q_+ - q_- = d_{c-1}/2 + d_c +
-// d_{c+1}/2, q_+ - q_c = (d_c + d_{c+1})/2, face offset d_c / 2; plus inverse
-// widths.  Appends one entry per extended cell.
+// d_{c+1}/2, q_+ - q_c = (d_c + d_{c+1})/2, face offset d_c / 2, with the
+// limiter parameter theta folded into the one-sided inverse distances; plus
+// inverse widths.  Appends one entry per extended cell.
 template <class T>
-inline void append_geometry(const std::vector<double>& e, std::vector<Geo<T>>& geo, std::vector<T>& iw) {
+inline void append_geometry(const std::vector<double>& e, double theta, std::vector<Geo<T>>& geo,
+                            std::vector<T>& iw) {
   const int m = (int)e.size();
   for (int k = 0; k < m; ++k) {
     const double dc = e[k];
     const double dm = e[k > 0 ? k - 1 : 0], dp = e[k + 1 < m ? k + 1 : m - 1];
     Geo<T> g;
-    g.icm = (T)(1.0 / (0.5 * (dm + dc)));
+    g.ticm = (T)(theta / (0.5 * (dm + dc)));
     g.ipm = (T)(1.0 / (0.5 * dm + dc + 0.5 * dp));
-    g.ipc = (T)(1.0 / (0.5 * (dc + dp)));
+    g.tipc = (T)(theta / (0.5 * (dc + dp)));
     g.h = (T)(0.5 * dc);
     geo.push_back(g);
     iw.push_back((T)(1.0 / dc));

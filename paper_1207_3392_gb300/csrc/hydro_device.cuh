@@ -15,12 +15,12 @@ enum : int { SOLVER_HLL = 0, SOLVER_HLLC = 1 };
 enum : unsigned { STATUS_NONPHYS = 1u, STATUS_TIMEOUT = 2u };
 
 // Per-cell reconstruction geometry along one axis (Eq. MinMod with
-// non-uniform centre distances): inverse distances centre-to-left-centre,
-// left-to-right centre, centre-to-right-centre, and the half width (face
-// offset from the geometric centre).
+// non-uniform centre distances): theta / (q_c - q_-), 1 / (q_+ - q_-),
+// theta / (q_+ - q_c), and the half width (face offset from the geometric
+// centre).  The limiter parameter theta is folded into the one-sided terms.
 template <class T>
 struct __align__(sizeof(T) * 4) Geo {
-  T icm, ipm, ipc, h;
+  T ticm, ipm, tipc, h;
 };
 
 // Ghost-cell source along one axis: periodic wrap, reflecting mirror (normal
@@ -51,10 +51,10 @@ __device__ __forceinline__ T minmod3(T a, T b, T c) {
   return lo > T(0) ? lo : (hi < T(0) ? hi : T(0));
 }
 
-// Limited slope of cell c from its neighbours (Eq. MinMod).
+// Limited slope of cell c from its neighbours (Eq. MinMod; theta is in g).
 template <class T>
-__device__ __forceinline__ T limited_slope(T wm, T wc, T wp, const Geo<T>& g, T theta) {
-  return minmod3(theta * ((wc - wm) * g.icm), (wp - wm) * g.ipm, theta * ((wp - wc) * g.ipc));
+__device__ __forceinline__ T limited_slope(T wm, T wc, T wp, const Geo<T>& g) {
+  return minmod3((wc - wm) * g.ticm, (wp - wm) * g.ipm, (wp - wc) * g.tipc);
 }
 
 // Division, reciprocal and square root used by the flux arithmetic.  FP64

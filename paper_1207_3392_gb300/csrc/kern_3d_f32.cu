@@ -3,10 +3,11 @@
 
 namespace gh {
 
-int tile_count_3d() { return 4; }
+int tile_count_3d_f32() { return 6; }
 
 // Register caps: 256-thread tiles at 3 CTAs per SM and 128-thread tiles at 6
-// (80 registers, 24 resident warps); tile 3 keeps the uncapped allocation.
+// (80 registers, 24 resident warps); tile 3 keeps the uncapped allocation;
+// tiles 4 and 5 (512 threads) are in kern_3d_f32_wide.cu.
 bool stage_variant_3d_f32(int solver, int stage, int tile, StageVariant* out) {
   switch (tile) {
     case 0: return pick_variant<3, float, 32, 8, 3>(solver, stage, out);
@@ -14,7 +15,7 @@ bool stage_variant_3d_f32(int solver, int stage, int tile, StageVariant* out) {
     case 2: return pick_variant<3, float, 64, 4, 3>(solver, stage, out);
     case 3: return pick_variant<3, float, 32, 8, 2>(solver, stage, out);
   }
-  return false;
+  return stage_variant_3d_f32_wide(solver, stage, tile, out);
 }
 
 }  // namespace gh

@@ -3,6 +3,8 @@
 
 namespace gh {
 
+int tile_count_3d_f64() { return 4; }
+
 bool stage_variant_3d_f64(int solver, int stage, int tile, StageVariant* out) {
   switch (tile) {
     case 0: return pick_variant<3, double, 32, 8>(solver, stage, out);

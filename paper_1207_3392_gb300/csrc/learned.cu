@@ -21,11 +21,18 @@ namespace gh {
 
 // ============================================================== MLP kernels
 
-// Y[n][4] = net(X[n][32]); one warp per 16 samples, weights in shared memory.
-__global__ void __launch_bounds__(256) mlp_infer_kernel(const float* __restrict__ P, const __nv_bfloat16* __restrict__ X,
-                                                        long long n, float* __restrict__ Y) {
-  __shared__ mlp::Weights W;
-  mlp::load_weights(W, P);
+// BF16 image of the forward-pass weights (one CTA).
+__global__ void __launch_bounds__(256) mlp_pack_kernel(const float* __restrict__ P, mlp::InferWeights* __restrict__ out) {
+  mlp::fill_layers(*out, P);
+}
+
+// Y[n][4] = net(X[n][32]); one warp per 16 samples, weights (a prepared
+// image) in shared memory; a persistent grid loops over the 16-sample tiles.
+__global__ void __launch_bounds__(256) mlp_infer_kernel(const mlp::InferWeights* __restrict__ Wg,
+                                                        const __nv_bfloat16* __restrict__ X, long long n,
+                                                        float* __restrict__ Y) {
+  __shared__ mlp::InferWeights W;
+  mlp::copy_weights(W, Wg);
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
   const long long ntile = (n + 15) / 16;
@@ -46,6 +53,18 @@ __global__ void __launch_bounds__(256) mlp_infer_kernel(const float* __restrict_
       }
     }
   }
+}
+
+// Inference over n samples with a persistent grid of up to 4 CTAs per SM.
+cudaError_t launch_mlp_infer(const mlp::InferWeights* W, const __nv_bfloat16* X, long long n, float* Y,
+                             cudaStream_t st) {
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const long long tiles = (n + 15) / 16, want = (tiles + 7) / 8, cap = 4LL * sms;
+  mlp_infer_kernel<<<(int)(want < cap ? want : cap), 256, 0, st>>>(W, X, n, Y);
+  return cudaGetLastError();
 }
 
 constexpr int TS = 128;            // samples per CTA iteration in training (8 warps x 16)
@@ -308,7 +327,8 @@ struct UpdateArgs {
   int stage;
   int fixup;                    // 0: corrected pass; k > 0: k-th widening pass; -1: all-plain pass
   int last;                     // last widening pass: remaining failures request the all-plain pass
-  unsigned* all_plain;          // device flag: redo the whole stage with plain fluxes
+  unsigned* all_plain;          // device flags: [0] redo the whole stage with plain fluxes,
+                                // [1] some cell failed in the corrected pass of this stage
   float ylim;                   // network outputs are clamped to [-ylim, ylim]
   const float* R;               // FCT ratios [8][ncell] (R+ then R- per variable), or null
 };
@@ -450,7 +470,8 @@ __global__ void lf_update_kernel(UpdateArgs A) {
   const long long ncell = (long long)M.nx * M.ny;
   const long long nxf = (long long)(M.nx + 1) * M.ny, nf = nxf + (long long)M.nx * (M.ny + 1);
   const float dt = (float)*A.dtp;
-  if (A.fixup < 0 && *A.all_plain == 0u) return;
+  if (A.fixup < 0 && A.all_plain[0] == 0u) return;
+  if (A.fixup > 0 && A.all_plain[1] == 0u) return;  // nothing to widen
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell; c += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(c % M.nx), j = (int)(c / M.nx);
     bool cl = true, cr = true, cb = true, ct = true, me = false;
@@ -493,12 +514,15 @@ __global__ void lf_update_kernel(UpdateArgs A) {
     const bool ok = w[0] > 0.f && M.gm1 * w[3] > 0.f && fabsf(w[1]) < INFINITY && fabsf(w[2]) < INFINITY;
     if (A.fixup == 0) {
       A.flag_out[c] = ok ? 0 : 1;
-      if (!ok) atomicAdd(A.nfallback, 1ull);
+      if (!ok) {
+        atomicAdd(A.nfallback, 1ull);
+        atomicOr(A.all_plain + 1, 1u);
+      }
     } else if (A.fixup > 0) {
       // flags only grow: a flagged cell stays plain, a newly failing one joins
       A.flag_out[c] = (me || !ok) ? 1 : 0;
       if (!ok && me) atomicOr(A.status, STATUS_NONPHYS);  // all its faces are plain already
-      if (!ok && A.last) atomicOr(A.all_plain, 1u);
+      if (!ok && A.last) atomicOr(A.all_plain, 1u);  // flag [0]
     } else if (!ok) {
       atomicOr(A.status, STATUS_NONPHYS);  // the plain scheme itself fails
     }
@@ -685,10 +709,13 @@ int genasis_mlp_forward(const float* params, const void* X, long long n, float* 
     return fail(GENASIS_EINVAL, "mlp_forward: params, X and Y must be device pointers");
   if (n == 0) return GENASIS_OK;
   cudaStream_t st = (cudaStream_t)stream;
-  const long long tiles = (n + 15) / 16;
-  const int nb = (int)((tiles + 7) / 8 < 4096 ? (tiles + 7) / 8 : 4096);
-  mlp_infer_kernel<<<nb, 256, 0, st>>>(params, (const __nv_bfloat16*)X, n, Y);
-  GH_CK(cudaGetLastError());
+  mlp::InferWeights* W = nullptr;
+  GH_CK(cudaMallocAsync((void**)&W, sizeof(mlp::InferWeights), st));
+  mlp_pack_kernel<<<1, 256, 0, st>>>(params, W);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = launch_mlp_infer(W, (const __nv_bfloat16*)X, n, Y, st);
+  cudaFreeAsync(W, st);
+  GH_CK(e);
   return GENASIS_OK;
 }
 
@@ -787,6 +814,7 @@ struct genasis_learned {
   float* dY = nullptr;
   unsigned char* flag[2] = {nullptr, nullptr};
   float* params = nullptr;
+  mlp::InferWeights* wimg = nullptr;  // BF16 image of params for inference
   bool corrected = false;
   float ylim = INFINITY;
   bool fct = true;
@@ -817,7 +845,7 @@ int learned_free(genasis_learned* l) {
   }
   for (void* p : {(void*)l->K, (void*)l->F, (void*)l->X, (void*)l->scale, (void*)l->dY, (void*)l->flag[0],
                   (void*)l->flag[1], (void*)l->params, (void*)l->scal, (void*)l->part_speed, (void*)l->status,
-                  (void*)l->nfallback, (void*)l->all_plain, (void*)l->R})
+                  (void*)l->nfallback, (void*)l->all_plain, (void*)l->R, (void*)l->wimg})
     cudaFree(p);
   if (l->own_stream && l->stream) cudaStreamDestroy(l->stream);
   delete l;
@@ -875,9 +903,7 @@ int learned_enqueue_step(genasis_learned* l, double cfl, double t_end, double fi
       lf_faces_kernel<SOLVER_HLLC><<<nb, 256, 0, st>>>(l->M, un, kin, l->scal + SCAL_DT, l->F, l->corrected ? l->X : nullptr, l->scale);
     GH_CK(cudaGetLastError());
     if (l->corrected) {
-      const long long tiles = (l->nf + 15) / 16;
-      mlp_infer_kernel<<<(int)((tiles + 7) / 8 < 4096 ? (tiles + 7) / 8 : 4096), 256, 0, st>>>(l->params, l->X, l->nf, l->dY);
-      GH_CK(cudaGetLastError());
+      GH_CK(launch_mlp_infer(l->wimg, l->X, l->nf, l->dY, st));
     }
     UpdateArgs A;
     A.M = l->M;
@@ -922,7 +948,7 @@ int learned_enqueue_step(genasis_learned* l, double cfl, double t_end, double fi
       A.fixup = -1;
       lf_update_kernel<<<nc, 256, 0, st>>>(A);
       GH_CK(cudaGetLastError());
-      GH_CK(cudaMemsetAsync(l->all_plain, 0, sizeof(unsigned), st));
+      GH_CK(cudaMemsetAsync(l->all_plain, 0, 2 * sizeof(unsigned), st));
     }
   }
   l->cur = 1 - l->cur;
@@ -959,7 +985,6 @@ int genasis_learned_create(const genasis_hydro_desc* d, genasis_learned_t* out) 
   }
   l->M.gamma = (float)d->gamma;
   l->M.gm1 = (float)(d->gamma - 1.0);
-  l->M.theta = (float)d->theta;
   l->ncell = (size_t)l->M.nx * l->M.ny;
   l->nf = (long long)(l->M.nx + 1) * l->M.ny + (long long)l->M.nx * (l->M.ny + 1);
 #define LCK(call)                                                                                   \
@@ -999,14 +1024,15 @@ int genasis_learned_create(const genasis_hydro_desc* d, genasis_learned_t* out) 
   LCK(cudaMalloc((void**)&l->status, sizeof(unsigned)));
   LCK(cudaMemsetAsync(l->status, 0, sizeof(unsigned), l->stream));
   LCK(cudaMalloc((void**)&l->R, l->ncell * 8 * sizeof(float)));
-  LCK(cudaMalloc((void**)&l->all_plain, sizeof(unsigned)));
-  LCK(cudaMemsetAsync(l->all_plain, 0, sizeof(unsigned), l->stream));
+  LCK(cudaMalloc((void**)&l->wimg, sizeof(mlp::InferWeights)));
+  LCK(cudaMalloc((void**)&l->all_plain, 2 * sizeof(unsigned)));
+  LCK(cudaMemsetAsync(l->all_plain, 0, 2 * sizeof(unsigned), l->stream));
   LCK(cudaMalloc((void**)&l->nfallback, sizeof(unsigned long long)));
   LCK(cudaMemsetAsync(l->nfallback, 0, sizeof(unsigned long long), l->stream));
   for (int q = 0; q < 2; ++q) {
     std::vector<Geo<float>> geo;
     std::vector<float> iw;
-    append_geometry<float>(extended_widths(d->widths[q], d->n[q], d->bc_lo[q], d->bc_hi[q]), geo, iw);
+    append_geometry<float>(extended_widths(d->widths[q], d->n[q], d->bc_lo[q], d->bc_hi[q]), d->theta, geo, iw);
     LCK(cudaMalloc((void**)&l->geo[q], geo.size() * sizeof(Geo<float>)));
     LCK(cudaMalloc((void**)&l->iw[q], iw.size() * sizeof(float)));
     LCK(cudaMalloc((void**)&l->wd[q], d->n[q] * sizeof(double)));
@@ -1036,6 +1062,8 @@ int genasis_learned_set_params(genasis_learned_t l, const float* params) {
   }
   GH_CK(cudaMemcpyAsync(l->params, params, mlp::NPARAM * sizeof(float),
                         is_device_ptr(params) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, l->stream));
+  mlp_pack_kernel<<<1, 256, 0, l->stream>>>(l->params, l->wimg);
+  GH_CK(cudaGetLastError());
   GH_CK(cudaStreamSynchronize(l->stream));
   l->corrected = true;
   return GENASIS_OK;

@@ -31,7 +31,7 @@ __device__ __forceinline__ int wrap_cell(int c, int n, int bc_lo, int bc_hi, boo
 struct Mesh2 {
   int nx, ny;
   int bc_lo[2], bc_hi[2];
-  float gamma, gm1, theta;
+  float gamma, gm1;
   const Geo<float>* geo[2];   // index c + 2, c in [-2, n + 2)
   const float* iw[2];
 };
@@ -71,8 +71,8 @@ __device__ __forceinline__ void plain_face_flux(const Mesh2& M, const float (&w)
   float wl[4], wr[4];
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
-    wl[v] = fmaf(limited_slope(w[0][v], w[1][v], w[2][v], gl, M.theta), gl.h, w[1][v]);
-    wr[v] = fmaf(-limited_slope(w[1][v], w[2][v], w[3][v], gr, M.theta), gr.h, w[2][v]);
+    wl[v] = fmaf(limited_slope(w[0][v], w[1][v], w[2][v], gl), gl.h, w[1][v]);
+    wr[v] = fmaf(-limited_slope(w[1][v], w[2][v], w[3][v], gr), gr.h, w[2][v]);
   }
   face_flux<float, 2, Q, SOLVER>(wl, wr, M.gamma, M.gm1, F);
 }

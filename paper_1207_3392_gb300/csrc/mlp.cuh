@@ -46,14 +46,29 @@ __device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], 
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-__device__ __forceinline__ float silu(float z) { return z / (1.0f + __expf(-z)); }
+// SiLU z sigma(z) and its derivative, with the hardware exponential and
+// reciprocal (z -> -inf gives 1 + e^{-z} = inf and sigma = 0, the limit).
+__device__ __forceinline__ float sigmoid(float z) { return __fdividef(1.0f, 1.0f + __expf(-z)); }
+__device__ __forceinline__ float silu(float z) { return z * sigmoid(z); }
 __device__ __forceinline__ float dsilu(float z) {
-  const float s = 1.0f / (1.0f + __expf(-z));
+  const float s = sigmoid(z);
   return s * (1.0f + z * (1.0f - s));
 }
 
-// Stage the BF16 weights from the FP32 parameter vector (all threads of the block).
-__device__ __forceinline__ void load_weights(Weights& W, const float* __restrict__ P) {
+// The layers the forward pass reads; a BF16 image of this struct is built once
+// per parameter set and copied to shared memory by each inference CTA.
+struct __align__(16) InferWeights {
+  __nv_bfloat16 w1[NH][KIN + PAD];
+  __nv_bfloat16 w2[NH][NH + PAD];
+  __nv_bfloat16 w3[NOUTP][NH + PAD];
+  float b1[NH], b2[NH], b3[NOUTP];
+};
+static_assert(sizeof(InferWeights) % 16 == 0, "copied as 16-byte vectors");
+
+// Fill the forward-pass layers of W (Weights or InferWeights) from the FP32
+// parameter vector (all threads of the block).
+template <class WT>
+__device__ __forceinline__ void fill_layers(WT& W, const float* __restrict__ P) {
   for (int i = threadIdx.x; i < NH * (KIN + PAD); i += blockDim.x) {
     const int o = i / (KIN + PAD), k = i % (KIN + PAD);
     W.w1[o][k] = __float2bfloat16(k < NIN ? P[OW1 + o * NIN + k] : 0.0f);
@@ -61,21 +76,36 @@ __device__ __forceinline__ void load_weights(Weights& W, const float* __restrict
   for (int i = threadIdx.x; i < NH * (NH + PAD); i += blockDim.x) {
     const int o = i / (NH + PAD), k = i % (NH + PAD);
     W.w2[o][k] = __float2bfloat16(k < NH ? P[OW2 + o * NH + k] : 0.0f);
-    W.w2t[o][k] = __float2bfloat16(k < NH ? P[OW2 + k * NH + o] : 0.0f);
   }
   for (int i = threadIdx.x; i < NOUTP * (NH + PAD); i += blockDim.x) {
     const int o = i / (NH + PAD), k = i % (NH + PAD);
     W.w3[o][k] = __float2bfloat16(o < NOUT && k < NH ? P[OW3 + o * NH + k] : 0.0f);
-  }
-  for (int i = threadIdx.x; i < NH * (16 + PAD); i += blockDim.x) {
-    const int j = i / (16 + PAD), o = i % (16 + PAD);
-    W.w3t[j][o] = __float2bfloat16(o < NOUT ? P[OW3 + o * NH + j] : 0.0f);
   }
   for (int i = threadIdx.x; i < NH; i += blockDim.x) {
     W.b1[i] = P[OB1 + i];
     W.b2[i] = P[OB2 + i];
   }
   for (int i = threadIdx.x; i < NOUTP; i += blockDim.x) W.b3[i] = i < NOUT ? P[OB3 + i] : 0.0f;
+}
+
+// Stage all BF16 weights, with the transposed copies the backward pass needs.
+__device__ __forceinline__ void load_weights(Weights& W, const float* __restrict__ P) {
+  fill_layers(W, P);
+  for (int i = threadIdx.x; i < NH * (NH + PAD); i += blockDim.x) {
+    const int o = i / (NH + PAD), k = i % (NH + PAD);
+    W.w2t[o][k] = __float2bfloat16(k < NH ? P[OW2 + k * NH + o] : 0.0f);
+  }
+  for (int i = threadIdx.x; i < NH * (16 + PAD); i += blockDim.x) {
+    const int j = i / (16 + PAD), o = i % (16 + PAD);
+    W.w3t[j][o] = __float2bfloat16(o < NOUT ? P[OW3 + o * NH + j] : 0.0f);
+  }
+}
+
+// Copy a prepared InferWeights image into shared memory (all threads).
+__device__ __forceinline__ void copy_weights(InferWeights& W, const InferWeights* __restrict__ G) {
+  const uint4* src = reinterpret_cast<const uint4*>(G);
+  uint4* dst = reinterpret_cast<uint4*>(&W);
+  for (int i = threadIdx.x; i < (int)(sizeof(InferWeights) / 16); i += blockDim.x) dst[i] = __ldg(src + i);
 }
 
 // Forward pass of one warp over 16 samples whose rows start at X (row stride
@@ -119,7 +149,8 @@ __device__ __forceinline__ void to_afrag(const float (&z)[8][4], uint32_t (&a)[4
   }
 }
 
-__device__ __forceinline__ void forward(Forward& F, const Weights& W) {
+template <class WT>
+__device__ __forceinline__ void forward(Forward& F, const WT& W) {
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
 #pragma unroll
   for (int nt = 0; nt < 8; ++nt) {

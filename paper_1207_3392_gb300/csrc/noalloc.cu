@@ -50,7 +50,8 @@ static unsigned char* g_noalloc_ptr[64] = {nullptr};
 // handle set-up: two ghost widths per side by the boundary rule, centre
 // distances of Eq. MinMod on a non-uniform Cartesian mesh).
 template <class T>
-__global__ void noalloc_geometry_kernel(int n, int lo, int hi, const double* __restrict__ w, Geo<T>* geo, T* iw) {
+__global__ void noalloc_geometry_kernel(int n, int lo, int hi, double theta, const double* __restrict__ w, Geo<T>* geo,
+                                        T* iw) {
   const int m = n + 4;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) {
     double e3[3];
@@ -65,9 +66,9 @@ __global__ void noalloc_geometry_kernel(int n, int lo, int hi, const double* __r
     }
     const double dm = e3[0], dc = e3[1], dp = e3[2];
     Geo<T> g;
-    g.icm = (T)(1.0 / (0.5 * (dm + dc)));
+    g.ticm = (T)(theta / (0.5 * (dm + dc)));
     g.ipm = (T)(1.0 / (0.5 * dm + dc + 0.5 * dp));
-    g.ipc = (T)(1.0 / (0.5 * (dc + dp)));
+    g.tipc = (T)(theta / (0.5 * (dc + dp)));
     g.h = (T)(0.5 * dc);
     geo[k] = g;
     iw[k] = (T)(1.0 / dc);
@@ -147,7 +148,8 @@ static int noalloc_step_t(const genasis_hydro_desc* d, unsigned char* base, cons
   for (int q = 0; q < ndim; ++q) {
     GH_CK(cudaMemcpyAsync(wd + (size_t)q * NOALLOC_MAX_N, d->widths[q], (size_t)n[q] * sizeof(double),
                           cudaMemcpyHostToDevice, st));
-    noalloc_geometry_kernel<T><<<(n[q] + 4 + 127) / 128, 128, 0, st>>>(n[q], lo[q], hi[q], wd + (size_t)q * NOALLOC_MAX_N,
+    noalloc_geometry_kernel<T><<<(n[q] + 4 + 127) / 128, 128, 0, st>>>(n[q], lo[q], hi[q], d->theta,
+                                                                       wd + (size_t)q * NOALLOC_MAX_N,
                                                                        geo + q * GEO_N, iw + q * GEO_N);
     GH_CK(cudaGetLastError());
   }
@@ -165,7 +167,6 @@ static int noalloc_step_t(const genasis_hydro_desc* d, unsigned char* base, cons
   }
   A.gamma = (T)d->gamma;
   A.gm1 = (T)(d->gamma - 1.0);
-  A.theta = (T)d->theta;
   A.un = uin;
   A.k1 = K;
   A.dt = scal + SCAL_DT;

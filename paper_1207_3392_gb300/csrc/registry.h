@@ -13,17 +13,19 @@ struct StageVariant {
   int tx, ty;          // tile shape (threads = tx * ty)
 };
 
-// Tile shapes compiled per dimensionality; index `tile` selects one.
-int stage_tile_count(int ndim);
+// Tile shapes compiled per dimensionality and precision; index `tile` selects one.
+int stage_tile_count(int ndim, bool fp64);
 // Fills *out for (ndim, fp64?, solver, stage, tile); returns false if absent.
 bool stage_variant(int ndim, bool fp64, int solver, int stage, int tile, StageVariant* out);
 
 bool stage_variant_1d(bool fp64, int solver, int stage, int tile, StageVariant* out);
 bool stage_variant_2d(bool fp64, int solver, int stage, int tile, StageVariant* out);
 bool stage_variant_3d_f32(int solver, int stage, int tile, StageVariant* out);
+bool stage_variant_3d_f32_wide(int solver, int stage, int tile, StageVariant* out);
 bool stage_variant_3d_f64(int solver, int stage, int tile, StageVariant* out);
 int tile_count_1d();
 int tile_count_2d();
-int tile_count_3d();
+int tile_count_3d_f32();
+int tile_count_3d_f64();
 
 }  // namespace gh

@@ -28,7 +28,7 @@ template <class T>
 struct StageArgs {
   int n[3];               // cells per axis; 1 on inactive axes
   int bc_lo[3], bc_hi[3];
-  T gamma, gm1, theta;
+  T gamma, gm1;
   const Geo<T>* geo[3];   // per axis, index c + 2 for c in [-2, n + 2)
   const T* iw[3];         // inverse widths, index c + 2
   const double* wd[3];    // widths in FP64, index c (totals)
@@ -132,8 +132,8 @@ struct StageKernel {
     for (int v = 0; v < NV; ++v) {
       const T w0 = S.w[v][srow][sl - 1], w1 = S.w[v][srow][sl], w2 = S.w[v][srow][sl + 1],
               w3 = S.w[v][srow][sl + 2];
-      wl[v] = fma(limited_slope(w0, w1, w2, gl, A.theta), gl.h, w1);
-      wr[v] = fma(-limited_slope(w1, w2, w3, gr, A.theta), gr.h, w2);
+      wl[v] = fma(limited_slope(w0, w1, w2, gl), gl.h, w1);
+      wr[v] = fma(-limited_slope(w1, w2, w3, gr), gr.h, w2);
     }
     face_flux<T, NDIM, 0, SOLVER>(wl, wr, A.gamma, A.gm1, f);
 #pragma unroll
@@ -148,8 +148,8 @@ struct StageKernel {
     for (int v = 0; v < NV; ++v) {
       const T w0 = S.w[v][sl - 1][scol], w1 = S.w[v][sl][scol], w2 = S.w[v][sl + 1][scol],
               w3 = S.w[v][sl + 2][scol];
-      wl[v] = fma(limited_slope(w0, w1, w2, gl, A.theta), gl.h, w1);
-      wr[v] = fma(-limited_slope(w1, w2, w3, gr, A.theta), gr.h, w2);
+      wl[v] = fma(limited_slope(w0, w1, w2, gl), gl.h, w1);
+      wr[v] = fma(-limited_slope(w1, w2, w3, gr), gr.h, w2);
     }
     face_flux<T, NDIM, 1, SOLVER>(wl, wr, A.gamma, A.gm1, f);
 #pragma unroll
@@ -173,7 +173,7 @@ struct StageKernel {
   static __device__ __forceinline__ void slopes(const StageArgs<T>& A, const T (&wm)[NV], const T (&wc)[NV],
                                                 const T (&wp)[NV], const Geo<T>& g, T (&s)[NV]) {
 #pragma unroll
-    for (int v = 0; v < NV; ++v) s[v] = limited_slope(wm[v], wc[v], wp[v], g, A.theta);
+    for (int v = 0; v < NV; ++v) s[v] = limited_slope(wm[v], wc[v], wp[v], g);
   }
 
   static __device__ __forceinline__ bool nonphysical(const T (&w)[NV], T gm1) {

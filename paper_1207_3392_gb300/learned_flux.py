@@ -262,9 +262,12 @@ def short_horizon(params, seeds=range(64, 72), n_coarse=256, factor=4, t_starts=
                            "l1_plain": _l1(plain.get_conserved()[0], truth)}
                     for k, L in runs.items():
                         if alive[k]:
-                            L.get_conserved(out)
-                            U = out.cpu().numpy()
-                            ok = bool(np.isfinite(U).all() and U[0].min() > 0)
+                            try:
+                                L.get_conserved(out)
+                                U = out.cpu().numpy()
+                                ok = bool(np.isfinite(U).all() and U[0].min() > 0)
+                            except H.HydroError:   # left the physical states
+                                ok = False
                             alive[k] = ok
                             res[f"l1_{k}"] = _l1(U[0], truth) if ok else math.inf
                         else:
