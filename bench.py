@@ -45,8 +45,10 @@ def _args():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="sedov", choices=["sedov", "batch"])
+    ap.add_argument("--workload", default="sedov", choices=["sedov", "batch", "learned"])
     ap.add_argument("--no-autotune", action="store_true", help="keep the default tile instead of autotuning")
+    ap.add_argument("--tile", type=int, default=-1, help="use this tile (and --kchunk) instead of autotuning")
+    ap.add_argument("--kchunk", type=int, default=0)
     return ap.parse_args()
 
 
@@ -147,6 +149,11 @@ FLOPS_3D = {"hllc": 12 + 150 + 60 + 3 * 96 + 40 + 25, "hll": 12 + 150 + 60 + 3 *
 # FP64 at the nominal 1.25 TFLOP/s.
 PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 PEAK_FP64_TFLOPS = 1.25
+# DRAM bytes (read + write) per cell of the FP32 HLLC 3D stage kernels, from
+# one ncu capture of the same kernels at 192^3 (summary under profiles/),
+# scaled to the bench's cell count (traffic grows with the cells).
+TRAFFIC_PER_CELL_FP32_HLLC = {"stage1": (148.504832e6 + 104.506624e6) / 192 ** 3,
+                              "stage2": (299.108608e6 + 119.765504e6) / 192 ** 3}
 
 
 def cpu_baseline(n_sample=256, steps=3):
@@ -217,7 +224,9 @@ def run_ours(args):
     del prob
     cells = h.ncell
     cfl = 0.3
-    if not args.no_autotune:
+    if args.tile >= 0:
+        h.set_tile(args.tile, args.kchunk)
+    elif not args.no_autotune:
         h.autotune(trial_steps=3)
     tile = h.tile_info()
 
@@ -265,6 +274,8 @@ def run_ours(args):
     flops = FLOPS_3D[args.solver] * cells
     peak_f = PEAK_FP32_TFLOPS if b == 4 else PEAK_FP64_TFLOPS
     achieved_f = flops / (dom_ms * 1e-3) / 1e12
+    traffic = (TRAFFIC_PER_CELL_FP32_HLLC[dom] * cells
+               if b == 4 and args.solver == "hllc" else None)
     # The stage kernel is bound by instruction issue on the vector pipes (ncu),
     # not by DRAM: the roofline is the vector-arithmetic one; the HBM figure of
     # the metric is reported beside it.
@@ -273,7 +284,8 @@ def run_ours(args):
                 "achieved": achieved_f, "peak": peak_f, "unit": "TFLOP/s", "frac": achieved_f / peak_f,
                 "peak_source": ("derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz" if b == 4
                                 else "nominal FP64 1.25 TFLOP/s"),
-                "algorithmic_flops_per_cell": FLOPS_3D[args.solver], "traffic": None,
+                "algorithmic_flops_per_cell": FLOPS_3D[args.solver], "traffic": traffic,
+                "traffic_source": ("ncu dram bytes at 192^3 scaled by cells" if traffic else None),
                 "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                         "peak_source": f"{peak_kind} hbm_gbs", "algorithmic_bytes_per_cell": dom_bytes // cells,
                         "step_frac": (bytes1 + bytes2) / ((st1 + fin + st2) * 1e-3) / 1e9 / peak},
@@ -435,12 +447,69 @@ def run_batch(args):
         dist.destroy_process_group()
 
 
+def run_learned(args):
+    """Learned flux correction on the 2D periodic shear layer, 256^2 FP32: one
+    RK2 step = CFL reduction, and per stage the plain face fluxes and
+    features, the BF16 MLP, the FCT ratios, the corrected update (plus the
+    fallback passes, which return at once when no cell failed).  The network
+    is a seeded random one of the trained shape; the cost does not depend on
+    the weights while no cell falls back."""
+    import torch
+    from paper_1207_3392_gb300 import build
+    from paper_1207_3392_gb300 import hydro as H
+    from paper_1207_3392_gb300 import problems as P
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    build.build()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    pr = P.kelvin_helmholtz(256, seed=64)
+    from paper_1207_3392_gb300 import learned_flux as LF
+    params = LF._init_params(0)
+    nlast = 4 * 64 + 4                      # output layer W3, b3 (zero at initialisation)
+    params[-nlast:] = np.random.default_rng(0).normal(0.0, 0.02, nlast).astype(np.float32)
+    L = H.Learned(pr, params=params, stream=stream.cuda_stream)
+    L.set_primitive(pr.rho, pr.vel, pr.p)
+    for _ in range(max(args.warmup, 3)):
+        L.advance(1, 0.5, sync=False)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        L.advance(1, 0.5, sync=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    fb = L.fallbacks()
+    L.close()
+    cells = 256 * 256
+    line = {"metric": METRIC, "value": world * cells * 2 / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16", "data": "synthetic",
+            "config": {"workload": "learned_kh2d_256^2_hllc_fct", "cells": cells, "faces": 2 * cells,
+                       "network": "24-64-64-4 SiLU, BF16 mma.sync, FP32 accumulate",
+                       "l2": "inputs smaller than L2 (state 1 MB): the step is launch- and latency-bound",
+                       "fallback_cells": fb},
+            "roofline": None, "clocks": clocks,
+            # per step: CFL speed + finalize, and per stage faces, MLP, FCT,
+            # the update, 3 widening passes and the all-plain pass
+            "gpu_launches": args.steps * (2 + 2 * 8)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = _args()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch":
         run_batch(args)
+    elif args.workload == "learned":
+        run_learned(args)
     else:
         run_ours(args)
 
