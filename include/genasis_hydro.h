@@ -110,6 +110,18 @@ int genasis_hydro_set_primitive(genasis_hydro_t h, const double *rho, const doub
 int genasis_hydro_set_conserved(genasis_hydro_t h, const void *U, int precision);
 int genasis_hydro_get_conserved(genasis_hydro_t h, void *U, int precision);
 
+/* The same copies, enqueued on the handle's stream without synchronising, so
+ * that transfers of one handle overlap the steps of another (the paper has no
+ * counterpart; it is the host <-> device side of the boundary).  A host U
+ * should be page-locked (otherwise the copy is staged and may not overlap);
+ * it must stay valid and unchanged until genasis_hydro_sync(h) returns.  The
+ * non-physical status is reported by genasis_hydro_sync, not here. */
+int genasis_hydro_set_conserved_async(genasis_hydro_t h, const void *U, int precision);
+int genasis_hydro_get_conserved_async(genasis_hydro_t h, void *U, int precision);
+/* Wait for all work enqueued on h's stream; returns ENONPHYS / ETIMEOUT if the
+ * sticky status is set, else OK. */
+int genasis_hydro_sync(genasis_hydro_t h);
+
 /* dt = cfl * dt_CFL of the current state (Eq. courantTimeStep); synchronises. */
 int genasis_hydro_compute_dt(genasis_hydro_t h, double cfl, double *dt);
 

@@ -352,6 +352,30 @@ int import_array(genasis_hydro* h, const void* src, int src_prec, size_t count, 
   return GENASIS_OK;
 }
 
+// Enqueue the copy of the current state into U (host or device) in the given
+// precision, converting on the device if it differs from the handle's.
+int export_array(genasis_hydro* h, void* U, int precision) {
+  const size_t count = h->ncell * h->nv;
+  const bool dev = is_device_ptr(U);
+  if (precision == h->prec) {
+    GH_CK(cudaMemcpyAsync(U, h->U[h->cur], count * h->esize, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                          h->stream));
+    return GENASIS_OK;
+  }
+  const size_t dsize = precision == GENASIS_FP64 ? 8 : 4;
+  void* dst = U;
+  if (!dev) GH_CK(cudaMallocAsync(&dst, count * dsize, h->stream));
+  cudaError_t e = h->prec == GENASIS_FP64
+                      ? launch_convert<double, float>(count, (const double*)h->U[h->cur], (float*)dst, h->stream)
+                      : launch_convert<float, double>(count, (const float*)h->U[h->cur], (double*)dst, h->stream);
+  GH_CK(e);
+  if (!dev) {
+    GH_CK(cudaMemcpyAsync(U, dst, count * dsize, cudaMemcpyDeviceToHost, h->stream));
+    GH_CK(cudaFreeAsync(dst, h->stream));
+  }
+  return GENASIS_OK;
+}
+
 int free_all(genasis_hydro* h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   for (int b = 0; b < 2; ++b)
@@ -483,29 +507,31 @@ int genasis_hydro_set_conserved(genasis_hydro_t h, const void* U, int precision)
   return GENASIS_OK;
 }
 
+int genasis_hydro_set_conserved_async(genasis_hydro_t h, const void* U, int precision) {
+  if (!h || !U) return fail(GENASIS_EINVAL, "NULL argument");
+  if (precision != GENASIS_FP64 && precision != GENASIS_FP32_MIXED) return fail(GENASIS_EINVAL, "bad precision");
+  return import_array(h, U, precision, h->ncell * h->nv, h->U[h->cur]);
+}
+
+int genasis_hydro_get_conserved_async(genasis_hydro_t h, void* U, int precision) {
+  if (!h || !U) return fail(GENASIS_EINVAL, "NULL argument");
+  if (precision != GENASIS_FP64 && precision != GENASIS_FP32_MIXED) return fail(GENASIS_EINVAL, "bad precision");
+  return export_array(h, U, precision);
+}
+
+int genasis_hydro_sync(genasis_hydro_t h) {
+  if (!h) return fail(GENASIS_EINVAL, "NULL handle");
+  return sync_status(h);
+}
+
 int genasis_hydro_get_conserved(genasis_hydro_t h, void* U, int precision) {
   if (!h || !U) return fail(GENASIS_EINVAL, "NULL argument");
   if (precision != GENASIS_FP64 && precision != GENASIS_FP32_MIXED) return fail(GENASIS_EINVAL, "bad precision");
-  const size_t count = h->ncell * h->nv;
-  const bool dev = is_device_ptr(U);
-  if (precision == h->prec) {
-    GH_CK(cudaMemcpyAsync(U, h->U[h->cur], count * h->esize, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                          h->stream));
-  } else {
-    const size_t dsize = precision == GENASIS_FP64 ? 8 : 4;
-    void* dst = U;
-    if (!dev) GH_CK(cudaMallocAsync(&dst, count * dsize, h->stream));
-    cudaError_t e = h->prec == GENASIS_FP64
-                        ? launch_convert<double, float>(count, (const double*)h->U[h->cur], (float*)dst, h->stream)
-                        : launch_convert<float, double>(count, (const float*)h->U[h->cur], (double*)dst, h->stream);
-    GH_CK(e);
-    if (!dev) {
-      GH_CK(cudaMemcpyAsync(U, dst, count * dsize, cudaMemcpyDeviceToHost, h->stream));
-      GH_CK(cudaFreeAsync(dst, h->stream));
-    }
-  }
+  int rc = export_array(h, U, precision);
+  if (rc) return rc;
   return sync_status(h);
 }
+
 
 int genasis_hydro_compute_dt(genasis_hydro_t h, double cfl, double* dt) {
   if (!h || !dt) return fail(GENASIS_EINVAL, "NULL argument");

@@ -62,6 +62,9 @@ SIGNATURES = {
     "genasis_hydro_get_totals": [_P, _P],
     "genasis_hydro_status": [_P],
     "genasis_hydro_clear_status": [_P],
+    "genasis_hydro_set_conserved_async": [_P, _P, _I],
+    "genasis_hydro_get_conserved_async": [_P, _P, _I],
+    "genasis_hydro_sync": [_P],
     "genasis_hydro_set_tile": [_P, _I, _I],
     "genasis_hydro_get_tile": [_P, _P],
     "genasis_hydro_autotune": [_P, _I, ctypes.c_char_p],
@@ -209,6 +212,31 @@ class Hydro:
         po, _ = _ptr(out, dt, self.ncell * self.nvar, "out")
         check(load().genasis_hydro_get_conserved(self._h, po, precision))
         return out
+
+    def set_conserved_async(self, U, precision=None):
+        """Enqueue the copy of U (page-locked host or device) without waiting;
+        U must stay unchanged until sync()."""
+        precision = self.precision if precision is None else precision
+        dt = np.float64 if precision == FP64 else np.float32
+        pu, keep = _ptr(U, dt, self.ncell * self.nvar, "U")
+        if keep is not U:
+            raise ValueError("U: an asynchronous copy needs a contiguous array of the exact dtype (no temporary)")
+        check(load().genasis_hydro_set_conserved_async(self._h, pu, precision))
+
+    def get_conserved_async(self, out, precision=None):
+        """Enqueue the copy of the state into `out` without waiting; read it
+        after sync()."""
+        precision = self.precision if precision is None else precision
+        dt = np.float64 if precision == FP64 else np.float32
+        po, keep = _ptr(out, dt, self.ncell * self.nvar, "out")
+        if keep is not out:
+            raise ValueError("out: an asynchronous copy needs a contiguous array of the exact dtype (no temporary)")
+        check(load().genasis_hydro_get_conserved_async(self._h, po, precision))
+        return out
+
+    def sync(self):
+        """Wait for the handle's stream; raises on a non-physical state."""
+        check(load().genasis_hydro_sync(self._h))
 
     # -- stepping -------------------------------------------------------------
     def compute_dt(self, cfl):

@@ -176,6 +176,38 @@ def test_device_and_host_pointers_agree():
         h.close()
 
 
+def test_async_copies_pipelined_over_handles():
+    """Three handles on three streams, each step's state copied in from
+    page-locked host memory and back without waiting in between, give the
+    same states as the synchronous path."""
+    import torch
+    pr = P.random_blocks(3, (24, 20, 18), seed=12, bc=P.REFLECT)
+    ref = H.Hydro.from_problem(pr, precision=H.FP32_MIXED)
+    U0 = ref.get_conserved()
+    ref.advance(1, 0.3)
+    want = ref.get_conserved()
+    ref.close()
+    streams = [torch.cuda.Stream() for _ in range(3)]
+    hs = [H.Hydro.from_problem(pr, precision=H.FP32_MIXED, stream=s.cuda_stream, set_state=False) for s in streams]
+    ins = [torch.from_numpy(U0.copy()).pin_memory() for _ in range(3)]
+    outs = [torch.empty(U0.shape, dtype=torch.float32).pin_memory() for _ in range(6)]
+    for k in range(6):
+        h = hs[k % 3]
+        if k >= 3:
+            h.sync()
+        h.set_conserved_async(ins[k % 3])
+        h.advance(1, 0.3, sync=False)
+        h.get_conserved_async(outs[k])
+    for h in hs:
+        h.sync()
+    for k in range(6):
+        np.testing.assert_array_equal(outs[k].numpy(), want, err_msg=f"step {k}")
+    with pytest.raises(ValueError):
+        hs[0].set_conserved_async(U0.astype(np.float64))  # would copy into a temporary
+    for h in hs:
+        h.close()
+
+
 def test_nonphysical_state_sets_status():
     pr = P.sod(64)
     pr.p[10] = -1.0
