@@ -242,7 +242,7 @@ StageArgs<T> stage_args(genasis_hydro* h, int stage) {
 
 template <class T>
 int enqueue_step_t(genasis_hydro* h, int mode, double fixed_dt, double cfl, double t_end, cudaEvent_t* ev) {
-  const dim3 block(h->v1.tx * h->v1.ty);
+  const dim3 block(h->v1.threads);
   StageArgs<T> a1 = stage_args<T>(h, 1);
   void* p1[] = {&a1};
   if (ev) GH_CK(cudaEventRecord(ev[0], h->stream));

@@ -15,6 +15,7 @@ inline void fill_variant(StageVariant* out) {
   out->smem = sizeof(typename K::Smem);
   out->tx = TX;
   out->ty = TY;
+  out->threads = TX * TY;
 }
 
 template <int NDIM, class T, int TX, int TY, int MINB = 1>

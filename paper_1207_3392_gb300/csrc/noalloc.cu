@@ -175,7 +175,7 @@ static int noalloc_step_t(const genasis_hydro_desc* d, unsigned char* base, cons
   A.part_tot = tot;
   A.status = status;
   A.want_totals = 0;
-  const dim3 grid(gx, gy, gz), block(v1.tx * v1.ty);
+  const dim3 grid(gx, gy, gz), block(v1.threads);
 
   StageArgs<T> a1 = A;
   a1.out = K;

@@ -10,7 +10,8 @@ namespace gh {
 struct StageVariant {
   const void* fn;      // kernel entry
   size_t smem;         // dynamic shared memory per CTA (bytes)
-  int tx, ty;          // tile shape (threads = tx * ty)
+  int tx, ty;          // tile shape in cells
+  int threads;         // threads per CTA
 };
 
 // Tile shapes compiled per dimensionality and precision; index `tile` selects one.

@@ -296,11 +296,20 @@ struct StageKernel {
       }
       __syncthreads();
 
-      // in-plane faces, each computed once, one call site per axis
+      // in-plane faces, each computed once, one call site per axis.  Whole
+      // rounds of NT faces go to all threads; the REM faces left over go to
+      // the last threads, which load no halo cells, so that no warp does
+      // both a halo load and an extra face.
       {
         constexpr int NXF = (TX + 1) * TY;
         constexpr int NYF = HAS_Y ? TX * (TY + 1) : 0;
-        for (int f = tid; f < NXF + NYF; f += NT) {
+        constexpr int NF = NXF + NYF, ROUNDS = NF / NT, REM = NF - ROUNDS * NT;
+        for (int k = 0; k <= ROUNDS; ++k) {
+          int f = tid + k * NT;
+          if (k == ROUNDS) {
+            if (REM == 0 || tid < NT - REM) break;
+            f = ROUNDS * NT + (tid - (NT - REM));
+          }
           if (f < NXF) {
             const int row = f / (TX + 1);
             const int face = f - row * (TX + 1);
