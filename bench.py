@@ -405,6 +405,22 @@ def run_ours(args):
         mv = a.elapsed_time(z) / 20
         variants["stretched_pulse_320^3_hllc_fp32"] = {"value": hv.ncell * 2 / (mv * 1e-3), "ms_per_step": mv}
         hv.close()
+        # the Rayleigh-Taylor set-up of Sec. 4.3.2 (external-force source), 256 x 768
+        pr = P.rayleigh_taylor(256, 768)
+        hv = H.Hydro.from_problem(pr, precision=H.FP32_MIXED, stream=stream.cuda_stream)
+        del pr
+        hv.autotune(trial_steps=2)
+        for _ in range(3):
+            hv.advance(1, 0.5, sync=False)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(50):
+            hv.advance(1, 0.5, sync=False)
+        z.record(stream)
+        torch.cuda.synchronize()
+        mv = a.elapsed_time(z) / 50
+        variants["rayleigh_taylor_256x768_hllc_fp32"] = {"value": hv.ncell * 2 / (mv * 1e-3), "ms_per_step": mv}
+        hv.close()
         line["variants"] = variants
 
     if rank == 0 and world == 1 and not args.no_cpu:

@@ -167,6 +167,14 @@ int genasis_hydro_autotune(genasis_hydro_t h, int trial_steps, const char *cache
  * an unknown option or value. */
 #define GENASIS_OPT_STEP_TOTALS 1
 int genasis_hydro_set_option(genasis_hydro_t h, int option, int value);
+/* External force of a linear potential Phi = grad_phi . x (the uniform force
+ * of the Rayleigh-Taylor test, Sec. 4.3.2): each stage adds the source
+ * S_q = -D dPhi/dq to the momenta and -sum_q S_q dPhi/dq to the energy,
+ * from each cell's stage-input state (the paper prints the source vector
+ * without its sign; the force is -grad Phi).  grad_phi[3] (entries beyond
+ * ndim are ignored); all zero turns the source off (the default).  Returns
+ * EINVAL for a non-finite entry. */
+int genasis_hydro_set_potential_gradient(genasis_hydro_t h, const double *grad_phi);
 /* Totals of U^n of the last step taken with GENASIS_OPT_STEP_TOTALS = 1
  * (totals[0 .. ndim + 1]); synchronises. */
 int genasis_hydro_get_step_totals(genasis_hydro_t h, double *totals);

@@ -41,7 +41,8 @@ class _Desc(ctypes.Structure):
     _fields_ = [("ndim", ctypes.c_int), ("n", ctypes.c_int * 3),
                 ("width", ctypes.c_void_p * 3), ("bc_lo", ctypes.c_int * 3),
                 ("bc_hi", ctypes.c_int * 3), ("gamma", ctypes.c_double),
-                ("theta", ctypes.c_double), ("solver", ctypes.c_int)]
+                ("theta", ctypes.c_double), ("solver", ctypes.c_int),
+                ("grad_phi", ctypes.c_double * 3)]
 
 
 _lib = None
@@ -83,6 +84,7 @@ class Grid:
         self.gamma = float(prob.gamma if gamma is None else gamma)
         self.theta = float(prob.theta if theta is None else theta)
         self.solver = int(prob.solver if solver is None else solver)
+        self.grad_phi = tuple(float(x) for x in getattr(prob, "grad_phi", (0.0, 0.0, 0.0)))
         d = _Desc()
         d.ndim = self.ndim
         for q in range(3):
@@ -91,6 +93,8 @@ class Grid:
             d.bc_hi[q] = self.bc_hi[q]
             d.width[q] = self.widths[q].ctypes.data if q < self.ndim else None
         d.gamma, d.theta, d.solver = self.gamma, self.theta, self.solver
+        for q in range(3):
+            d.grad_phi[q] = self.grad_phi[q]
         self._d = d
 
     @property

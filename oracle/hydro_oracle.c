@@ -21,6 +21,8 @@
  *   TVD RK2 (Heun)                Eqs. Update, RungeKutta1..RungeKutta3 (Sec. 3.4)
  *   CFL time step                 Eq. courantTimeStep and the C_CFL factor after it (Sec. 3.6)
  *   conserved totals              sums over cells of U dV (Sec. 3.3, conservation on leaf cells)
+ *   external-force source         the source vector of the Rayleigh-Taylor test (Sec. 4.3.2),
+ *                                 potential at cell centres, gradient by centred differences
  *
  * Readings where the paper is garbled or silent (each also listed in the design doc):
  *   - Eq. PressureMiddle as printed violates p*_L = p*_R (stated right after
@@ -47,7 +49,10 @@
  *   - Reconstructed primitive set W = (n, v, e); p = (gamma-1) e afterwards.
  *   - No floors: a non-positive density or pressure, or a non-finite value, in
  *     an interior cell makes the call return OG_ENONPHYS.
- *   - m (average baryon mass) = 1 throughout, so rho = n.
+ * *   - m (average baryon mass) = 1 throughout, so rho = n.
+ *   - The source vector of Sec. 4.3.2 is printed without a sign; the force
+ *     -grad Phi must pull the fluid down the potential, so the source is
+ *     S = -[0, m D dPhi/dx_q, (S . grad Phi)] (momentum q and energy).
  *
  * Layout: structure of arrays, U[var][k][j][i], x fastest; nvar = ndim + 2
  * (D, S_1..S_ndim, G).  Interior arrays only cross this interface; ghost layers
@@ -72,6 +77,7 @@ typedef struct {
   double gamma;
   double theta;
   int solver;
+  double grad_phi[3];  /* gradient of a linear external potential Phi = grad_phi . x; 0: no source */
 } og_desc;
 
 /* Grid with ghost layers. */
@@ -362,6 +368,36 @@ static int og_rhs_grid(const og_grid *G, const og_desc *d, const double *U, doub
             for (int v = 0; v < nv; ++v) L[(size_t)v * nin + li] += F[v] * inv;
           }
         }
+  }
+  /* External-force source (Sec. 4.3.2): Phi = grad_phi . x at the cell centres,
+   * its gradient along q by the centred difference over the two neighbour
+   * centres (exact for this linear potential up to rounding), then
+   * S_q += -D dPhi/dq and G += -S_q dPhi/dq from the cell's own U. */
+  if (d->grad_phi[0] != 0.0 || d->grad_phi[1] != 0.0 || d->grad_phi[2] != 0.0) {
+    for (int q = 0; q < nd; ++q) {
+      if (d->grad_phi[q] == 0.0) continue;
+      const double *wq = G->w[q];
+      /* centre coordinates of cells -1 .. n_q (origin at the low face of cell 0) */
+      double *xc = (double *)malloc(sizeof(double) * (G->n[q] + 2));
+      if (!xc) { free(Ue); free(We); free(Win); free(Wout); return OG_ENOMEM; }
+      xc[1] = 0.5 * wq[OG_NG];
+      for (int c = 1; c < G->n[q]; ++c) xc[c + 1] = xc[c] + 0.5 * (wq[c - 1 + OG_NG] + wq[c + OG_NG]);
+      xc[0] = xc[1] - 0.5 * (wq[OG_NG - 1] + wq[OG_NG]);
+      xc[G->n[q] + 1] = xc[G->n[q]] + 0.5 * (wq[G->n[q] - 1 + OG_NG] + wq[G->n[q] + OG_NG]);
+      for (int k = 0; k < G->n[2]; ++k)
+        for (int j = 0; j < G->n[1]; ++j)
+          for (int i = 0; i < G->n[0]; ++i) {
+            int c[3] = {i, j, k};
+            int cq = c[q];
+            double phim = d->grad_phi[q] * xc[cq], phip = d->grad_phi[q] * xc[cq + 2];
+            double dphi = (phip - phim) / (xc[cq + 2] - xc[cq]);
+            size_t li = ((size_t)k * G->n[1] + j) * G->n[0] + i;
+            double D = U[li], Sq = U[(size_t)(1 + q) * nin + li];
+            L[(size_t)(1 + q) * nin + li] -= D * dphi;
+            L[(size_t)(nv - 1) * nin + li] -= Sq * dphi;
+          }
+      free(xc);
+    }
   }
   free(Ue); free(We); free(Win); free(Wout);
   return bad ? OG_ENONPHYS : OG_OK;

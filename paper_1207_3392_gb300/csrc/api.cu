@@ -61,6 +61,8 @@ using namespace gh;
 struct genasis_hydro {
   int ndim = 0, nv = 0, n[3] = {1, 1, 1}, bc_lo[3] = {0, 0, 0}, bc_hi[3] = {0, 0, 0};
   double gamma = 1.4, theta = 1.4;
+  double grad_phi[3] = {0.0, 0.0, 0.0};  // external potential gradient (source off when zero)
+  int has_source = 0;
   int solver = 1, prec = 0;
   size_t ncell = 0, esize = 8;
   cudaStream_t stream = nullptr;
@@ -237,6 +239,8 @@ StageArgs<T> stage_args(genasis_hydro* h, int stage) {
   A.part_tot = h->part_tot;
   A.status = h->status;
   A.want_totals = h->want_totals;
+  A.has_source = h->has_source;
+  for (int q = 0; q < 3; ++q) A.grad_phi[q] = (T)h->grad_phi[q];
   return A;
 }
 
@@ -661,6 +665,24 @@ int genasis_hydro_set_option(genasis_hydro_t h, int option, int value) {
     return GENASIS_OK;
   }
   return fail(GENASIS_EINVAL, "unknown option %d", option);
+}
+
+int genasis_hydro_set_potential_gradient(genasis_hydro_t h, const double* grad_phi) {
+  if (!h || !grad_phi) return fail(GENASIS_EINVAL, "NULL argument");
+  for (int q = 0; q < 3; ++q)
+    if (!(fabs(grad_phi[q]) < INFINITY)) return fail(GENASIS_EINVAL, "potential gradient must be finite");
+  int on = 0;
+  for (int q = 0; q < 3; ++q) {
+    h->grad_phi[q] = q < h->ndim ? grad_phi[q] : 0.0;
+    on |= h->grad_phi[q] != 0.0;
+  }
+  h->has_source = on;
+  for (int b = 0; b < 2; ++b)  // captured step graphs hold the old arguments
+    if (h->graph[b]) {
+      cudaGraphExecDestroy(h->graph[b]);
+      h->graph[b] = nullptr;
+    }
+  return GENASIS_OK;
 }
 
 int genasis_hydro_get_step_totals(genasis_hydro_t h, double* totals) {

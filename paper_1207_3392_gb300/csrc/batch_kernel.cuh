@@ -82,6 +82,8 @@ struct BatchKernel {
     A.part_tot = nullptr;
     A.status = B.status + p;
     A.want_totals = 0;
+    A.has_source = 0;
+    A.grad_phi[0] = A.grad_phi[1] = A.grad_phi[2] = T(0);
     return A;
   }
 

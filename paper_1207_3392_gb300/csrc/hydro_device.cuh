@@ -64,6 +64,11 @@ __device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
 __device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ double frcp(double x) { return 1.0 / x; }
 __device__ __forceinline__ float frcp(float x) { return __fdividef(1.0f, x); }
+// Correctly rounded sum that the compiler may not fuse with a product feeding
+// it: keeps the stage combine bitwise the same in every kernel that inlines it,
+// whatever the surrounding code lets the compiler contract.
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
 // sqrt of a positive argument
 __device__ __forceinline__ double fsqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float fsqrt(float x) { return x * rsqrtf(x); }

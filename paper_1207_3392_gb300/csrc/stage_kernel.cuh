@@ -43,6 +43,8 @@ struct StageArgs {
   double* part_tot;           // stage 1: per-CTA sums of U dV, [nblocks][NV]
   unsigned* status;
   int want_totals;
+  int has_source;             // external-force source on (Sec. 4.3.2)
+  T grad_phi[3];              // gradient of the linear external potential
 };
 
 template <int NDIM, class T, int SOLVER, int STAGE, int TX, int TY>
@@ -336,6 +338,17 @@ struct StageKernel {
           if constexpr (MARCH) d += (fhi[v] - flo[v]) * iwm;
           L[v] = -d;
         }
+        if (A.has_source) {
+          // external force and power (Sec. 4.3.2): S_q -= D dPhi/dq,
+          // G -= sum_q S_q dPhi/dq, from this cell's stage-input state
+          T power = T(0);
+#pragma unroll
+          for (int q = 0; q < NDIM; ++q) {
+            L[1 + q] -= wown[0] * A.grad_phi[q];
+            power = fma(wown[0] * wown[1 + q], A.grad_phi[q], power);
+          }
+          L[NV - 1] -= power;
+        }
         const size_t c = cell(A, ca, cb, m);
         bad |= nonphysical(wown, A.gm1);
         if (STAGE == 1) {
@@ -357,7 +370,7 @@ struct StageKernel {
 #pragma unroll
           for (int v = 0; v < NV; ++v) {
             const T u0 = __ldg(A.un + v * vs + c), k = __ldg(A.k1 + v * vs + c);
-            A.out[v * vs + c] = fma(hdt, k + L[v], u0);
+            A.out[v * vs + c] = fma(hdt, add_rn(k, L[v]), u0);
           }
         }
       }

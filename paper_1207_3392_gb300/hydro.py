@@ -65,6 +65,7 @@ SIGNATURES = {
     "genasis_hydro_set_conserved_async": [_P, _P, _I],
     "genasis_hydro_get_conserved_async": [_P, _P, _I],
     "genasis_hydro_sync": [_P],
+    "genasis_hydro_set_potential_gradient": [_P, _P],
     "genasis_hydro_set_tile": [_P, _I, _I],
     "genasis_hydro_get_tile": [_P, _P],
     "genasis_hydro_autotune": [_P, _I, ctypes.c_char_p],
@@ -185,6 +186,8 @@ class Hydro:
     def from_problem(cls, prob, precision=FP64, solver=None, stream=None, set_state=True):
         h = cls(prob.ndim, prob.n, prob.widths, prob.bc_lo, prob.bc_hi, prob.gamma,
                 prob.solver if solver is None else solver, prob.theta, precision, stream)
+        if any(getattr(prob, "grad_phi", (0.0, 0.0, 0.0))):
+            h.set_potential_gradient(prob.grad_phi)
         if set_state:
             h.set_primitive(prob.rho, prob.vel, prob.p)
         return h
@@ -237,6 +240,12 @@ class Hydro:
     def sync(self):
         """Wait for the handle's stream; raises on a non-physical state."""
         check(load().genasis_hydro_sync(self._h))
+
+    def set_potential_gradient(self, grad_phi):
+        """External force -grad Phi of a linear potential (Sec. 4.3.2)."""
+        g = np.zeros(3)
+        g[: len(grad_phi)] = grad_phi
+        check(load().genasis_hydro_set_potential_gradient(self._h, g.ctypes.data))
 
     # -- stepping -------------------------------------------------------------
     def compute_dt(self, cfl):

@@ -46,6 +46,7 @@ class Problem:
     t_end: float = 0.0
     steps: int = 0
     origin: tuple = (0.0, 0.0, 0.0)
+    grad_phi: tuple = (0.0, 0.0, 0.0)  # gradient of a linear external potential (force -grad Phi)
     meta: dict = field(default_factory=dict)
 
     @property
@@ -217,6 +218,37 @@ def kelvin_helmholtz(n=256, seed=0, solver=HLLC, t_end=1.0, amp_modes=0.01, amp_
     return _make("kelvin_helmholtz", 2, (n, n), [w, w], ((PERIODIC,) * 2, (PERIODIC,) * 2), 1.4,
                  rho, np.stack([vx, vy]), p, (-0.5, -0.5), t_end=t_end, cfl=0.5, solver=solver,
                  meta={"seed": seed, "phases": phases})
+
+
+def rayleigh_taylor(nx=256, ny=768, solver=HLLC, g=0.1, amp=0.01, t_end=8.5):
+    """Rayleigh-Taylor set-up of Sec. 4.3.2: [-0.25, 0.25] x [-0.75, 0.75],
+    periodic in x, reflecting in y; rho = 2 above y = 0, 1 below; uniform
+    force -g y^ (potential gradient (0, g)); hydrostatic p = 2.5 - rho g y;
+    gamma = 1.4; v = A/4 [1 + cos(2 pi x / Lx)] [1 + cos(3 pi y)] y^."""
+    lx, ly = 0.5, 1.5
+    wx = uniform_widths(nx, -0.25, 0.25)
+    wy = uniform_widths(ny, -0.75, 0.75)
+    x = -0.25 + (np.arange(nx) + 0.5) * (lx / nx)
+    y = -0.75 + (np.arange(ny) + 0.5) * (ly / ny)
+    X, Y = np.meshgrid(x, y)
+    rho = np.where(Y > 0.0, 2.0, 1.0)
+    p = 2.5 - rho * g * Y
+    vy = 0.25 * amp * (1.0 + np.cos(2.0 * np.pi * X / lx)) * (1.0 + np.cos(3.0 * np.pi * Y))
+    vel = np.stack([np.zeros_like(vy), vy])
+    return _make("rayleigh_taylor", 2, (nx, ny), [wx, wy], ((PERIODIC, REFLECT), (PERIODIC, REFLECT)), 1.4,
+                 rho, vel, p, (-0.25, -0.75), t_end=t_end, cfl=0.5, solver=solver, grad_phi=(0.0, g, 0.0))
+
+
+def free_fall(ndim, n, grad_phi, rho=1.0, p=1.0, gamma=1.4, solver=HLLC):
+    """Uniform gas at rest in a periodic box under a uniform force -grad Phi:
+    every flux divergence vanishes, so S_q(t) = -rho grad_phi_q t and
+    G(t) = G(0) + rho |grad_phi|^2 t^2 / 2 exactly (RK2 integrates both
+    exactly)."""
+    shape = (n,) * ndim
+    w = uniform_widths(n, 0.0, 1.0)
+    return _make("free_fall", ndim, shape, [w] * ndim, ((PERIODIC,) * ndim, (PERIODIC,) * ndim), gamma,
+                 np.full(shape, rho), np.zeros((ndim,) + shape), np.full(shape, p), (0.0,) * ndim,
+                 cfl=0.5, solver=solver, grad_phi=tuple(grad_phi) + (0.0,) * (3 - len(grad_phi)))
 
 
 # --------------------------------------------------------------------------- 3D

@@ -92,6 +92,63 @@ def test_stretched_pulse_reduced():
     _check(Ug, Uo, 3, TOL_FP32, "stretched 80^3")
 
 
+@pytest.mark.parametrize("solver", [H.HLL, H.HLLC])
+def test_rayleigh_taylor_reduced(solver):
+    """Rayleigh-Taylor set-up of Sec. 4.3.2 (uniform external force, periodic
+    x, reflecting y) at 32 x 96 for 60 steps."""
+    pr = P.rayleigh_taylor(32, 96, solver=solver)
+    Uo, to = oracle_run(pr, steps=60)
+    # FP32 momenta: in hydrostatic balance the momentum tendency is the
+    # difference of the pressure-flux difference (p ~ 2.5, formed in FP32) and
+    # the source rho g, each ~ rho g; the FP32 rounding of p, 2.5 x 6e-8,
+    # against rho g dy ~ 1.6e-3 is a relative error of ~1e-4 on a tendency
+    # that the small perturbation velocities only barely exceed.  Density and
+    # energy keep the 1e-5 bar.
+    tol32 = np.array([TOL_FP32, 3e-4, 3e-4, TOL_FP32])
+    for precision, tol in ((H.FP64, TOL_FP64), (H.FP32_MIXED, tol32)):
+        Ug, tg = gpu_run(pr, precision, steps=60)
+        assert tg == pytest.approx(to, rel=1e-9 if precision == H.FP64 else 1e-5)
+        _check(Ug, Uo, 2, tol, f"rayleigh-taylor prec={precision}")
+
+
+def test_potential_gradient_on_every_axis_3d():
+    """A force with components on all three axes (x and y in the tile plane,
+    z along the march) on random blocks with reflecting walls."""
+    pr = P.random_blocks(3, (30, 26, 22), seed=21, bc=P.REFLECT).with_(grad_phi=(0.3, -0.2, 0.5))
+    Uo, _ = oracle_run(pr, steps=8)
+    for precision, tol in PRECISIONS:
+        Ug, _ = gpu_run(pr, precision, steps=8)
+        _check(Ug, Uo, 3, tol, f"3d source prec={precision}")
+
+
+def test_free_fall_closed_form_gpu():
+    """Uniform gas in a periodic box: S(t) = -rho grad_phi t and
+    G(t) = G(0) + rho |grad_phi|^2 t^2 / 2 exactly; switching the source off
+    again gives the plain step bitwise."""
+    grad = (0.2, -0.5, 0.35)
+    pr = P.free_fall(3, 16, grad, rho=1.3, p=0.9)
+    h = H.Hydro.from_problem(pr, precision=H.FP64)
+    G0 = h.get_conserved()[-1].copy()
+    t = 0.0
+    for dt in (0.02, 0.013, 0.031):
+        h.step(dt)
+        t += dt
+    U = h.get_conserved()
+    for q in range(3):
+        np.testing.assert_allclose(U[1 + q], -1.3 * grad[q] * t, rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(U[-1], G0 + 0.5 * 1.3 * sum(x * x for x in grad) * t * t, rtol=1e-13)
+    h.set_potential_gradient((0.0, 0.0, 0.0))
+    h2 = H.Hydro.from_problem(pr.with_(grad_phi=(0.0, 0.0, 0.0)), precision=H.FP64)
+    h2.set_conserved(U)
+    h.step(0.01)
+    h2.step(0.01)
+    np.testing.assert_array_equal(h.get_conserved(), h2.get_conserved())
+    with pytest.raises(H.HydroError):
+        h.set_potential_gradient((0.0, float("nan"), 0.0))
+    h.close()
+    h2.close()
+
+
 def test_kelvin_helmholtz_reduced():
     """Periodic shear layer at 64^2, HLLC, FP32-mixed and FP64, 40 steps."""
     pr = P.kelvin_helmholtz(64, seed=5)
