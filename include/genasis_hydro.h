@@ -63,6 +63,10 @@ extern "C" {
 #define GENASIS_FP64 0         /* state stored and processed in FP64 */
 #define GENASIS_FP32_MIXED 1   /* state stored and fluxes in FP32; internal-energy
                                   cancellation, dt and totals reductions in FP64 */
+#define GENASIS_FP64_DW 2      /* state and arithmetic as double-word pairs of FP32
+                                  (hi + lo, ~48 bits) on the FP32 pipes; the same
+                                  results as GENASIS_FP64 to ~1e-13; host arrays are
+                                  FP64 (or FP32) and converted on the device */
 
 typedef struct genasis_hydro *genasis_hydro_t;
 
@@ -75,7 +79,7 @@ typedef struct genasis_hydro *genasis_hydro_t;
  *   gamma       adiabatic index of p = (gamma - 1) e (> 1)
  *   solver      GENASIS_HLL or GENASIS_HLLC
  *   theta       slope limiter parameter of Eq. MinMod, in [1, 2] (paper: 1.4)
- *   precision   GENASIS_FP64 or GENASIS_FP32_MIXED
+ *   precision   GENASIS_FP64, GENASIS_FP32_MIXED or GENASIS_FP64_DW
  *   stream      cudaStream_t to run on, or NULL for a stream owned by the handle */
 typedef struct {
   int ndim;

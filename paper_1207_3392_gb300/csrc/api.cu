@@ -10,6 +10,7 @@
 #include <string.h>
 
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "genasis_hydro.h"
@@ -42,17 +43,21 @@ bool is_device_ptr(const void* p) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
-int tile_count(int ndim, bool fp64) {
+int tile_count(int ndim, int prec) {
+  if (prec == GENASIS_FP64_DW) return tile_count_dw(ndim);
+  const bool fp64 = prec == GENASIS_FP64;
   return ndim == 1 ? tile_count_1d() : ndim == 2 ? tile_count_2d() : fp64 ? tile_count_3d_f64() : tile_count_3d_f32();
 }
 
-bool stage_variant(int ndim, bool fp64, int solver, int stage, int tile, StageVariant* out) {
+bool stage_variant(int ndim, int prec, int solver, int stage, int tile, StageVariant* out) {
+  if (prec == GENASIS_FP64_DW) return stage_variant_dw(ndim, solver, stage, tile, out);
+  const bool fp64 = prec == GENASIS_FP64;
   if (ndim == 1) return stage_variant_1d(fp64, solver, stage, tile, out);
   if (ndim == 2) return stage_variant_2d(fp64, solver, stage, tile, out);
   return fp64 ? stage_variant_3d_f64(solver, stage, tile, out) : stage_variant_3d_f32(solver, stage, tile, out);
 }
 
-int stage_tile_count(int ndim, bool fp64) { return tile_count(ndim, fp64); }
+int stage_tile_count(int ndim, int prec) { return tile_count(ndim, prec); }
 
 }  // namespace gh
 
@@ -75,6 +80,7 @@ struct genasis_hydro {
   void* iw[3] = {nullptr, nullptr, nullptr};
   double* wd[3] = {nullptr, nullptr, nullptr};
   float* wpair[3] = {nullptr, nullptr, nullptr};  // FP32 state: widths as hi[n] then lo[n]
+  dw* wdw[3] = {nullptr, nullptr, nullptr};       // double-word state: widths as pairs
   double* part_speed = nullptr;
   double* part_tot = nullptr;
   size_t part_cap = 0;  // blocks the partial buffers hold
@@ -112,7 +118,7 @@ int validate(const genasis_hydro_desc* d) {
   if (!(d->gamma > 1.0) || !isfinite(d->gamma)) return fail(GENASIS_EINVAL, "gamma must be > 1");
   if (d->solver != GENASIS_HLL && d->solver != GENASIS_HLLC) return fail(GENASIS_EINVAL, "bad solver %d", d->solver);
   if (!(d->theta >= 1.0 && d->theta <= 2.0)) return fail(GENASIS_EINVAL, "theta must lie in [1, 2]");
-  if (d->precision != GENASIS_FP64 && d->precision != GENASIS_FP32_MIXED)
+  if (d->precision != GENASIS_FP64 && d->precision != GENASIS_FP32_MIXED && d->precision != GENASIS_FP64_DW)
     return fail(GENASIS_EINVAL, "bad precision %d", d->precision);
   size_t cells = 1;
   for (int q = 0; q < d->ndim; ++q) {
@@ -149,15 +155,20 @@ int upload_geometry(genasis_hydro* h, const genasis_hydro_desc* d) {
       GH_CK(cudaMalloc(&h->wpair[q], pair.size() * sizeof(float)));
       GH_CK(cudaMemcpy(h->wpair[q], pair.data(), pair.size() * sizeof(float), cudaMemcpyHostToDevice));
     }
+    if (std::is_same<T, dw>::value) {
+      std::vector<dw> pw(w.begin(), w.end());
+      GH_CK(cudaMalloc(&h->wdw[q], pw.size() * sizeof(dw)));
+      GH_CK(cudaMemcpy(h->wdw[q], pw.data(), pw.size() * sizeof(dw), cudaMemcpyHostToDevice));
+    }
   }
   return GENASIS_OK;
 }
 
 int configure(genasis_hydro* h, int tile, int kchunk_req) {
-  if (tile < 0 || tile >= tile_count(h->ndim, h->prec == GENASIS_FP64)) return fail(GENASIS_EINVAL, "tile %d out of range", tile);
+  if (tile < 0 || tile >= tile_count(h->ndim, h->prec)) return fail(GENASIS_EINVAL, "tile %d out of range", tile);
   StageVariant v1, v2;
-  const bool fp64 = h->prec == GENASIS_FP64;
-  if (!stage_variant(h->ndim, fp64, h->solver, 1, tile, &v1) || !stage_variant(h->ndim, fp64, h->solver, 2, tile, &v2))
+  if (!stage_variant(h->ndim, h->prec, h->solver, 1, tile, &v1) ||
+      !stage_variant(h->ndim, h->prec, h->solver, 2, tile, &v2))
     return fail(GENASIS_EINVAL, "no compiled kernel for this configuration");
   const int gx = (h->n[0] + v1.tx - 1) / v1.tx;
   const int gy = h->ndim == 3 ? (h->n[1] + v1.ty - 1) / v1.ty : 1;
@@ -223,6 +234,9 @@ StageArgs<T> stage_args(genasis_hydro* h, int stage) {
       const size_t nq = q < h->ndim ? (size_t)h->n[q] : 2;
       A.wdh[q] = (const T*)h->wpair[q];
       A.wdl[q] = (const T*)(h->wpair[q] + nq);
+    } else if (std::is_same<T, dw>::value) {
+      A.wdh[q] = (const T*)h->wdw[q];
+      A.wdl[q] = (const T*)h->wdw[q];
     } else {
       A.wdh[q] = (const T*)h->wd[q];
       A.wdl[q] = (const T*)h->wd[q];
@@ -275,8 +289,9 @@ int enqueue_step_t(genasis_hydro* h, int mode, double fixed_dt, double cfl, doub
 
 int enqueue_step(genasis_hydro* h, int mode, double fixed_dt, double cfl, double t_end,
                  cudaEvent_t* ev = nullptr) {
-  return h->prec == GENASIS_FP64 ? enqueue_step_t<double>(h, mode, fixed_dt, cfl, t_end, ev)
-                                 : enqueue_step_t<float>(h, mode, fixed_dt, cfl, t_end, ev);
+  return h->prec == GENASIS_FP64         ? enqueue_step_t<double>(h, mode, fixed_dt, cfl, t_end, ev)
+         : h->prec == GENASIS_FP32_MIXED ? enqueue_step_t<float>(h, mode, fixed_dt, cfl, t_end, ev)
+                                         : enqueue_step_t<dw>(h, mode, fixed_dt, cfl, t_end, ev);
 }
 
 template <class T>
@@ -305,10 +320,14 @@ int reduce_now(genasis_hydro* h, bool speed) {
     ReduceArgs<double> A = reduce_args<double>(h);
     nblk = A.nblk;
     GH_CK(speed ? launch_speed<double>(h->ndim, A, h->stream) : launch_totals<double>(h->ndim, A, h->stream));
-  } else {
+  } else if (h->prec == GENASIS_FP32_MIXED) {
     ReduceArgs<float> A = reduce_args<float>(h);
     nblk = A.nblk;
     GH_CK(speed ? launch_speed<float>(h->ndim, A, h->stream) : launch_totals<float>(h->ndim, A, h->stream));
+  } else {
+    ReduceArgs<dw> A = reduce_args<dw>(h);
+    nblk = A.nblk;
+    GH_CK(speed ? launch_speed<dw>(h->ndim, A, h->stream) : launch_totals<dw>(h->ndim, A, h->stream));
   }
   FinalizeArgs F;
   memset(&F, 0, sizeof(F));
@@ -348,9 +367,13 @@ int import_array(genasis_hydro* h, const void* src, int src_prec, size_t count, 
     GH_CK(cudaMemcpyAsync(tmp, src, count * ssize, cudaMemcpyHostToDevice, h->stream));
     dsrc = tmp;
   }
-  cudaError_t e = src_prec == GENASIS_FP64
-                      ? launch_convert<double, float>(count, (const double*)dsrc, (float*)dst, h->stream)
-                      : launch_convert<float, double>(count, (const float*)dsrc, (double*)dst, h->stream);
+  cudaError_t e;
+  if (h->prec == GENASIS_FP64_DW)
+    e = src_prec == GENASIS_FP64 ? launch_convert<double, dw>(count, (const double*)dsrc, (dw*)dst, h->stream)
+                                 : launch_convert<float, dw>(count, (const float*)dsrc, (dw*)dst, h->stream);
+  else
+    e = src_prec == GENASIS_FP64 ? launch_convert<double, float>(count, (const double*)dsrc, (float*)dst, h->stream)
+                                 : launch_convert<float, double>(count, (const float*)dsrc, (double*)dst, h->stream);
   if (tmp) cudaFreeAsync(tmp, h->stream);
   GH_CK(e);
   return GENASIS_OK;
@@ -369,9 +392,14 @@ int export_array(genasis_hydro* h, void* U, int precision) {
   const size_t dsize = precision == GENASIS_FP64 ? 8 : 4;
   void* dst = U;
   if (!dev) GH_CK(cudaMallocAsync(&dst, count * dsize, h->stream));
-  cudaError_t e = h->prec == GENASIS_FP64
-                      ? launch_convert<double, float>(count, (const double*)h->U[h->cur], (float*)dst, h->stream)
-                      : launch_convert<float, double>(count, (const float*)h->U[h->cur], (double*)dst, h->stream);
+  const void* src = h->U[h->cur];
+  cudaError_t e;
+  if (h->prec == GENASIS_FP64_DW)
+    e = precision == GENASIS_FP64 ? launch_convert<dw, double>(count, (const dw*)src, (double*)dst, h->stream)
+                                  : launch_convert<dw, float>(count, (const dw*)src, (float*)dst, h->stream);
+  else
+    e = h->prec == GENASIS_FP64 ? launch_convert<double, float>(count, (const double*)src, (float*)dst, h->stream)
+                                : launch_convert<float, double>(count, (const float*)src, (double*)dst, h->stream);
   GH_CK(e);
   if (!dev) {
     GH_CK(cudaMemcpyAsync(U, dst, count * dsize, cudaMemcpyDeviceToHost, h->stream));
@@ -391,6 +419,7 @@ int free_all(genasis_hydro* h) {
     cudaFree(h->iw[q]);
     cudaFree(h->wd[q]);
     cudaFree(h->wpair[q]);
+    cudaFree(h->wdw[q]);
   }
   cudaFree(h->part_speed);
   cudaFree(h->part_tot);
@@ -426,7 +455,7 @@ int genasis_hydro_create(const genasis_hydro_desc* d, genasis_hydro_t* out) {
   h->theta = d->theta;
   h->solver = d->solver;
   h->prec = d->precision;
-  h->esize = h->prec == GENASIS_FP64 ? 8 : 4;
+  h->esize = h->prec == GENASIS_FP32_MIXED ? 4 : 8;
 #define GH_CK_CREATE(call)                                                                          \
   do {                                                                                              \
     cudaError_t e_ = (call);                                                                        \
@@ -455,7 +484,9 @@ int genasis_hydro_create(const genasis_hydro_desc* d, genasis_hydro_t* out) {
   GH_CK_CREATE(cudaMemsetAsync(h->scal, 0, SCAL_COUNT * sizeof(double), h->stream));
   GH_CK_CREATE(cudaMalloc(&h->status, sizeof(unsigned)));
   GH_CK_CREATE(cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream));
-  rc = h->prec == GENASIS_FP64 ? upload_geometry<double>(h, d) : upload_geometry<float>(h, d);
+  rc = h->prec == GENASIS_FP64         ? upload_geometry<double>(h, d)
+       : h->prec == GENASIS_FP32_MIXED ? upload_geometry<float>(h, d)
+                                       : upload_geometry<dw>(h, d);
   if (!rc) rc = configure(h, 0, 0);
   if (rc) {
     free_all(h);
@@ -488,9 +519,13 @@ int genasis_hydro_set_primitive(genasis_hydro_t h, const double* rho, const doub
     const double* r = dev[0] ? dev[0] : rho;
     const double* v = dev[1] ? dev[1] : vel;
     const double* pp = dev[2] ? dev[2] : p;
-    cudaError_t e = h->prec == GENASIS_FP64
-                        ? launch_init_from_primitive<double>(h->ndim, h->ncell, h->gamma, r, v, pp, (double*)h->U[h->cur], h->stream)
-                        : launch_init_from_primitive<float>(h->ndim, h->ncell, h->gamma, r, v, pp, (float*)h->U[h->cur], h->stream);
+    void* U = h->U[h->cur];
+    cudaError_t e =
+        h->prec == GENASIS_FP64
+            ? launch_init_from_primitive<double>(h->ndim, h->ncell, h->gamma, r, v, pp, (double*)U, h->stream)
+        : h->prec == GENASIS_FP32_MIXED
+            ? launch_init_from_primitive<float>(h->ndim, h->ncell, h->gamma, r, v, pp, (float*)U, h->stream)
+            : launch_init_from_primitive<dw>(h->ndim, h->ncell, h->gamma, r, v, pp, (dw*)U, h->stream);
     if (e != cudaSuccess) rc = fail(GENASIS_ECUDA, "init kernel: %s", cudaGetErrorString(e));
   }
   for (int a = 0; a < 3; ++a)
@@ -646,7 +681,7 @@ int genasis_hydro_get_tile(genasis_hydro_t h, int* info) {
   info[2] = h->v1.ty;
   info[3] = h->kchunk;
   info[4] = (int)(h->grid.x * h->grid.y * h->grid.z);
-  info[5] = tile_count(h->ndim, h->prec == GENASIS_FP64);
+  info[5] = tile_count(h->ndim, h->prec);
   return GENASIS_OK;
 }
 
@@ -778,7 +813,7 @@ int genasis_hydro_autotune(genasis_hydro_t h, int trial_steps, const char* cache
         }
       }
       fclose(f);
-      if (tile >= 0 && tile < tile_count(h->ndim, h->prec == GENASIS_FP64)) return configure(h, tile, kc);
+      if (tile >= 0 && tile < tile_count(h->ndim, h->prec)) return configure(h, tile, kc);
     }
   }
   // save state, time, status
@@ -796,7 +831,7 @@ int genasis_hydro_autotune(genasis_hydro_t h, int trial_steps, const char* cache
   int best_tile = 0, best_kc = 0;
   int rc = GENASIS_OK;
   const int nm = h->ndim >= 2 ? h->n[h->ndim - 1] : 1;
-  for (int tile = 0; tile < tile_count(h->ndim, h->prec == GENASIS_FP64) && !rc; ++tile) {
+  for (int tile = 0; tile < tile_count(h->ndim, h->prec) && !rc; ++tile) {
     std::vector<int> kcs = {0};
     if (h->ndim >= 2)
       for (int kc : {12, 16, 24, 32, 48, 64})

@@ -213,5 +213,13 @@ template cudaError_t launch_speed<float>(int, const ReduceArgs<float>&, cudaStre
 template cudaError_t launch_speed<double>(int, const ReduceArgs<double>&, cudaStream_t);
 template cudaError_t launch_totals<float>(int, const ReduceArgs<float>&, cudaStream_t);
 template cudaError_t launch_totals<double>(int, const ReduceArgs<double>&, cudaStream_t);
+template cudaError_t launch_init_from_primitive<dw>(int, size_t, double, const double*, const double*, const double*,
+                                                    dw*, cudaStream_t);
+template cudaError_t launch_convert<double, dw>(size_t, const double*, dw*, cudaStream_t);
+template cudaError_t launch_convert<float, dw>(size_t, const float*, dw*, cudaStream_t);
+template cudaError_t launch_convert<dw, double>(size_t, const dw*, double*, cudaStream_t);
+template cudaError_t launch_convert<dw, float>(size_t, const dw*, float*, cudaStream_t);
+template cudaError_t launch_speed<dw>(int, const ReduceArgs<dw>&, cudaStream_t);
+template cudaError_t launch_totals<dw>(int, const ReduceArgs<dw>&, cudaStream_t);
 
 }  // namespace gh

@@ -8,6 +8,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "dword.cuh"
+
 namespace gh {
 
 enum : int { BC_PERIODIC = 0, BC_REFLECT = 1, BC_OUTFLOW = 2 };
@@ -72,6 +74,11 @@ __device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, 
 // sqrt of a positive argument
 __device__ __forceinline__ double fsqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float fsqrt(float x) { return x * rsqrtf(x); }
+// double-word: the operations of dword.cuh
+__device__ __forceinline__ dw fdiv(dw a, dw b) { return a / b; }
+__device__ __forceinline__ dw frcp(dw x) { return dw(1.0f, 0.0f) / x; }
+__device__ __forceinline__ dw fsqrt(dw x) { return sqrt(x); }
+__device__ __forceinline__ dw add_rn(dw a, dw b) { return a + b; }
 
 // ---------------------------------------------------------------------------
 // Conserved -> primitive recovery.
@@ -103,6 +110,21 @@ __device__ __forceinline__ void recover(const double (&u)[NDIM + 2], double (&w)
 static __device__ __noinline__ float energy_density_times_n_fp64(float n, float s1, float s2, float s3, float G) {
   const double s2d = fma((double)s1, (double)s1, fma((double)s2, (double)s2, (double)s3 * (double)s3));
   return (float)fma(-0.5, s2d, (double)G * (double)n);
+}
+
+// Double-word path: the FP64 formulas in double-word arithmetic.
+template <int NDIM>
+__device__ __forceinline__ void recover(const dw (&u)[NDIM + 2], dw (&w)[NDIM + 2]) {
+  constexpr int NV = NDIM + 2;
+  const dw rn = frcp(u[0]);
+  dw v2 = dw(0.0f, 0.0f);
+  w[0] = u[0];
+#pragma unroll
+  for (int q = 0; q < NDIM; ++q) {
+    w[1 + q] = u[1 + q] * rn;
+    v2 = fma(w[1 + q], w[1 + q], v2);
+  }
+  w[NV - 1] = u[NV - 1] - dw(0.5f, 0.0f) * u[0] * v2;
 }
 
 template <int NDIM>
@@ -250,6 +272,14 @@ struct ColumnSum<float> {
     lo += err + pe;
   }
   __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+// Double-word state: the column sum in double-word arithmetic (dz as a pair).
+template <>
+struct ColumnSum<dw> {
+  dw s = dw(0.0f, 0.0f);
+  __device__ __forceinline__ void add_product(dw u, dw dz, dw) { s = fma(u, dz, s); }
+  __device__ __forceinline__ double value() const { return (double)s; }
 };
 
 // Deterministic block reductions (fixed shuffle tree, then warps in order).

@@ -110,7 +110,8 @@ static int noalloc_step_t(const genasis_hydro_desc* d, unsigned char* base, cons
   // launch configuration: tile 0, about four CTAs per SM, at least 8 planes per CTA
   StageVariant v1, v2;
   const bool fp64 = sizeof(T) == 8;
-  if (!stage_variant(ndim, fp64, d->solver, 1, 0, &v1) || !stage_variant(ndim, fp64, d->solver, 2, 0, &v2))
+  const int prec = fp64 ? GENASIS_FP64 : GENASIS_FP32_MIXED;
+  if (!stage_variant(ndim, prec, d->solver, 1, 0, &v1) || !stage_variant(ndim, prec, d->solver, 2, 0, &v2))
     return fail(GENASIS_EINVAL, "step_noalloc: no compiled kernel for this configuration");
   int dev = 0, sms = 0;
   GH_CK(cudaGetDevice(&dev));

@@ -14,10 +14,14 @@ struct StageVariant {
   int threads;         // threads per CTA
 };
 
-// Tile shapes compiled per dimensionality and precision; index `tile` selects one.
-int stage_tile_count(int ndim, bool fp64);
-// Fills *out for (ndim, fp64?, solver, stage, tile); returns false if absent.
-bool stage_variant(int ndim, bool fp64, int solver, int stage, int tile, StageVariant* out);
+// Tile shapes compiled per dimensionality and precision (GENASIS_FP64,
+// GENASIS_FP32_MIXED, GENASIS_FP64_DW); index `tile` selects one.
+int stage_tile_count(int ndim, int prec);
+// Fills *out for (ndim, precision, solver, stage, tile); returns false if absent.
+bool stage_variant(int ndim, int prec, int solver, int stage, int tile, StageVariant* out);
+bool stage_variant_dw(int ndim, int solver, int stage, int tile, StageVariant* out);
+bool stage_variant_dw_3d(int solver, int stage, int tile, StageVariant* out);
+int tile_count_dw(int ndim);
 
 bool stage_variant_1d(bool fp64, int solver, int stage, int tile, StageVariant* out);
 bool stage_variant_2d(bool fp64, int solver, int stage, int tile, StageVariant* out);

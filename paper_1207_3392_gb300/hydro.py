@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(HERE, "_lib", "libgenasis_hydro.so")
 OK, EINVAL, ENOMEM, ECUDA, ENONPHYS, ETIMEOUT = 0, -1, -2, -3, -4, -5
 HLL, HLLC = 0, 1
 BC_PERIODIC, BC_REFLECT, BC_OUTFLOW = 0, 1, 2
-FP64, FP32_MIXED = 0, 1
+FP64, FP32_MIXED, FP64_DW = 0, 1, 2  # FP64_DW: double-word FP32 pairs on the device, FP64 on the host
 OPT_STEP_TOTALS = 1
 
 
@@ -162,7 +162,9 @@ class Hydro:
         self.ndim = int(ndim)
         self.n = tuple(int(x) for x in (list(n) + [1, 1, 1])[:3])
         self.precision = int(precision)
-        self.dtype = np.float64 if self.precision == FP64 else np.float32
+        # host arrays: FP32 for the FP32 state, FP64 otherwise
+        self.host_precision = FP32_MIXED if self.precision == FP32_MIXED else FP64
+        self.dtype = np.float64 if self.host_precision == FP64 else np.float32
         self._widths = [np.ascontiguousarray(widths[q], dtype=np.float64) for q in range(self.ndim)]
         d = Desc()
         d.ndim = self.ndim
@@ -200,7 +202,7 @@ class Hydro:
         check(load().genasis_hydro_set_primitive(self._h, pr, pv, pp))
 
     def set_conserved(self, U, precision=None):
-        precision = self.precision if precision is None else precision
+        precision = self.host_precision if precision is None else precision
         dt = np.float64 if precision == FP64 else np.float32
         pu, keep = _ptr(U, dt, self.ncell * self.nvar, "U")
         check(load().genasis_hydro_set_conserved(self._h, pu, precision))
@@ -208,7 +210,7 @@ class Hydro:
     def get_conserved(self, out=None, precision=None):
         """Return the conserved state, shape (nvar,) + shape; into `out` (numpy
         or torch, host or CUDA) if given."""
-        precision = self.precision if precision is None else precision
+        precision = self.host_precision if precision is None else precision
         dt = np.float64 if precision == FP64 else np.float32
         if out is None:
             out = np.empty((self.nvar,) + self.shape, dtype=dt)
@@ -219,7 +221,7 @@ class Hydro:
     def set_conserved_async(self, U, precision=None):
         """Enqueue the copy of U (page-locked host or device) without waiting;
         U must stay unchanged until sync()."""
-        precision = self.precision if precision is None else precision
+        precision = self.host_precision if precision is None else precision
         dt = np.float64 if precision == FP64 else np.float32
         pu, keep = _ptr(U, dt, self.ncell * self.nvar, "U")
         if keep is not U:
@@ -229,7 +231,7 @@ class Hydro:
     def get_conserved_async(self, out, precision=None):
         """Enqueue the copy of the state into `out` without waiting; read it
         after sync()."""
-        precision = self.precision if precision is None else precision
+        precision = self.host_precision if precision is None else precision
         dt = np.float64 if precision == FP64 else np.float32
         po, keep = _ptr(out, dt, self.ncell * self.nvar, "out")
         if keep is not out:

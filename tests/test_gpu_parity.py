@@ -158,7 +158,8 @@ def test_kelvin_helmholtz_reduced():
         _check(Ug, Uo, 2, tol, f"kh prec={precision}")
 
 
-@pytest.mark.parametrize("ndim,precision", [(3, H.FP32_MIXED), (3, H.FP64), (2, H.FP32_MIXED), (1, H.FP32_MIXED)])
+@pytest.mark.parametrize("ndim,precision", [(3, H.FP32_MIXED), (3, H.FP64), (2, H.FP32_MIXED), (1, H.FP32_MIXED),
+                                            (3, H.FP64_DW)])
 def test_every_tile_shape_identical(ndim, precision):
     """Each compiled tile shape and plane count gives bitwise the same state."""
     shape = {3: (70, 34, 41), 2: (150, 97), 1: (700,)}[ndim]
@@ -171,6 +172,28 @@ def test_every_tile_shape_identical(ndim, precision):
         for kc in ((0, 7, shape[-1]) if ndim > 1 else (0,)):
             U, _ = gpu_run(pr, precision, steps=4, tile=tile, kchunk=kc)
             np.testing.assert_array_equal(U, ref, err_msg=f"tile {tile} kchunk {kc}")
+
+
+DW_CASES = {
+    "sod_1d": lambda: (P.sod(256), 200),
+    "blocks_2d_reflect": lambda: (P.random_blocks(2, (70, 45), seed=4, bc=P.REFLECT), 20),
+    "blocks_3d_periodic": lambda: (P.random_blocks(3, (36, 28, 22), seed=6, bc=P.PERIODIC), 8),
+    "blocks_3d_outflow": lambda: (P.random_blocks(3, (30, 34, 26), seed=8, bc=P.OUTFLOW), 8),
+    "sedov_48": lambda: (P.sedov_3d(48), 40),
+    "stretched_40": lambda: (P.stretched_pulse_3d(40, steps=10), 10),
+    "kelvin_helmholtz_64": lambda: (P.kelvin_helmholtz(64, seed=5), 40),
+    "rayleigh_taylor_32x96": lambda: (P.rayleigh_taylor(32, 96), 40),
+}
+
+
+@pytest.mark.parametrize("case", sorted(DW_CASES))
+def test_double_word_matches_oracle(case):
+    """Double-word FP32 pairs (GENASIS_FP64_DW) hold the FP64 parity bar."""
+    pr, steps = DW_CASES[case]()
+    Uo, to = oracle_run(pr, steps=steps)
+    Ug, tg = gpu_run(pr, H.FP64_DW, steps=steps)
+    assert tg == pytest.approx(to, rel=1e-10)
+    _check(Ug, Uo, pr.ndim, TOL_FP64, f"double-word {case}")
 
 
 def test_fixed_dt_step_matches_oracle():
