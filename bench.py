@@ -462,7 +462,7 @@ def run_batch(args):
     all_specs = shard.weak_scaling_specs(world)
     specs = shard.rank_specs(all_specs, rank, world)
     total_cells = sum(sp.n ** sp.ndim for sp in all_specs)
-    prec = H.FP32_MIXED if args.precision == "fp32" else H.FP64
+    prec = {"fp32": H.FP32_MIXED, "fp64": H.FP64, "fp64dw": H.FP64_DW}[args.precision]
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
 
@@ -515,7 +515,8 @@ def run_batch(args):
     info = b.tile_info()
     line = {"metric": METRIC, "value": total_cells * 2 / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if esz == 4 else "f64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {H.FP32_MIXED: "f32", H.FP64: "f64", H.FP64_DW: "f32x2 double-word"}[prec], "data": "synthetic",
             "config": {"workload": f"batched_riemann_4096_{args.precision}", "problems": len(all_specs),
                        "cells": total_cells, "rank0_problems": len(specs), "rank0_cells": cells,
                        "parallelism": f"{world} GPU(s), problems LPT-sharded by cells x steps, no exchange",

@@ -133,9 +133,10 @@ int configure(genasis_batch* b, int tile, int chunk) {
   if (tile < 0 || tile >= batch_tile_count()) return fail(GENASIS_EINVAL, "batch tile %d out of range", tile);
   if (chunk < 0) return fail(GENASIS_EINVAL, "chunk < 0");
   BatchVariant v1, v2;
-  const bool ok = b->prec == GENASIS_FP64
-                      ? batch_variant_f64(b->solver, 1, tile, &v1) && batch_variant_f64(b->solver, 2, tile, &v2)
-                      : batch_variant_f32(b->solver, 1, tile, &v1) && batch_variant_f32(b->solver, 2, tile, &v2);
+  const bool ok =
+      b->prec == GENASIS_FP64         ? batch_variant_f64(b->solver, 1, tile, &v1) && batch_variant_f64(b->solver, 2, tile, &v2)
+      : b->prec == GENASIS_FP32_MIXED ? batch_variant_f32(b->solver, 1, tile, &v1) && batch_variant_f32(b->solver, 2, tile, &v2)
+                                      : batch_variant_dw(b->solver, 1, tile, &v1) && batch_variant_dw(b->solver, 2, tile, &v2);
   if (!ok) return fail(GENASIS_EINVAL, "no compiled batch kernel for this configuration");
   const int tx = v1.tx;
   if (chunk == 0) chunk = 32;
@@ -226,8 +227,9 @@ int enqueue_batch_step_t(genasis_batch* b, int mode, double cfl, double t_end, u
 
 int enqueue_batch_step(genasis_batch* b, double cfl, double t_end, unsigned* c1, unsigned* c2,
                        cudaEvent_t* ev = nullptr) {
-  return b->prec == GENASIS_FP64 ? enqueue_batch_step_t<double>(b, FIN_CFL, cfl, t_end, c1, c2, ev)
-                                 : enqueue_batch_step_t<float>(b, FIN_CFL, cfl, t_end, c1, c2, ev);
+  return b->prec == GENASIS_FP64         ? enqueue_batch_step_t<double>(b, FIN_CFL, cfl, t_end, c1, c2, ev)
+         : b->prec == GENASIS_FP32_MIXED ? enqueue_batch_step_t<float>(b, FIN_CFL, cfl, t_end, c1, c2, ev)
+                                         : enqueue_batch_step_t<dw>(b, FIN_CFL, cfl, t_end, c1, c2, ev);
 }
 
 int ensure_counters(genasis_batch* b, int n) {
@@ -305,13 +307,14 @@ int genasis_batch_create(int nprob, const genasis_batch_problem* probs, int solv
   if (nprob < 1 || !probs) return fail(GENASIS_EINVAL, "need at least one problem");
   if (solver != GENASIS_HLL && solver != GENASIS_HLLC) return fail(GENASIS_EINVAL, "bad solver");
   if (!(theta >= 1.0 && theta <= 2.0)) return fail(GENASIS_EINVAL, "theta must lie in [1, 2]");
-  if (precision != GENASIS_FP64 && precision != GENASIS_FP32_MIXED) return fail(GENASIS_EINVAL, "bad precision");
+  if (precision != GENASIS_FP64 && precision != GENASIS_FP32_MIXED && precision != GENASIS_FP64_DW)
+    return fail(GENASIS_EINVAL, "bad precision");
   genasis_batch* b = new genasis_batch();
   b->nprob = nprob;
   b->solver = solver;
   b->theta = theta;
   b->prec = precision;
-  b->esize = precision == GENASIS_FP64 ? 8 : 4;
+  b->esize = precision == GENASIS_FP32_MIXED ? 4 : 8;
   b->hp.resize(nprob);
   for (int p = 0; p < nprob; ++p) {
     const genasis_batch_problem& d = probs[p];
@@ -390,7 +393,9 @@ int genasis_batch_create(int nprob, const genasis_batch_problem* probs, int solv
   BCK(cudaMemsetAsync(b->t, 0, nprob * sizeof(double), b->stream));
   BCK(cudaMemsetAsync(b->speed, 0, nprob * sizeof(unsigned long long), b->stream));
   BCK(cudaMemsetAsync(b->status, 0, nprob * sizeof(unsigned), b->stream));
-  int rc = b->prec == GENASIS_FP64 ? upload_tables<double>(b, probs) : upload_tables<float>(b, probs);
+  int rc = b->prec == GENASIS_FP64         ? upload_tables<double>(b, probs)
+           : b->prec == GENASIS_FP32_MIXED ? upload_tables<float>(b, probs)
+                                           : upload_tables<dw>(b, probs);
   if (!rc) rc = configure(b, 0, 0);
   if (rc) {
     free_batch(b);
@@ -427,11 +432,15 @@ int genasis_batch_set_primitive(genasis_batch_t b, int iprob, const double* rho,
     use[a] = tmp[a];
   }
   if (!rc) {
-    cudaError_t e = b->prec == GENASIS_FP64
-                        ? launch_init_from_primitive<double>(h.ndim, h.ncell, h.gamma, use[0], use[1], use[2],
-                                                             (double*)b->U[b->cur] + h.off, b->stream)
-                        : launch_init_from_primitive<float>(h.ndim, h.ncell, h.gamma, use[0], use[1], use[2],
-                                                            (float*)b->U[b->cur] + h.off, b->stream);
+    cudaError_t e =
+        b->prec == GENASIS_FP64
+            ? launch_init_from_primitive<double>(h.ndim, h.ncell, h.gamma, use[0], use[1], use[2],
+                                                 (double*)b->U[b->cur] + h.off, b->stream)
+        : b->prec == GENASIS_FP32_MIXED
+            ? launch_init_from_primitive<float>(h.ndim, h.ncell, h.gamma, use[0], use[1], use[2],
+                                                (float*)b->U[b->cur] + h.off, b->stream)
+            : launch_init_from_primitive<dw>(h.ndim, h.ncell, h.gamma, use[0], use[1], use[2], (dw*)b->U[b->cur] + h.off,
+                                             b->stream);
     if (e != cudaSuccess) rc = fail(GENASIS_ECUDA, "init kernel: %s", cudaGetErrorString(e));
   }
   for (int a = 0; a < 3; ++a)
@@ -456,9 +465,13 @@ int genasis_batch_get_conserved(genasis_batch_t b, int iprob, void* U, int preci
     const size_t dsize = precision == GENASIS_FP64 ? 8 : 4;
     void* dst = U;
     if (!dev) GH_CK(cudaMallocAsync(&dst, count * dsize, b->stream));
-    cudaError_t e = b->prec == GENASIS_FP64
-                        ? launch_convert<double, float>(count, (const double*)src, (float*)dst, b->stream)
-                        : launch_convert<float, double>(count, (const float*)src, (double*)dst, b->stream);
+    cudaError_t e;
+    if (b->prec == GENASIS_FP64_DW)
+      e = precision == GENASIS_FP64 ? launch_convert<dw, double>(count, (const dw*)src, (double*)dst, b->stream)
+                                    : launch_convert<dw, float>(count, (const dw*)src, (float*)dst, b->stream);
+    else
+      e = b->prec == GENASIS_FP64 ? launch_convert<double, float>(count, (const double*)src, (float*)dst, b->stream)
+                                  : launch_convert<float, double>(count, (const float*)src, (double*)dst, b->stream);
     GH_CK(e);
     if (!dev) {
       GH_CK(cudaMemcpyAsync(U, dst, count * dsize, cudaMemcpyDeviceToHost, b->stream));

@@ -14,5 +14,6 @@ struct BatchVariant {
 int batch_tile_count();
 bool batch_variant_f32(int solver, int stage, int tile, BatchVariant* out);
 bool batch_variant_f64(int solver, int stage, int tile, BatchVariant* out);
+bool batch_variant_dw(int solver, int stage, int tile, BatchVariant* out);
 
 }  // namespace gh

@@ -371,6 +371,7 @@ class Batch:
     def __init__(self, problems, solver=HLLC, theta=1.4, precision=FP64, stream=None):
         lib = load()
         self.precision = int(precision)
+        self.host_precision = FP32_MIXED if self.precision == FP32_MIXED else FP64
         self.nprob = len(problems)
         self._keep = []
         arr = (BatchProblemDesc * self.nprob)()
