@@ -40,7 +40,7 @@ def _args():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp64dw"])
-    ap.add_argument("--solver", default="hllc", choices=["hllc", "hll"])
+    ap.add_argument("--solver", default="hllc", choices=["hllc", "hll", "hllc_switch"])
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -61,7 +61,7 @@ def _dist():
 
 def _workload(n, solver_name):
     from paper_1207_3392_gb300 import problems as P
-    solver = P.HLLC if solver_name == "hllc" else P.HLL
+    solver = {"hllc": P.HLLC, "hll": P.HLL, "hllc_switch": P.HLLC_SWITCH}[solver_name]
     return P.sedov_3d(n, solver=solver)
 
 
@@ -146,6 +146,7 @@ def _peaks():
 #   (HLLC 96 / HLL 90 each), divergence 40, stage combine (stage 2: U^1 on
 #   load 10 + final 15; stage 1: CFL speed 15 + totals 10)
 FLOPS_3D = {"hllc": 12 + 150 + 60 + 3 * 96 + 40 + 25, "hll": 12 + 150 + 60 + 3 * 90 + 40 + 25}
+FLOPS_3D["hllc_switch"] = FLOPS_3D["hllc"]  # away from shocks; the detector's own work is not counted
 # Vector peak of this GPU: 152 SMs x 128 lanes x 2 (FMA) x 2.07 GHz (FP32);
 # FP64 at the nominal 1.25 TFLOP/s.
 PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
@@ -199,7 +200,7 @@ def run_reference(args):
     n_sample = args.n
     cores = os.cpu_count() or 1
     os.environ.setdefault("OMP_NUM_THREADS", str(cores))
-    pr = P.sedov_3d(n_sample, solver=P.HLLC if args.solver == "hllc" else P.HLL)
+    pr = P.sedov_3d(n_sample, solver={"hllc": P.HLLC, "hll": P.HLL, "hllc_switch": P.HLLC_SWITCH}[args.solver])
     g = O.Grid(pr)
     U = O.initial_state(pr, g)
     U, _, _ = O.evolve(g, U, pr.cfl, max_steps=args.warmup)
@@ -377,7 +378,8 @@ def run_ours(args):
         for pname, pc, sname, totals in (("fp32", H.FP32_MIXED, args.solver, False),
                                          ("fp32", H.FP32_MIXED, "hllc", True), ("fp32", H.FP32_MIXED, "hll", True),
                                          ("fp64", H.FP64, "hllc", True), ("fp64", H.FP64, "hll", True),
-                                         ("fp64dw", H.FP64_DW, "hllc", True)):
+                                         ("fp64dw", H.FP64_DW, "hllc", True),
+                                         ("fp32", H.FP32_MIXED, "hllc_switch", True)):
                 if (pname, sname, totals) == (args.precision, args.solver, True):
                     continue
                 pr = _workload(n, sname)

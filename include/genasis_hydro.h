@@ -55,6 +55,15 @@ extern "C" {
 
 #define GENASIS_HLL 0
 #define GENASIS_HLLC 1
+/* HLLC, switching to HLL in the vicinity of a shock on the faces transverse to
+ * its motion (Sec. 3.2; the detector, which the paper does not give, is: a
+ * cell lies on a shock moving along axis r when, across its two neighbours
+ * along r, v_r decreases and the pressure jumps by more than half the smaller
+ * pressure; a face normal to q takes HLL when either of its cells lies on a
+ * shock moving along an axis other than q).  The bits come from each RK
+ * stage's input state.  2D and 3D, GENASIS_FP64 or GENASIS_FP32_MIXED; in 1D
+ * it is plain HLLC. */
+#define GENASIS_HLLC_SWITCH 2
 
 #define GENASIS_BC_PERIODIC 0  /* wrap-around */
 #define GENASIS_BC_REFLECT 1   /* mirror, normal momentum negated */

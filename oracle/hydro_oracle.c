@@ -50,6 +50,10 @@
  *   - No floors: a non-positive density or pressure, or a non-finite value, in
  *     an interior cell makes the call return OG_ENONPHYS.
  * *   - m (average baryon mass) = 1 throughout, so rho = n.
+ *   - HLLC with the shock switch (solver 2): a face normal to q takes the HLL
+ *     flux when either of its two cells lies on a shock moving along another
+ *     axis r != q (detector above, from the stage's input state); a ghost cell
+ *     carries the flags of the interior cell it is filled from.
  *   - The source vector of Sec. 4.3.2 is printed without a sign; the force
  *     -grad Phi must pull the fluid down the potential, so the source is
  *     S = -[0, m D dPhi/dx_q, (S . grad Phi)] (momentum q and energy).
@@ -66,7 +70,14 @@
 #define OG_NG 2
 
 enum { OG_PERIODIC = 0, OG_REFLECT = 1, OG_OUTFLOW = 2 };
-enum { OG_HLL = 0, OG_HLLC = 1 };
+enum { OG_HLL = 0, OG_HLLC = 1, OG_HLLC_SWITCH = 2 };
+
+/* Shock detector of the HLLC -> HLL switch (Sec. 3.2 describes the switch but
+ * not the detector; this criterion is this implementation's reading): a cell
+ * lies on a shock moving along axis r when, across its two neighbours along r,
+ * the flow is compressive (v_r(+) - v_r(-) < 0) and the pressure jumps by more
+ * than OG_SHOCK_JUMP of the smaller pressure. */
+#define OG_SHOCK_JUMP 0.5
 enum { OG_OK = 0, OG_EINVAL = -1, OG_ENOMEM = -2, OG_ENONPHYS = -4 };
 
 typedef struct {
@@ -310,6 +321,28 @@ static int og_rhs_grid(const og_grid *G, const og_desc *d, const double *U, doub
 
   for (size_t t = 0; t < nv * nin; ++t) L[t] = 0.0;
 
+  /* shock flags of the interior cells (bit r: on a shock moving along r) */
+  unsigned char *flag = NULL;
+  if (d->solver == OG_HLLC_SWITCH) {
+    flag = (unsigned char *)calloc(nin, 1);
+    if (!flag) { free(Ue); free(We); free(Win); free(Wout); return OG_ENOMEM; }
+    for (int k = 0; k < G->n[2]; ++k)
+      for (int j = 0; j < G->n[1]; ++j)
+        for (int i = 0; i < G->n[0]; ++i) {
+          unsigned char bits = 0;
+          for (int r = 0; r < nd; ++r) {
+            int cm[3] = {i, j, k}, cp[3] = {i, j, k};
+            cm[r] -= 1; cp[r] += 1;
+            size_t tm = og_at(G, cm[0], cm[1], cm[2]), tp = og_at(G, cp[0], cp[1], cp[2]);
+            double pm = (d->gamma - 1.0) * We[(size_t)(nd + 1) * ne + tm];
+            double pp = (d->gamma - 1.0) * We[(size_t)(nd + 1) * ne + tp];
+            double vm = We[(size_t)(1 + r) * ne + tm], vp = We[(size_t)(1 + r) * ne + tp];
+            if (vp - vm < 0.0 && fabs(pp - pm) > OG_SHOCK_JUMP * fmin(pp, pm)) bits |= (unsigned char)(1u << r);
+          }
+          flag[((size_t)k * G->n[1] + j) * G->n[0] + i] = bits;
+        }
+  }
+
   for (int q = 0; q < nd; ++q) {
     const double *wq = G->w[q];  /* wq[c + NG] = width of cell c along q */
     /* differences and reconstructed face values: interior cells plus one
@@ -356,7 +389,17 @@ static int og_rhs_grid(const og_grid *G, const og_desc *d, const double *U, doub
           size_t tr = og_at(G, c[0], c[1], c[2]), tl = og_at(G, cl[0], cl[1], cl[2]);
           double WL[5], WR[5], F[5];
           for (int v = 0; v < nv; ++v) { WL[v] = Wout[(size_t)v * ne + tl]; WR[v] = Win[(size_t)v * ne + tr]; }
-          og_face_flux(d->solver, d->gamma, nd, q, WL, WR, F, NULL);
+          int solver = d->solver;
+          if (solver == OG_HLLC_SWITCH) {
+            /* flags of the two cells; a ghost (along q) takes its source cell's */
+            int fl_, sl[3] = {cl[0], cl[1], cl[2]}, sr[3] = {c[0], c[1], c[2]};
+            if (sl[q] < 0) sl[q] = og_ghost_src(sl[q], G->n[q], d->bc_lo[q], &fl_);
+            if (sr[q] >= G->n[q]) sr[q] = og_ghost_src(sr[q], G->n[q], d->bc_hi[q], &fl_);
+            unsigned char bits = flag[((size_t)sl[2] * G->n[1] + sl[1]) * G->n[0] + sl[0]] |
+                                 flag[((size_t)sr[2] * G->n[1] + sr[1]) * G->n[0] + sr[0]];
+            solver = (bits & (unsigned char)~(1u << q)) ? OG_HLL : OG_HLLC;
+          }
+          og_face_flux(solver, d->gamma, nd, q, WL, WR, F, NULL);
           if (f >= 1) {          /* outer face of cell f-1 */
             size_t li = ((size_t)cl[2] * G->n[1] + cl[1]) * G->n[0] + cl[0];
             double inv = 1.0 / wq[f - 1 + OG_NG];
@@ -379,7 +422,7 @@ static int og_rhs_grid(const og_grid *G, const og_desc *d, const double *U, doub
       const double *wq = G->w[q];
       /* centre coordinates of cells -1 .. n_q (origin at the low face of cell 0) */
       double *xc = (double *)malloc(sizeof(double) * (G->n[q] + 2));
-      if (!xc) { free(Ue); free(We); free(Win); free(Wout); return OG_ENOMEM; }
+      if (!xc) { free(flag); free(Ue); free(We); free(Win); free(Wout); return OG_ENOMEM; }
       xc[1] = 0.5 * wq[OG_NG];
       for (int c = 1; c < G->n[q]; ++c) xc[c + 1] = xc[c] + 0.5 * (wq[c - 1 + OG_NG] + wq[c + OG_NG]);
       xc[0] = xc[1] - 0.5 * (wq[OG_NG - 1] + wq[OG_NG]);
@@ -399,6 +442,7 @@ static int og_rhs_grid(const og_grid *G, const og_desc *d, const double *U, doub
       free(xc);
     }
   }
+  free(flag);
   free(Ue); free(We); free(Win); free(Wout);
   return bad ? OG_ENONPHYS : OG_OK;
 }

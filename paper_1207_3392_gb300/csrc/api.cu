@@ -81,6 +81,7 @@ struct genasis_hydro {
   double* wd[3] = {nullptr, nullptr, nullptr};
   float* wpair[3] = {nullptr, nullptr, nullptr};  // FP32 state: widths as hi[n] then lo[n]
   dw* wdw[3] = {nullptr, nullptr, nullptr};       // double-word state: widths as pairs
+  unsigned char* flags = nullptr;                 // shock bits (GENASIS_HLLC_SWITCH)
   double* part_speed = nullptr;
   double* part_tot = nullptr;
   size_t part_cap = 0;  // blocks the partial buffers hold
@@ -116,7 +117,10 @@ int validate(const genasis_hydro_desc* d) {
       return fail(GENASIS_EINVAL, "axis %d: periodic must be set on both ends", q);
   }
   if (!(d->gamma > 1.0) || !isfinite(d->gamma)) return fail(GENASIS_EINVAL, "gamma must be > 1");
-  if (d->solver != GENASIS_HLL && d->solver != GENASIS_HLLC) return fail(GENASIS_EINVAL, "bad solver %d", d->solver);
+  if (d->solver != GENASIS_HLL && d->solver != GENASIS_HLLC && d->solver != GENASIS_HLLC_SWITCH)
+    return fail(GENASIS_EINVAL, "bad solver %d", d->solver);
+  if (d->solver == GENASIS_HLLC_SWITCH && d->precision == GENASIS_FP64_DW)
+    return fail(GENASIS_EINVAL, "the shock switch is compiled for GENASIS_FP64 and GENASIS_FP32_MIXED");
   if (!(d->theta >= 1.0 && d->theta <= 2.0)) return fail(GENASIS_EINVAL, "theta must lie in [1, 2]");
   if (d->precision != GENASIS_FP64 && d->precision != GENASIS_FP32_MIXED && d->precision != GENASIS_FP64_DW)
     return fail(GENASIS_EINVAL, "bad precision %d", d->precision);
@@ -254,8 +258,32 @@ StageArgs<T> stage_args(genasis_hydro* h, int stage) {
   A.status = h->status;
   A.want_totals = h->want_totals;
   A.has_source = h->has_source;
+  A.flags = h->flags;
   for (int q = 0; q < 3; ++q) A.grad_phi[q] = (T)h->grad_phi[q];
   return A;
+}
+
+template <class T>
+int enqueue_flags(genasis_hydro* h, int stage) {
+  if constexpr (!std::is_same<T, dw>::value) {
+    if (h->solver != GENASIS_HLLC_SWITCH) return GENASIS_OK;
+    FlagArgs<T> F;
+    memset(&F, 0, sizeof(F));
+    for (int q = 0; q < 3; ++q) {
+      F.n[q] = h->n[q];
+      F.bc_lo[q] = h->bc_lo[q];
+      F.bc_hi[q] = h->bc_hi[q];
+    }
+    F.gamma = h->gamma;
+    F.un = (const T*)h->U[h->cur];
+    F.k1 = (const T*)h->K;
+    F.dt = h->scal + SCAL_DT;
+    F.flags = h->flags;
+    F.ncell = h->ncell;
+    F.stage = stage;
+    GH_CK(launch_shock_flags<T>(h->ndim, F, h->stream));
+  }
+  return GENASIS_OK;
 }
 
 template <class T>
@@ -264,6 +292,8 @@ int enqueue_step_t(genasis_hydro* h, int mode, double fixed_dt, double cfl, doub
   StageArgs<T> a1 = stage_args<T>(h, 1);
   void* p1[] = {&a1};
   if (ev) GH_CK(cudaEventRecord(ev[0], h->stream));
+  int rc = enqueue_flags<T>(h, 1);
+  if (rc) return rc;
   GH_CK(cudaLaunchKernel(h->v1.fn, h->grid, block, p1, h->v1.smem, h->stream));
   if (ev) GH_CK(cudaEventRecord(ev[1], h->stream));
   FinalizeArgs F;
@@ -281,6 +311,8 @@ int enqueue_step_t(genasis_hydro* h, int mode, double fixed_dt, double cfl, doub
   if (ev) GH_CK(cudaEventRecord(ev[2], h->stream));
   StageArgs<T> a2 = stage_args<T>(h, 2);
   void* p2[] = {&a2};
+  rc = enqueue_flags<T>(h, 2);
+  if (rc) return rc;
   GH_CK(cudaLaunchKernel(h->v2.fn, h->grid, block, p2, h->v2.smem, h->stream));
   if (ev) GH_CK(cudaEventRecord(ev[3], h->stream));
   h->cur = 1 - h->cur;
@@ -423,6 +455,7 @@ int free_all(genasis_hydro* h) {
   }
   cudaFree(h->part_speed);
   cudaFree(h->part_tot);
+  cudaFree(h->flags);
   cudaFree(h->scal);
   cudaFree(h->status);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -453,7 +486,8 @@ int genasis_hydro_create(const genasis_hydro_desc* d, genasis_hydro_t* out) {
   }
   h->gamma = d->gamma;
   h->theta = d->theta;
-  h->solver = d->solver;
+  // in 1D no face is transverse to a shock: the switch is plain HLLC
+  h->solver = d->solver == GENASIS_HLLC_SWITCH && d->ndim == 1 ? GENASIS_HLLC : d->solver;
   h->prec = d->precision;
   h->esize = h->prec == GENASIS_FP32_MIXED ? 4 : 8;
 #define GH_CK_CREATE(call)                                                                          \
@@ -480,6 +514,7 @@ int genasis_hydro_create(const genasis_hydro_desc* d, genasis_hydro_t* out) {
     GH_CK_CREATE(cudaMemsetAsync(h->U[b], 0, bytes, h->stream));
   }
   GH_CK_CREATE(cudaMalloc(&h->K, bytes));
+  if (h->solver == GENASIS_HLLC_SWITCH) GH_CK_CREATE(cudaMalloc(&h->flags, h->ncell));
   GH_CK_CREATE(cudaMalloc(&h->scal, SCAL_COUNT * sizeof(double)));
   GH_CK_CREATE(cudaMemsetAsync(h->scal, 0, SCAL_COUNT * sizeof(double), h->stream));
   GH_CK_CREATE(cudaMalloc(&h->status, sizeof(unsigned)));
@@ -769,7 +804,7 @@ int genasis_hydro_restrict(genasis_hydro_t h, int factor, float* U_coarse) {
 
 int genasis_hydro_launches_per_step(genasis_hydro_t h) {
   if (!h) return fail(GENASIS_EINVAL, "NULL handle");
-  return 3;
+  return h->solver == GENASIS_HLLC_SWITCH ? 5 : 3;
 }
 
 int genasis_hydro_profile_step(genasis_hydro_t h, double cfl, float* ms) {
@@ -832,6 +867,8 @@ int genasis_hydro_autotune(genasis_hydro_t h, int trial_steps, const char* cache
   int rc = GENASIS_OK;
   const int nm = h->ndim >= 2 ? h->n[h->ndim - 1] : 1;
   for (int tile = 0; tile < tile_count(h->ndim, h->prec) && !rc; ++tile) {
+    StageVariant probe;
+    if (!stage_variant(h->ndim, h->prec, h->solver, 1, tile, &probe)) continue;  // not compiled for this solver
     std::vector<int> kcs = {0};
     if (h->ndim >= 2)
       for (int kc : {12, 16, 24, 32, 48, 64})

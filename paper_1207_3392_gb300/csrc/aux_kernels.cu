@@ -157,6 +157,52 @@ __global__ void __launch_bounds__(256) finalize_kernel(FinalizeArgs A) {
   }
 }
 
+// Shock detector of the HLLC -> HLL switch (Sec. 3.2 describes the switch, not
+// the detector): cell c lies on a shock moving along axis r when, across its
+// two neighbours along r (boundary-mapped like the stage kernel's ghosts), the
+// flow is compressive, v_r(+) - v_r(-) < 0, and the pressure jumps by more
+// than half the smaller pressure.  Bit r of flags[c] records it.
+template <class T, int NDIM>
+__global__ void shock_flags_kernel(FlagArgs<T> A) {
+  constexpr int NV = NDIM + 2;
+  const T gm1 = (T)(A.gamma - 1.0);
+  const T dt = A.stage == 2 ? (T)(*A.dt) : T(0);
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < A.ncell; c += (size_t)gridDim.x * blockDim.x) {
+    int idx[3] = {0, 0, 0};
+    size_t r_ = c;
+#pragma unroll
+    for (int q = 0; q < NDIM; ++q) {
+      idx[q] = (int)(r_ % A.n[q]);
+      r_ /= A.n[q];
+    }
+    unsigned bits = 0;
+#pragma unroll
+    for (int r = 0; r < NDIM; ++r) {
+      T p[2], v[2];
+#pragma unroll
+      for (int side = 0; side < 2; ++side) {
+        int j[3] = {idx[0], idx[1], idx[2]};
+        bool flip = false;
+        j[r] = bc_map(idx[r] + (side ? 1 : -1), A.n[r], A.bc_lo[r], A.bc_hi[r], flip);
+        const size_t cc = ((size_t)j[2] * A.n[1] + j[1]) * A.n[0] + j[0];
+        T u[NV], w[NV];
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+          T x = A.un[k * A.ncell + cc];
+          if (A.stage == 2) x = fma(dt, A.k1[k * A.ncell + cc], x);
+          u[k] = x;
+        }
+        if (flip) u[1 + r] = -u[1 + r];
+        recover<NDIM>(u, w);
+        p[side] = gm1 * w[NV - 1];
+        v[side] = w[1 + r];
+      }
+      if (v[1] - v[0] < T(0) && fabs(p[1] - p[0]) > T(0.5) * fmin(p[0], p[1])) bits |= 1u << r;
+    }
+    A.flags[c] = (unsigned char)bits;
+  }
+}
+
 // ------------------------------------------------------------------ launchers
 
 static int grid_for(size_t count, int block, int max_blocks) {
@@ -198,6 +244,17 @@ cudaError_t launch_totals(int ndim, const ReduceArgs<T>& A, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+template <class T>
+cudaError_t launch_shock_flags(int ndim, const FlagArgs<T>& A, cudaStream_t s) {
+  const int nb = grid_for(A.ncell, 256, 4096);
+  switch (ndim) {
+    case 1: shock_flags_kernel<T, 1><<<nb, 256, 0, s>>>(A); break;
+    case 2: shock_flags_kernel<T, 2><<<nb, 256, 0, s>>>(A); break;
+    default: shock_flags_kernel<T, 3><<<nb, 256, 0, s>>>(A); break;
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_finalize(const FinalizeArgs& A, cudaStream_t s) {
   finalize_kernel<<<1, 256, 0, s>>>(A);
   return cudaGetLastError();
@@ -221,5 +278,7 @@ template cudaError_t launch_convert<dw, double>(size_t, const dw*, double*, cuda
 template cudaError_t launch_convert<dw, float>(size_t, const dw*, float*, cudaStream_t);
 template cudaError_t launch_speed<dw>(int, const ReduceArgs<dw>&, cudaStream_t);
 template cudaError_t launch_totals<dw>(int, const ReduceArgs<dw>&, cudaStream_t);
+template cudaError_t launch_shock_flags<float>(int, const FlagArgs<float>&, cudaStream_t);
+template cudaError_t launch_shock_flags<double>(int, const FlagArgs<double>&, cudaStream_t);
 
 }  // namespace gh

@@ -35,6 +35,24 @@ struct FinalizeArgs {
   unsigned* status;
 };
 
+// Shock bits of every cell for the HLLC -> HLL switch, from a stage's input
+// state (stage 1: U^n; stage 2: U^n + dt K).
+template <class T>
+struct FlagArgs {
+  int n[3];
+  int bc_lo[3], bc_hi[3];
+  double gamma;
+  const T* un;
+  const T* k1;        // stage 2 only
+  const double* dt;   // stage 2 only
+  unsigned char* flags;
+  size_t ncell;
+  int stage;
+};
+
+template <class T>
+cudaError_t launch_shock_flags(int ndim, const FlagArgs<T>& A, cudaStream_t s);
+
 template <class T>
 cudaError_t launch_init_from_primitive(int ndim, size_t ncell, double gamma, const double* rho, const double* vel,
                                        const double* p, T* U, cudaStream_t s);

@@ -83,6 +83,7 @@ struct BatchKernel {
     A.status = B.status + p;
     A.want_totals = 0;
     A.has_source = 0;
+    A.flags = nullptr;
     A.grad_phi[0] = A.grad_phi[1] = A.grad_phi[2] = T(0);
     return A;
   }

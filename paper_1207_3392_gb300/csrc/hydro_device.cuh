@@ -13,7 +13,8 @@
 namespace gh {
 
 enum : int { BC_PERIODIC = 0, BC_REFLECT = 1, BC_OUTFLOW = 2 };
-enum : int { SOLVER_HLL = 0, SOLVER_HLLC = 1 };
+// SOLVER_HLLC_SW: HLLC, with HLL on faces transverse to a shock (Sec. 3.2)
+enum : int { SOLVER_HLL = 0, SOLVER_HLLC = 1, SOLVER_HLLC_SW = 2 };
 enum : unsigned { STATUS_NONPHYS = 1u, STATUS_TIMEOUT = 2u };
 
 // Per-cell reconstruction geometry along one axis (Eq. MinMod with

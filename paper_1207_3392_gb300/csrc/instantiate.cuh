@@ -28,4 +28,13 @@ inline bool pick_variant(int solver, int stage, StageVariant* out) {
   return true;
 }
 
+// HLLC with the shock switch (compiled for one tile per dimensionality).
+template <int NDIM, class T, int TX, int TY, int MINB = 1>
+inline bool pick_switch(int stage, StageVariant* out) {
+  if (stage == 1) fill_variant<NDIM, T, SOLVER_HLLC_SW, 1, TX, TY, MINB>(out);
+  else if (stage == 2) fill_variant<NDIM, T, SOLVER_HLLC_SW, 2, TX, TY, MINB>(out);
+  else return false;
+  return true;
+}
+
 }  // namespace gh

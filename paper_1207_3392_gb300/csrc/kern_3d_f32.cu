@@ -9,6 +9,7 @@ int tile_count_3d_f32() { return 6; }
 // (80 registers, 24 resident warps); tile 3 keeps the uncapped allocation;
 // tiles 4 and 5 (512 threads) are in kern_3d_f32_wide.cu.
 bool stage_variant_3d_f32(int solver, int stage, int tile, StageVariant* out) {
+  if (solver == SOLVER_HLLC_SW) return tile == 0 && pick_switch<3, float, 32, 8, 3>(stage, out);
   switch (tile) {
     case 0: return pick_variant<3, float, 32, 8, 3>(solver, stage, out);
     case 1: return pick_variant<3, float, 32, 4, 6>(solver, stage, out);

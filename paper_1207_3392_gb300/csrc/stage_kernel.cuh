@@ -44,12 +44,14 @@ struct StageArgs {
   unsigned* status;
   int want_totals;
   int has_source;             // external-force source on (Sec. 4.3.2)
+  const unsigned char* flags; // SOLVER_HLLC_SW: per-cell shock bits (bit r: shock moving along r)
   T grad_phi[3];              // gradient of the linear external potential
 };
 
 template <int NDIM, class T, int SOLVER, int STAGE, int TX, int TY>
 struct StageKernel {
   static constexpr int NV = NDIM + 2;
+  static constexpr bool SW = SOLVER == SOLVER_HLLC_SW;  // per-face HLLC/HLL choice from shock bits
   static constexpr bool MARCH = NDIM >= 2;
   static constexpr bool HAS_Y = NDIM == 3;
   static constexpr int AM = NDIM - 1;  // march axis (2D: y, 3D: z)
@@ -68,6 +70,7 @@ struct StageKernel {
     T fx[NV][TY][TX + 1];
     T fy[HAS_Y ? NV : 1][HAS_Y ? TY + 1 : 1][TX];
     double red[NT / 32][NV + 1];
+    unsigned char fl[SW ? SY : 1][SW ? SX : 1];  // shock bits of the plane (own cells and halo)
   };
 
   // Linear index of cell (a, b, m): a = x, b = in-plane y (3D), m = march
@@ -96,9 +99,10 @@ struct StageKernel {
     return r;
   }
 
-  // Primitives of the (possibly ghost) cell (ref, m); see load_prim.
+  // Primitives of the (possibly ghost) cell (ref, m) and, for the shock
+  // switch, the shock bits of the interior cell it maps to.
   static __device__ __forceinline__ void load_col(const StageArgs<T>& A, const ColRef& r, int m, T dt, size_t vs,
-                                                  T (&w)[NV]) {
+                                                  T (&w)[NV], unsigned char& fl) {
     bool fm = false;
     size_t c = r.off;
     if constexpr (MARCH) {
@@ -116,6 +120,20 @@ struct StageKernel {
     if constexpr (HAS_Y) { if (r.fb) u[2] = -u[2]; }
     if constexpr (MARCH) { if (fm) u[1 + AM] = -u[1 + AM]; }
     recover<NDIM>(u, w);
+    if constexpr (SW) fl = A.flags[c];
+  }
+
+  // Face flux along axis Q; with the switch, HLL when either cell's shock
+  // bits name an axis other than Q (a shock moving transverse to the face).
+  template <int Q>
+  static __device__ __forceinline__ void flux(const StageArgs<T>& A, const T (&wl)[NV], const T (&wr)[NV],
+                                              unsigned bits, T (&f)[NV]) {
+    if constexpr (SW) {
+      if (bits & ~(1u << Q)) face_flux<T, NDIM, Q, SOLVER_HLL>(wl, wr, A.gamma, A.gm1, f);
+      else face_flux<T, NDIM, Q, SOLVER_HLLC>(wl, wr, A.gamma, A.gm1, f);
+    } else {
+      face_flux<T, NDIM, Q, SOLVER>(wl, wr, A.gamma, A.gm1, f);
+    }
   }
 
   static __device__ __forceinline__ Geo<T> geo(const StageArgs<T>& A, int q, int c) {
@@ -137,7 +155,7 @@ struct StageKernel {
       wl[v] = fma(limited_slope(w0, w1, w2, gl), gl.h, w1);
       wr[v] = fma(-limited_slope(w1, w2, w3, gr), gr.h, w2);
     }
-    face_flux<T, NDIM, 0, SOLVER>(wl, wr, A.gamma, A.gm1, f);
+    flux<0>(A, wl, wr, SW ? (unsigned)(S.fl[SW ? srow : 0][SW ? sl : 0] | S.fl[SW ? srow : 0][SW ? sl + 1 : 0]) : 0u, f);
 #pragma unroll
     for (int v = 0; v < NV; ++v) S.fx[v][frow][face] = f[v];
   }
@@ -153,7 +171,7 @@ struct StageKernel {
       wl[v] = fma(limited_slope(w0, w1, w2, gl), gl.h, w1);
       wr[v] = fma(-limited_slope(w1, w2, w3, gr), gr.h, w2);
     }
-    face_flux<T, NDIM, 1, SOLVER>(wl, wr, A.gamma, A.gm1, f);
+    flux<1>(A, wl, wr, SW ? (unsigned)(S.fl[SW ? sl : 0][SW ? scol : 0] | S.fl[SW ? sl + 1 : 0][SW ? scol : 0]) : 0u, f);
 #pragma unroll
     for (int v = 0; v < NV; ++v) S.fy[v][face][scol - 2] = f[v];
   }
@@ -162,14 +180,14 @@ struct StageKernel {
   // slope sa, geometry ga) and wb (above, slope sb, geometry gb).
   static __device__ __forceinline__ void m_face(const StageArgs<T>& A, const T (&wa)[NV], const T (&sa)[NV],
                                                 T ha, const T (&wb)[NV], const T (&sb)[NV], T hb,
-                                                T (&f)[NV]) {
+                                                unsigned bits, T (&f)[NV]) {
     T wl[NV], wr[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       wl[v] = fma(sa[v], ha, wa[v]);
       wr[v] = fma(-sb[v], hb, wb[v]);
     }
-    face_flux<T, NDIM, AM, SOLVER>(wl, wr, A.gamma, A.gm1, f);
+    flux<AM>(A, wl, wr, bits, f);
   }
 
   static __device__ __forceinline__ void slopes(const StageArgs<T>& A, const T (&wm)[NV], const T (&wc)[NV],
@@ -248,6 +266,7 @@ struct StageKernel {
     // comes from the same code (bitwise the same values as the neighbouring
     // chunk computes for the shared face).
     T wk[NV], wk1[NV], sk[NV], flo[NV];
+    unsigned char fk = 0, fk1 = 0;  // shock bits of the own column at m, m + 1 (switch only)
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       sk[v] = T(0);
@@ -255,19 +274,20 @@ struct StageKernel {
     }
     int mstart = m0;
     if constexpr (MARCH) {
-      load_col(A, own, m0 - 2, dt, vs, wk);
-      load_col(A, own, m0 - 1, dt, vs, wk1);
+      load_col(A, own, m0 - 2, dt, vs, wk, fk);
+      load_col(A, own, m0 - 1, dt, vs, wk1, fk1);
       mstart = m0 - 2;
     }
 
     for (int m = mstart; m < m1; ++m) {
       T fhi[NV], wk2[NV], sk1[NV];
       T wown[NV];
+      unsigned char fk2 = 0, fown = 0;
       if constexpr (MARCH) {
-        load_col(A, own, m + 2, dt, vs, wk2);
+        load_col(A, own, m + 2, dt, vs, wk2, fk2);
         const Geo<T> g0 = geo(A, AM, m), g1 = geo(A, AM, m + 1);
         slopes(A, wk, wk1, wk2, g1, sk1);
-        m_face(A, wk, sk, g0.h, wk1, sk1, g1.h, fhi);
+        m_face(A, wk, sk, g0.h, wk1, sk1, g1.h, (unsigned)(fk | fk1), fhi);
         if (m < m0) {  // warm-up planes: advance the ring only
 #pragma unroll
           for (int v = 0; v < NV; ++v) {
@@ -276,24 +296,30 @@ struct StageKernel {
             wk1[v] = wk2[v];
             sk[v] = sk1[v];
           }
+          fk = fk1;
+          fk1 = fk2;
           continue;
         }
 #pragma unroll
         for (int v = 0; v < NV; ++v) wown[v] = wk[v];
+        fown = fk;
       } else {
-        load_col(A, own, 0, dt, vs, wown);
+        load_col(A, own, 0, dt, vs, wown, fown);
       }
       // own cell into the shared plane
 #pragma unroll
       for (int v = 0; v < NV; ++v) S.w[v][HAS_Y ? ty + 2 : 0][tx + 2] = wown[v];
+      if constexpr (SW) S.fl[HAS_Y ? ty + 2 : 0][tx + 2] = fown;
       // cross-shaped in-plane halo
 #pragma unroll
       for (int k = 0; k < HSLOTS; ++k) {
         if (tid + k * NT < NHALO) {
           T wh[NV];
-          load_col(A, halo[k], m, dt, vs, wh);
+          unsigned char fh = 0;
+          load_col(A, halo[k], m, dt, vs, wh, fh);
 #pragma unroll
           for (int v = 0; v < NV; ++v) S.w[v][hsy[k]][hsx[k]] = wh[v];
+          if constexpr (SW) S.fl[hsy[k]][hsx[k]] = fh;
         }
       }
       __syncthreads();
@@ -382,6 +408,8 @@ struct StageKernel {
           wk1[v] = wk2[v];
           sk[v] = sk1[v];
         }
+        fk = fk1;
+        fk1 = fk2;
       }
     }
 

@@ -19,7 +19,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_lib", "libgenasis_hydro.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ENONPHYS, ETIMEOUT = 0, -1, -2, -3, -4, -5
-HLL, HLLC = 0, 1
+HLL, HLLC, HLLC_SWITCH = 0, 1, 2  # HLLC_SWITCH: HLLC with HLL transverse to shocks
 BC_PERIODIC, BC_REFLECT, BC_OUTFLOW = 0, 1, 2
 FP64, FP32_MIXED, FP64_DW = 0, 1, 2  # FP64_DW: double-word FP32 pairs on the device, FP64 on the host
 OPT_STEP_TOTALS = 1

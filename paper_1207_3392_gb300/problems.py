@@ -19,7 +19,7 @@ import math
 import numpy as np
 
 PERIODIC, REFLECT, OUTFLOW = 0, 1, 2
-HLL, HLLC = 0, 1
+HLL, HLLC, HLLC_SWITCH = 0, 1, 2  # HLLC_SWITCH: HLLC, with HLL transverse to shocks (Sec. 3.2)
 
 
 @dataclass
@@ -249,6 +249,58 @@ def free_fall(ndim, n, grad_phi, rho=1.0, p=1.0, gamma=1.4, solver=HLLC):
     return _make("free_fall", ndim, shape, [w] * ndim, ((PERIODIC,) * ndim, (PERIODIC,) * ndim), gamma,
                  np.full(shape, rho), np.zeros((ndim,) + shape), np.full(shape, p), (0.0,) * ndim,
                  cfl=0.5, solver=solver, grad_phi=tuple(grad_phi) + (0.0,) * (3 - len(grad_phi)))
+
+
+def planar_shock(nx=400, ny=20, mach=20.0, solver=HLLC, seed=0, noise=1e-6, gamma=1.4):
+    """A strong planar shock moving along +x into gas at rest (rho = 1, p = 1),
+    post-shock state from the Rankine-Hugoniot conditions, shock at 10% of the
+    channel; outflow in x, periodic in y; density noise of relative size
+    `noise` (seeded).  On a Cartesian mesh the HLLC flux lets the noise grow
+    into odd-even decoupling behind the shock (Quirk 1994); HLL does not."""
+    rho0, p0 = 1.0, 1.0
+    c0 = math.sqrt(gamma * p0 / rho0)
+    m2 = mach * mach
+    rho1 = rho0 * (gamma + 1.0) * m2 / ((gamma - 1.0) * m2 + 2.0)
+    p1 = p0 * (2.0 * gamma * m2 - (gamma - 1.0)) / (gamma + 1.0)
+    u1 = mach * c0 * (1.0 - rho0 / rho1)
+    lx, ly = nx / ny, 1.0
+    wx = uniform_widths(nx, 0.0, lx)
+    wy = uniform_widths(ny, 0.0, ly)
+    X = np.tile((np.arange(nx) + 0.5) * (lx / nx), (ny, 1))
+    behind = X < 0.1 * lx
+    rng = np.random.default_rng(seed)
+    rho = np.where(behind, rho1, rho0) * (1.0 + noise * rng.uniform(-1.0, 1.0, X.shape))
+    p = np.where(behind, p1, p0)
+    vx = np.where(behind, u1, 0.0)
+    return _make("planar_shock", 2, (nx, ny), [wx, wy], ((OUTFLOW, PERIODIC), (OUTFLOW, PERIODIC)), gamma,
+                 rho, np.stack([vx, np.zeros_like(vx)]), p, (0.0, 0.0), cfl=0.4, solver=solver,
+                 meta={"mach": mach, "post": (rho1, u1, p1)})
+
+
+def planar_shock_3d(n_long=96, n_cross=12, axis=2, mach=10.0, solver=HLLC, seed=0, noise=1e-6, gamma=1.4):
+    """The planar shock of planar_shock in 3D, moving along `axis` (outflow
+    along it, periodic across), with seeded density noise."""
+    rho0, p0 = 1.0, 1.0
+    c0 = math.sqrt(gamma * p0 / rho0)
+    m2 = mach * mach
+    rho1 = rho0 * (gamma + 1.0) * m2 / ((gamma - 1.0) * m2 + 2.0)
+    p1 = p0 * (2.0 * gamma * m2 - (gamma - 1.0)) / (gamma + 1.0)
+    u1 = mach * c0 * (1.0 - rho0 / rho1)
+    n = [n_cross] * 3
+    n[axis] = n_long
+    widths = [uniform_widths(n[q], 0.0, n[q] / n_cross) for q in range(3)]
+    shape = (n[2], n[1], n[0])
+    coord = (np.indices(shape)[2 - axis] + 0.5) / n_cross
+    behind = coord < 0.1 * n_long / n_cross
+    rng = np.random.default_rng(seed)
+    rho = np.where(behind, rho1, rho0) * (1.0 + noise * rng.uniform(-1.0, 1.0, shape))
+    p = np.where(behind, p1, p0)
+    vel = np.zeros((3,) + shape)
+    vel[axis] = np.where(behind, u1, 0.0)
+    bc = [PERIODIC] * 3
+    bc[axis] = OUTFLOW
+    return _make("planar_shock_3d", 3, tuple(n), widths, (tuple(bc), tuple(bc)), gamma, rho, vel, p,
+                 (0.0, 0.0, 0.0), cfl=0.3, solver=solver, meta={"mach": mach, "axis": axis})
 
 
 # --------------------------------------------------------------------------- 3D
