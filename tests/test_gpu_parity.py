@@ -382,3 +382,44 @@ def test_sedov_full_size_symmetry_and_mass():
     assert t1[4] == pytest.approx(t0[4], rel=1e-12)
     np.testing.assert_allclose(U[0], U[0][::-1, ::-1, ::-1], rtol=1e-12)
     np.testing.assert_allclose(U[0], np.transpose(U[0], (2, 1, 0)), rtol=1e-12)
+
+
+def test_largest_mesh_rows_match_the_1d_oracle():
+    """A mesh whose arrays hold more than 2^32 values per state (1100^3
+    cells x 5 variables, 80 GB of FP32 state): a Sod tube along x, uniform in
+    y and z, one CFL step.  Every (y, z) row must equal the 1D oracle's step
+    of the same tube (fluxes along y and z cancel exactly); rows are sampled
+    across the mesh, including the last planes, whose offsets need 64 bits."""
+    import torch
+    free, _ = torch.cuda.mem_get_info()
+    if free < 200e9:
+        pytest.skip(f"needs ~150 GB of free device memory, {free / 1e9:.0f} GB free")
+    n = 1100
+    tube = P.sod(n)
+    U1, t1 = oracle_run(tube, steps=1)   # 1D oracle, same CFL rule (1D speeds only)
+    shape = (n, n, n)
+    rho = torch.from_numpy(tube.rho).cuda().reshape(1, 1, n).expand(shape).contiguous()
+    vel = torch.zeros((3,) + shape, dtype=torch.float64, device="cuda")
+    p = torch.from_numpy(tube.p).cuda().reshape(1, 1, n).expand(shape).contiguous()
+    w = tube.widths[0]
+    pr3 = P.Problem(name="sod_tube_3d", ndim=3, n=(n, n, n), widths=[w, w, w],
+                    bc_lo=(P.OUTFLOW, P.PERIODIC, P.PERIODIC), bc_hi=(P.OUTFLOW, P.PERIODIC, P.PERIODIC),
+                    gamma=tube.gamma, rho=np.zeros(1), vel=np.zeros(1), p=np.zeros(1), solver=tube.solver,
+                    theta=tube.theta, cfl=tube.cfl)
+    h = H.Hydro.from_problem(pr3, precision=H.FP32_MIXED, set_state=False)
+    h.set_primitive(rho, vel, p)
+    del rho, vel, p
+    torch.cuda.empty_cache()
+    tg = h.advance(1, tube.cfl)
+    out = torch.empty((5,) + shape, dtype=torch.float32, device="cuda")
+    h.get_conserved(out)
+    h.close()
+    assert tg == pytest.approx(t1, rel=1e-6)
+    want = np.stack([U1[0], U1[1], np.zeros(n), np.zeros(n), U1[2]])
+    for (k, j) in ((0, 0), (n // 2, 7), (n - 1, n - 1), (n - 2, 3), (517, n - 5)):
+        row = out[:, k, j, :].double().cpu().numpy()
+        err = rel_l1(row[[0, 1, 4]], want[[0, 1, 4]], 1)
+        assert np.all(err <= TOL_FP32), (k, j, err)
+        assert np.abs(row[2:4]).max() == 0.0
+    del out
+    torch.cuda.empty_cache()
