@@ -61,7 +61,7 @@ def _load():
                            ("og_prim_to_cons", [D, P, P, P, P]), ("og_cons_to_prim", [D, P, P, P, P]),
                            ("og_riemann_flux", [ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, P, P, P, P]),
                            ("og_physical_flux", [ctypes.c_double, ctypes.c_int, ctypes.c_int, P, P]),
-                           ("og_face_fluxes_2d", [D, P, P, P])]:
+                           ("og_face_fluxes_2d", [D, P, P, P]), ("og_face_fluxes", [D, P, P, P, P])]:
             f = getattr(lib, name)
             f.argtypes = args
             f.restype = ctypes.c_int
@@ -225,6 +225,27 @@ def face_fluxes_2d(g: Grid, U):
     Fy = np.empty((4, ny + 1, nx))
     _check(lib.og_face_fluxes_2d(g._ptr(), pu, Fx.ctypes.data, Fy.ctypes.data), "face_fluxes_2d")
     return Fx, Fy
+
+
+def face_fluxes(g: Grid, U):
+    """Plain face fluxes along every axis: a list of arrays, axis q of shape
+    (nvar,) + (n_2', n_1', n_0') with one more face than cells along q."""
+    lib = _load()
+    U, pu = _arr(U)
+    out = []
+    ptrs = []
+    for q in range(3):
+        if q < g.ndim:
+            nf = [g.n[a] if a < g.ndim else 1 for a in range(3)]
+            nf[q] += 1
+            shape = (g.nvar,) + tuple(reversed(nf[: g.ndim]))
+            a = np.empty(shape)
+            out.append(a)
+            ptrs.append(a.ctypes.data)
+        else:
+            ptrs.append(None)
+    _check(lib.og_face_fluxes(g._ptr(), pu, *ptrs), "face_fluxes")
+    return out
 
 
 def minmod(a, b, c):

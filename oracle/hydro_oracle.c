@@ -678,5 +678,111 @@ out:
   return rc;
 }
 
+/* Plain face fluxes of a state in 1, 2 or 3 dimensions: F[q] holds, for axis
+ * q, [nv][faces] with the faces of axis q in x-fastest order over
+ * (n_0 + (q==0)) x (n_1 + (q==1)) x (n_2 + (q==2)); face index f along q lies
+ * between cells f-1 and f.  Same ghost filling, recovery, reconstruction and
+ * Riemann solver (including the shock switch) as og_rhs_grid, which this
+ * repeats without the divergence. */
+int og_face_fluxes(const og_desc *d, const double *U, double *F0, double *F1, double *F2) {
+  og_grid G;
+  int rc = og_grid_init(&G, d);
+  if (rc != OG_OK) { og_grid_free(&G); return rc; }
+  int nd = G.ndim, nv = G.nvar;
+  size_t ne = G.next, nin = (size_t)G.n[0] * G.n[1] * G.n[2];
+  double *Fq[3] = {F0, F1, F2};
+  double *Ue = (double *)malloc(sizeof(double) * nv * ne);
+  double *We = (double *)malloc(sizeof(double) * nv * ne);
+  double *Win = (double *)malloc(sizeof(double) * nv * ne);
+  double *Wout = (double *)malloc(sizeof(double) * nv * ne);
+  double *L = (double *)malloc(sizeof(double) * nv * nin);
+  if (!Ue || !We || !Win || !Wout || !L) { rc = OG_ENOMEM; goto done; }
+  /* the divergence is not needed, but og_rhs_grid's flags and face loops are
+   * reproduced here face by face */
+  for (size_t t = 0; t < nv * ne; ++t) Ue[t] = NAN;
+  for (int k = 0; k < G.n[2]; ++k)
+    for (int j = 0; j < G.n[1]; ++j)
+      for (int i = 0; i < G.n[0]; ++i)
+        for (int v = 0; v < nv; ++v)
+          Ue[(size_t)v * ne + og_at(&G, i, j, k)] = U[(size_t)v * nin + ((size_t)k * G.n[1] + j) * G.n[0] + i];
+  og_fill_ghosts(&G, d, Ue);
+  for (size_t t = 0; t < ne; ++t) {
+    double u[5] = {0, 0, 0, 0, 0}, w[5];
+    for (int v = 0; v < nv; ++v) u[v] = Ue[(size_t)v * ne + t];
+    og_prim_from_cons(nd, u, w);
+    for (int v = 0; v < nv; ++v) We[(size_t)v * ne + t] = w[v];
+  }
+  unsigned char *flag = NULL;
+  if (d->solver == OG_HLLC_SWITCH) {
+    flag = (unsigned char *)calloc(nin, 1);
+    if (!flag) { rc = OG_ENOMEM; goto done; }
+    for (int k = 0; k < G.n[2]; ++k)
+      for (int j = 0; j < G.n[1]; ++j)
+        for (int i = 0; i < G.n[0]; ++i) {
+          unsigned char bits = 0;
+          for (int r = 0; r < nd; ++r) {
+            int cm[3] = {i, j, k}, cp[3] = {i, j, k};
+            cm[r] -= 1; cp[r] += 1;
+            size_t tm = og_at(&G, cm[0], cm[1], cm[2]), tp = og_at(&G, cp[0], cp[1], cp[2]);
+            double pm = (d->gamma - 1.0) * We[(size_t)(nd + 1) * ne + tm];
+            double pp = (d->gamma - 1.0) * We[(size_t)(nd + 1) * ne + tp];
+            double vm = We[(size_t)(1 + r) * ne + tm], vp = We[(size_t)(1 + r) * ne + tp];
+            if (vp - vm < 0.0 && fabs(pp - pm) > OG_SHOCK_JUMP * fmin(pp, pm)) bits |= (unsigned char)(1u << r);
+          }
+          flag[((size_t)k * G.n[1] + j) * G.n[0] + i] = bits;
+        }
+  }
+  for (int q = 0; q < nd; ++q) {
+    const double *wq = G.w[q];
+    int lo[3] = {0, 0, 0}, hi[3] = {G.n[0], G.n[1], G.n[2]};
+    lo[q] = -1; hi[q] = G.n[q] + 1;
+    for (int k = lo[2]; k < hi[2]; ++k)
+      for (int j = lo[1]; j < hi[1]; ++j)
+        for (int i = lo[0]; i < hi[0]; ++i) {
+          int c[3] = {i, j, k}, cm[3] = {i, j, k}, cp[3] = {i, j, k};
+          cm[q] -= 1; cp[q] += 1;
+          size_t tc = og_at(&G, i, j, k), tm = og_at(&G, cm[0], cm[1], cm[2]), tp = og_at(&G, cp[0], cp[1], cp[2]);
+          double dm = wq[c[q] - 1 + OG_NG], dc = wq[c[q] + OG_NG], dp = wq[c[q] + 1 + OG_NG];
+          double dist_cm = 0.5 * (dm + dc), dist_pm = 0.5 * dm + dc + 0.5 * dp, dist_pc = 0.5 * (dc + dp);
+          for (int v = 0; v < nv; ++v) {
+            double Wc = We[(size_t)v * ne + tc], Wm = We[(size_t)v * ne + tm], Wp = We[(size_t)v * ne + tp];
+            double D = og_minmod3(d->theta * ((Wc - Wm) / dist_cm), (Wp - Wm) / dist_pm, d->theta * ((Wp - Wc) / dist_pc));
+            Win[(size_t)v * ne + tc] = Wc - D * (0.5 * dc);
+            Wout[(size_t)v * ne + tc] = Wc + D * (0.5 * dc);
+          }
+        }
+    int nf[3] = {G.n[0], G.n[1], G.n[2]};
+    nf[q] += 1;
+    size_t nfaces = (size_t)nf[0] * nf[1] * nf[2];
+    for (int k = 0; k < nf[2]; ++k)
+      for (int j = 0; j < nf[1]; ++j)
+        for (int i = 0; i < nf[0]; ++i) {
+          int cr[3] = {i, j, k}, cl[3] = {i, j, k};
+          cl[q] -= 1;
+          double WL[5], WR[5], F[5];
+          for (int v = 0; v < nv; ++v) {
+            WL[v] = Wout[(size_t)v * ne + og_at(&G, cl[0], cl[1], cl[2])];
+            WR[v] = Win[(size_t)v * ne + og_at(&G, cr[0], cr[1], cr[2])];
+          }
+          int solver = d->solver;
+          if (solver == OG_HLLC_SWITCH) {
+            int fl_, sl[3] = {cl[0], cl[1], cl[2]}, sr[3] = {cr[0], cr[1], cr[2]};
+            if (sl[q] < 0) sl[q] = og_ghost_src(sl[q], G.n[q], d->bc_lo[q], &fl_);
+            if (sr[q] >= G.n[q]) sr[q] = og_ghost_src(sr[q], G.n[q], d->bc_hi[q], &fl_);
+            unsigned char bits = flag[((size_t)sl[2] * G.n[1] + sl[1]) * G.n[0] + sl[0]] |
+                                 flag[((size_t)sr[2] * G.n[1] + sr[1]) * G.n[0] + sr[0]];
+            solver = (bits & (unsigned char)~(1u << q)) ? OG_HLL : OG_HLLC;
+          }
+          og_face_flux(solver, d->gamma, nd, q, WL, WR, F, NULL);
+          for (int v = 0; v < nv; ++v) Fq[q][(size_t)v * nfaces + ((size_t)k * nf[1] + j) * nf[0] + i] = F[v];
+        }
+  }
+  free(flag);
+done:
+  free(Ue); free(We); free(Win); free(Wout); free(L);
+  og_grid_free(&G);
+  return rc;
+}
+
 /* Exposed for the limiter unit test. */
 double og_minmod(double a, double b, double c) { return og_minmod3(a, b, c); }
