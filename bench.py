@@ -45,7 +45,8 @@ def _args():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="sedov", choices=["sedov", "batch", "learned"])
+    ap.add_argument("--workload", default="sedov", choices=["sedov", "batch", "learned", "fmr"])
+    ap.add_argument("--levels", type=int, default=4, help="fmr workload: nested levels")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default tile instead of autotuning")
     ap.add_argument("--tile", type=int, default=-1, help="use this tile (and --kchunk) instead of autotuning")
     ap.add_argument("--kchunk", type=int, default=0)
@@ -590,6 +591,67 @@ def run_learned(args):
         print(json.dumps(line), flush=True)
 
 
+def run_fmr(args):
+    """Point blast on nested levels (multilevel evolution with subcycling,
+    Algorithms Evolve / EvolveLevel / StepLevel): `levels` boxes of n^3 cells,
+    each covering the central half of its parent at twice its resolution, so
+    the finest level has the resolution of a (n 2^(levels-1))^3 single-level
+    mesh.  A step is one global step (2^l steps of level l)."""
+    import torch
+    from paper_1207_3392_gb300 import build
+    from paper_1207_3392_gb300 import hydro as H
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    build.build()
+    n = args.n if args.n != 256 else 128
+    L = args.levels
+    prec = {"fp32": H.FP32_MIXED, "fp64": H.FP64, "fp64dw": H.FP64}[args.precision]
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    g = H.Fmr(3, n, L, 1.0, 1, solver=H.HLLC if args.solver != "hll" else H.HLL, precision=prec, stream=stream)
+    gamma = 1.4
+    for l in range(L):
+        m = n + (4 if l else 0)
+        U = torch.zeros((5, m, m, m), dtype=torch.float64, device="cuda")
+        U[0] = 1.0
+        U[4] = 1e-5 / (gamma - 1.0)
+        if l == L - 1:
+            o = (2 if l else 0) + n // 2 - 1
+            h = 1.0 / n / 2 ** l
+            U[4, o:o + 2, o:o + 2, o:o + 2] = 1.0 / (8 * h ** 3)
+        g.set_level(l, U)
+        del U
+    # warm-up; the first global step also restricts the deposit onto the covered coarse cells
+    g.step(max(args.warmup, 3), 0.3)  # also captures the two-step graph
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    lib = H.load()
+    H.check(lib.genasis_fmr_step(g._h, args.steps, 0.3, None))  # replays the captured two-step graph
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    t = g.step(0, 0.3)
+    g.close()
+    cells_per_step = sum(2 ** l * n ** 3 for l in range(L))
+    line = {"metric": METRIC, "value": cells_per_step * 2 / (ms * 1e-3), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == H.FP32_MIXED else "f64",
+            "data": "synthetic",
+            "config": {"workload": f"sedov3d_fmr_{L}x{n}^3_{args.solver}_{args.precision}", "levels": L,
+                       "cells_per_level": n ** 3, "finest_equivalent": f"{n * 2 ** (L - 1)}^3",
+                       "cell_updates_per_global_step": cells_per_step,
+                       "step": "one global step: 2^l RK2 steps of level l, prolongation, restriction, "
+                               "flux replacement, provisional coarse substeps", "time_reached": t},
+            "roofline": None, "clocks": clocks, "gpu_launches": None}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = _args()
     if args.impl == "reference":
@@ -598,6 +660,8 @@ def main():
         run_batch(args)
     elif args.workload == "learned":
         run_learned(args)
+    elif args.workload == "fmr":
+        run_fmr(args)
     else:
         run_ours(args)
 

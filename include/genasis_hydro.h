@@ -382,6 +382,53 @@ int genasis_batch_autotune(genasis_batch_t b, int trial_steps, const char *cache
  * per-problem dt kernel (ms[0..2]) from one extra profiled step; synchronises. */
 int genasis_batch_profile_step(genasis_batch_t b, double cfl, float *ms);
 
+/* ---------------------------------------------------------------------------
+ * Multilevel evolution with subcycling on a fixed mesh of nested levels
+ * (Sec. 3.7, Algorithms Evolve, EvolveLevel, StepLevel).  The paper refines
+ * oct-tree cells inside nested spheres; here each level l >= 1 is an n^d box
+ * over the central half of level l-1 (per axis) at twice its resolution, so
+ * its cells are the children of the coarse cells [n/4, 3n/4).  Level 0 covers
+ * the cube of side `size` with the wall rule `bc` on every face.
+ *   - a level l >= 1 is stored with a two-cell exterior ring: (n+4)^d cells,
+ *     x fastest; level 0 as n^d;
+ *   - before each step of level l the ring is prolonged from level l-1
+ *     (coarse value plus minmod-limited conserved slopes times the child
+ *     offset) and held through both RK stages;
+ *   - after a step, covered coarse cells take the mean of their children,
+ *     and the uncovered coarse cells next to a child's box have the coarse
+ *     flux through the shared faces replaced by the child's time-integrated
+ *     Heun-effective flux (conservation on leaf cells);
+ *   - the deepest level steps with cfl x min_l dt_CFL(l) / 2^(L-1-l), each
+ *     coarser level by the time its child advanced; between a level's two
+ *     steps its parent takes a provisional forward-Euler substep, undone
+ *     afterwards.
+ * n a multiple of 4 in [16, 1024]; ndim 2 or 3; GENASIS_FP64 or GENASIS_FP32_MIXED;
+ * HLL or HLLC. */
+typedef struct genasis_fmr *genasis_fmr_t;
+typedef struct {
+  int ndim;          /* 2 or 3 */
+  int n;             /* cells per axis on every level */
+  int nlevels;       /* 1 .. 12 */
+  double size;       /* side of the level-0 cube */
+  int bc;            /* GENASIS_BC_* on every face of level 0 */
+  double gamma;
+  int solver;        /* GENASIS_HLL or GENASIS_HLLC */
+  double theta;      /* limiter parameter */
+  int precision;     /* GENASIS_FP64 or GENASIS_FP32_MIXED */
+  void *stream;      /* NULL: the library creates one */
+} genasis_fmr_desc;
+
+int genasis_fmr_create(const genasis_fmr_desc *desc, genasis_fmr_t *out);
+int genasis_fmr_destroy(genasis_fmr_t f);
+/* Set / read level `level` in its stored layout (conserved, FP64, host or
+ * device; (ndim+2) planes of n^d (level 0) or (n+4)^d cells). */
+int genasis_fmr_set_level(genasis_fmr_t f, int level, const double *U);
+int genasis_fmr_get_level(genasis_fmr_t f, int level, double *U);
+/* nsteps global steps (one pass of Algorithm Evolve's loop each); if t_out
+ * is non-NULL it synchronises, stores the time reached and reports
+ * ENONPHYS if any level met a non-physical state. */
+int genasis_fmr_step(genasis_fmr_t f, int nsteps, double cfl, double *t_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -124,13 +124,14 @@ class Multilevel:
             lo_sel, hi_sel = list(core), list(core)
             lo_sel[ax] = slice(0, m)
             hi_sel[ax] = slice(2, m + 2)
-            dm = (sub - B[tuple(lo_sel)]) / hc
-            dp = (B[tuple(hi_sel)] - sub) / hc
+            # minmod of the one-sided differences; times the child offset
+            # -+h_c/4 this is the limited slope times the offset
+            dm = sub - B[tuple(lo_sel)]
+            dp = B[tuple(hi_sel)] - sub
             s = np.where(dm * dp > 0.0, np.where(np.abs(dm) < np.abs(dp), dm, dp), 0.0)
             for ax2 in range(1, nd + 1):
                 s = np.repeat(s, 2, axis=ax2)
-            # child offset along q: -hc/4 for the first child, +hc/4 for the second
-            off = np.tile(np.array([-0.25, 0.25]) * hc, m)
+            off = np.tile(np.array([-0.25, 0.25]), m)
             shape = [1] * (nd + 1)
             shape[ax] = -1
             out = out + s * off.reshape(shape)

@@ -21,6 +21,7 @@
 #include "hydro_device.cuh"
 #include "registry.h"
 #include "stage_kernel.cuh"
+#include "hydro_handle.h"
 
 namespace gh {
 
@@ -63,40 +64,6 @@ int stage_tile_count(int ndim, int prec) { return tile_count(ndim, prec); }
 
 using namespace gh;
 
-struct genasis_hydro {
-  int ndim = 0, nv = 0, n[3] = {1, 1, 1}, bc_lo[3] = {0, 0, 0}, bc_hi[3] = {0, 0, 0};
-  double gamma = 1.4, theta = 1.4;
-  double grad_phi[3] = {0.0, 0.0, 0.0};  // external potential gradient (source off when zero)
-  int has_source = 0;
-  int solver = 1, prec = 0;
-  size_t ncell = 0, esize = 8;
-  cudaStream_t stream = nullptr;
-  bool own_stream = false;
-  int device = 0, num_sms = 0;
-  void* U[2] = {nullptr, nullptr};
-  int cur = 0;
-  void* K = nullptr;
-  void* geo[3] = {nullptr, nullptr, nullptr};
-  void* iw[3] = {nullptr, nullptr, nullptr};
-  double* wd[3] = {nullptr, nullptr, nullptr};
-  float* wpair[3] = {nullptr, nullptr, nullptr};  // FP32 state: widths as hi[n] then lo[n]
-  dw* wdw[3] = {nullptr, nullptr, nullptr};       // double-word state: widths as pairs
-  unsigned char* flags = nullptr;                 // shock bits (GENASIS_HLLC_SWITCH)
-  double* part_speed = nullptr;
-  double* part_tot = nullptr;
-  size_t part_cap = 0;  // blocks the partial buffers hold
-  double* scal = nullptr;
-  unsigned* status = nullptr;
-  // launch configuration
-  int tile = 0, kchunk_req = 0, kchunk = 1;
-  StageVariant v1{}, v2{};
-  dim3 grid;
-  int want_totals = 1;
-  // cached graphs of `advance`, one per starting state buffer
-  cudaGraphExec_t graph[2] = {nullptr, nullptr};
-  int g_nsteps = -1;
-  double g_cfl = 0, g_tend = 0;
-};
 
 namespace {
 
@@ -223,45 +190,6 @@ int configure(genasis_hydro* h, int tile, int kchunk_req) {
   return GENASIS_OK;
 }
 
-template <class T>
-StageArgs<T> stage_args(genasis_hydro* h, int stage) {
-  StageArgs<T> A;
-  memset(&A, 0, sizeof(A));
-  for (int q = 0; q < 3; ++q) {
-    A.n[q] = h->n[q];
-    A.bc_lo[q] = h->bc_lo[q];
-    A.bc_hi[q] = h->bc_hi[q];
-    A.geo[q] = (const Geo<T>*)h->geo[q];
-    A.iw[q] = (const T*)h->iw[q];
-    A.wd[q] = h->wd[q];
-    if (sizeof(T) == 4) {
-      const size_t nq = q < h->ndim ? (size_t)h->n[q] : 2;
-      A.wdh[q] = (const T*)h->wpair[q];
-      A.wdl[q] = (const T*)(h->wpair[q] + nq);
-    } else if (std::is_same<T, dw>::value) {
-      A.wdh[q] = (const T*)h->wdw[q];
-      A.wdl[q] = (const T*)h->wdw[q];
-    } else {
-      A.wdh[q] = (const T*)h->wd[q];
-      A.wdl[q] = (const T*)h->wd[q];
-    }
-  }
-  A.gamma = (T)h->gamma;
-  A.gm1 = (T)(h->gamma - 1.0);
-  A.un = (const T*)h->U[h->cur];
-  A.k1 = (const T*)h->K;
-  A.out = stage == 1 ? (T*)h->K : (T*)h->U[1 - h->cur];
-  A.dt = h->scal + SCAL_DT;
-  A.kchunk = h->kchunk;
-  A.part_speed = h->part_speed;
-  A.part_tot = h->part_tot;
-  A.status = h->status;
-  A.want_totals = h->want_totals;
-  A.has_source = h->has_source;
-  A.flags = h->flags;
-  for (int q = 0; q < 3; ++q) A.grad_phi[q] = (T)h->grad_phi[q];
-  return A;
-}
 
 template <class T>
 int enqueue_flags(genasis_hydro* h, int stage) {

@@ -66,6 +66,11 @@ SIGNATURES = {
     "genasis_hydro_get_conserved_async": [_P, _P, _I],
     "genasis_hydro_sync": [_P],
     "genasis_hydro_set_potential_gradient": [_P, _P],
+    "genasis_fmr_create": [_P, _P],
+    "genasis_fmr_destroy": [_P],
+    "genasis_fmr_set_level": [_P, _I, _P],
+    "genasis_fmr_get_level": [_P, _I, _P],
+    "genasis_fmr_step": [_P, _I, ctypes.c_double, _P],
     "genasis_hydro_set_tile": [_P, _I, _I],
     "genasis_hydro_get_tile": [_P, _P],
     "genasis_hydro_autotune": [_P, _I, ctypes.c_char_p],
@@ -358,6 +363,54 @@ class Hydro:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class FmrDesc(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int), ("n", ctypes.c_int), ("nlevels", ctypes.c_int), ("size", ctypes.c_double),
+                ("bc", ctypes.c_int), ("gamma", ctypes.c_double), ("solver", ctypes.c_int),
+                ("theta", ctypes.c_double), ("precision", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+class Fmr:
+    """Nested-box multilevel mesh with subcycled evolution (genasis_fmr_t).
+    Level l >= 1 is stored with a two-cell exterior ring: (n+4)^d cells."""
+
+    def __init__(self, ndim, n, nlevels, size, bc, gamma=1.4, solver=HLLC, theta=1.4, precision=FP64,
+                 stream=None):
+        d = FmrDesc(int(ndim), int(n), int(nlevels), float(size), int(bc), float(gamma), int(solver), float(theta),
+                    int(precision), None if stream is None else int(getattr(stream, "cuda_stream", stream)))
+        self._h = ctypes.c_void_p()
+        check(load().genasis_fmr_create(ctypes.byref(d), ctypes.byref(self._h)))
+        self.ndim, self.n, self.nlevels = int(ndim), int(n), int(nlevels)
+
+    def stored_shape(self, level):
+        m = self.n + (4 if level else 0)
+        return (self.ndim + 2,) + (m,) * self.ndim
+
+    def set_level(self, level, U):
+        pu, keep = _ptr(U, np.float64, int(np.prod(self.stored_shape(level))), "U")
+        check(load().genasis_fmr_set_level(self._h, int(level), pu))
+
+    def get_level(self, level):
+        out = np.empty(self.stored_shape(level))
+        check(load().genasis_fmr_get_level(self._h, int(level), out.ctypes.data))
+        return out
+
+    def step(self, nsteps, cfl):
+        t = ctypes.c_double()
+        check(load().genasis_fmr_step(self._h, int(nsteps), float(cfl), ctypes.byref(t)))
+        return t.value
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load().genasis_fmr_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class BatchProblemDesc(ctypes.Structure):
