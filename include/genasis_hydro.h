@@ -114,7 +114,10 @@ int genasis_hydro_destroy(genasis_hydro_t h);
 
 /* Set the state from primitives (Eqs. BalancedBaryonDensity, MomentumDensity,
  * balancedEnergy with p = (gamma-1) e): rho[ncell], vel[ndim * ncell] (one
- * plane per axis), p[ncell]; FP64, host or device.  Resets time to 0. */
+ * plane per axis), p[ncell]; FP64, host or device.  Resets time to 0.
+ * Device inputs are read on the handle's stream: work on other streams that
+ * writes them must be complete (or ordered before it) when this is called;
+ * the same holds for every call below that takes device pointers. */
 int genasis_hydro_set_primitive(genasis_hydro_t h, const double *rho, const double *vel, const double *p);
 
 /* Set / read the conserved state U[(ndim + 2) * ncell] in the given precision

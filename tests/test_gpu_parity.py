@@ -407,6 +407,7 @@ def test_largest_mesh_rows_match_the_1d_oracle():
                     gamma=tube.gamma, rho=np.zeros(1), vel=np.zeros(1), p=np.zeros(1), solver=tube.solver,
                     theta=tube.theta, cfl=tube.cfl)
     h = H.Hydro.from_problem(pr3, precision=H.FP32_MIXED, set_state=False)
+    torch.cuda.synchronize()  # the library's stream does not wait for torch's
     h.set_primitive(rho, vel, p)
     del rho, vel, p
     torch.cuda.empty_cache()
