@@ -54,6 +54,16 @@ __device__ __forceinline__ T minmod3(T a, T b, T c) {
   return lo > T(0) ? lo : (hi < T(0) ? hi : T(0));
 }
 
+// FP32: the extremes from the three-input min/max of sm_100+, and the case
+// split as max(lo, 0) + min(hi, 0) (one of the two terms is zero): the same
+// value as the template above in five instructions instead of eight.
+__device__ __forceinline__ float minmod3(float a, float b, float c) {
+  float lo, hi;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(lo) : "f"(a), "f"(b), "f"(c));
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(hi) : "f"(a), "f"(b), "f"(c));
+  return fmaxf(lo, 0.0f) + fminf(hi, 0.0f);
+}
+
 // Limited slope of cell c from its neighbours (Eq. MinMod; theta is in g).
 template <class T>
 __device__ __forceinline__ T limited_slope(T wm, T wc, T wp, const Geo<T>& g) {
@@ -165,7 +175,10 @@ __device__ __forceinline__ void recover(const float (&u)[NDIM + 2], float (&w)[N
 //                  F*  = F_K + S_K (U* - U_K)
 //                which are the outer jump conditions of Sec. 3.2 solved for the
 //                middle state (this form satisfies p*_L = p*_R).
-//                alpha_- = 0 gives F_L, alpha_+ = 0 gives F_R (upwind).
+//                alpha_- = 0 gives F_L, alpha_+ = 0 gives F_R (upwind): those
+//                cases select that side, where S_K = 0, so F* = F_K exactly
+//                once the factor 1 / (S_K - alpha_m) of the (unused) middle
+//                state is replaced by 0 to keep it finite.
 // ---------------------------------------------------------------------------
 template <class T, int NDIM, int Q, int SOLVER>
 __device__ __forceinline__ void face_flux(const T (&wl)[NDIM + 2], const T (&wr)[NDIM + 2],
@@ -219,13 +232,13 @@ __device__ __forceinline__ void face_flux(const T (&wl)[NDIM + 2], const T (&wr)
   const T sl = am + vl;  // = -(S_L - v_L) > 0
   const T sr = ap - vr;  // =   S_R - v_R  > 0
   const T alpha_m = fdiv(ur[1 + Q] * sr + ul[1 + Q] * sl - (pr - pl), nr * sr + nl * sl);
-  const bool left = alpha_m >= T(0);
+  const bool left = am == T(0) || (ap != T(0) && alpha_m >= T(0));
   const T SK = left ? -am : ap;
   const T nK = left ? nl : nr;
   const T vK = left ? vl : vr;
   const T pK = left ? pl : pr;
   const T dK = SK - vK;                       // S_K - v_K
-  const T rden = frcp(SK - alpha_m);
+  const T rden = SK == T(0) ? T(0) : frcp(SK - alpha_m);
   const T Ds = nK * dK * rden;
   const T ps = pK + nK * dK * (alpha_m - vK);
   T us[NV];
@@ -238,10 +251,7 @@ __device__ __forceinline__ void face_flux(const T (&wl)[NDIM + 2], const T (&wr)
   for (int v = 0; v < NV; ++v) {
     const T fK = left ? fl[v] : fr[v];
     const T uK = left ? ul[v] : ur[v];
-    T f = fK + SK * (us[v] - uK);
-    f = (am == T(0)) ? fl[v] : f;
-    f = (ap == T(0)) ? fr[v] : f;
-    F[v] = f;
+    F[v] = fK + SK * (us[v] - uK);
   }
 }
 

@@ -3,7 +3,7 @@
 
 namespace gh {
 
-int tile_count_3d_f32() { return 6; }
+int tile_count_3d_f32() { return 8; }
 
 // Register caps: 256-thread tiles at 3 CTAs per SM and 128-thread tiles at 6
 // (80 registers, 24 resident warps); tile 3 keeps the uncapped allocation;
@@ -15,6 +15,8 @@ bool stage_variant_3d_f32(int solver, int stage, int tile, StageVariant* out) {
     case 1: return pick_variant<3, float, 32, 4, 6>(solver, stage, out);
     case 2: return pick_variant<3, float, 64, 4, 3>(solver, stage, out);
     case 3: return pick_variant<3, float, 32, 8, 2>(solver, stage, out);
+    case 6: return pick_variant<3, float, 32, 8, 3, false>(solver, stage, out);
+    case 7: return pick_variant<3, float, 32, 8, 4>(solver, stage, out);
   }
   return stage_variant_3d_f32_wide(solver, stage, tile, out);
 }

@@ -14,9 +14,15 @@
 //      of W along the march axis; limited slopes and the march-axis face flux
 //      are computed once per cell per stage),
 //   2. loads + recovers the cross-shaped in-plane halo (2 cells each side),
-//   3. computes every in-plane face flux exactly once into shared memory,
-//   4. forms the flux divergence (Eq. BalanceEquationAverage, A_q/V = 1/dq)
+//   3. (PRE) limits the in-plane slopes of each cell once and stores the
+//      reconstructed values at both of its in-plane faces in shared memory,
+//   4. computes every in-plane face flux exactly once into shared memory
+//      (PRE: while loading the next plane, steps 1-2, into a second buffer,
+//      so that a plane takes two barriers),
+//   5. forms the flux divergence (Eq. BalanceEquationAverage, A_q/V = 1/dq)
 //      and the stage combine for its own cells.
+// Without PRE each in-plane face limits the slopes of its two cells itself,
+// so every in-plane slope is formed twice (one barrier per plane fewer).
 // Boundary conditions are applied by index mapping on load (bc_map).
 #pragma once
 
@@ -48,7 +54,9 @@ struct StageArgs {
   T grad_phi[3];              // gradient of the linear external potential
 };
 
-template <int NDIM, class T, int SOLVER, int STAGE, int TX, int TY>
+// PRE pays in 3D, where both in-plane axes would form every slope twice; in
+// 1D/2D one axis gains less than the extra barrier costs.
+template <int NDIM, class T, int SOLVER, int STAGE, int TX, int TY, bool PRE = (NDIM == 3)>
 struct StageKernel {
   static constexpr int NV = NDIM + 2;
   static constexpr bool SW = SOLVER == SOLVER_HLLC_SW;  // per-face HLLC/HLL choice from shock bits
@@ -62,15 +70,28 @@ struct StageKernel {
   static_assert(HAS_Y || TY == 1, "tiles of 1D/2D runs are one row high");
   static_assert(NT % 32 == 0, "whole warps");
   static constexpr int HSLOTS = (NHALO + NT - 1) / NT;  // halo slots per thread
+  // PRE: one-sided face states of the halo cells next to the tile (columns
+  // -1 and TX of every row; rows -1 and TY of every column in 3D), formed by
+  // the last NJ threads, which load no halo cells when NT >= NHALO + NJ.
+  static constexpr int NJ = HAS_Y ? 2 * TY + 2 * TX : 2;
+  static_assert(!PRE || NJ <= NT, "one halo face state per thread at most");
+  // PRE double-buffers the shared plane: the next plane is loaded while the
+  // faces of this one are computed.
+  static constexpr int NB = PRE ? 2 : 1;
 
   struct Smem {
     Geo<T> gx[TX + 4];                 // geometry of cells a0 - 2 .. a0 + TX + 1
     Geo<T> gy[HAS_Y ? TY + 4 : 1];     // geometry of cells b0 - 2 .. b0 + TY + 1
-    T w[NV][SY][SX];
+    T w[NB][NV][SY][SX];
     T fx[NV][TY][TX + 1];
     T fy[HAS_Y ? NV : 1][HAS_Y ? TY + 1 : 1][TX];
     double red[NT / 32][NV + 1];
-    unsigned char fl[SW ? SY : 1][SW ? SX : 1];  // shock bits of the plane (own cells and halo)
+    unsigned char fl[NB][SW ? SY : 1][SW ? SX : 1];  // shock bits of the plane (own cells and halo)
+    // PRE: reconstructed primitives at the lower [0] and upper [1] x face of
+    // the cells of column slot j (cell a0 + j - 1) and at the lower/upper y
+    // face of the cells of row slot i (cell b0 + i - 1)
+    T xs[PRE ? 2 : 1][PRE ? NV : 1][PRE ? TY : 1][PRE ? TX + 2 : 1];
+    T ys[PRE && HAS_Y ? 2 : 1][PRE && HAS_Y ? NV : 1][PRE && HAS_Y ? TY + 2 : 1][PRE && HAS_Y ? TX : 1];
   };
 
   // Linear index of cell (a, b, m): a = x, b = in-plane y (3D), m = march
@@ -143,35 +164,53 @@ struct StageKernel {
 
   // Flux through the face between slot positions (s - 1, s) along x of shared
   // row `row`; slot s holds cell a0 + s - 2.
-  static __device__ __forceinline__ void x_face(const StageArgs<T>& A, Smem& S, int a0, int face, int srow,
+  static __device__ __forceinline__ void x_face(const StageArgs<T>& A, Smem& S, int b, int face, int srow,
                                                 int frow) {
     const int sl = face + 1;  // slot of the left cell
-    const Geo<T> gl = S.gx[face + 1], gr = S.gx[face + 2];
     T wl[NV], wr[NV], f[NV];
+    if constexpr (PRE) {
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      const T w0 = S.w[v][srow][sl - 1], w1 = S.w[v][srow][sl], w2 = S.w[v][srow][sl + 1],
-              w3 = S.w[v][srow][sl + 2];
-      wl[v] = fma(limited_slope(w0, w1, w2, gl), gl.h, w1);
-      wr[v] = fma(-limited_slope(w1, w2, w3, gr), gr.h, w2);
+      for (int v = 0; v < NV; ++v) {
+        wl[v] = S.xs[1][v][frow][face];
+        wr[v] = S.xs[0][v][frow][face + 1];
+      }
+    } else {
+      const Geo<T> gl = S.gx[face + 1], gr = S.gx[face + 2];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const T w0 = S.w[b][v][srow][sl - 1], w1 = S.w[b][v][srow][sl], w2 = S.w[b][v][srow][sl + 1],
+                w3 = S.w[b][v][srow][sl + 2];
+        wl[v] = fma(limited_slope(w0, w1, w2, gl), gl.h, w1);
+        wr[v] = fma(-limited_slope(w1, w2, w3, gr), gr.h, w2);
+      }
     }
-    flux<0>(A, wl, wr, SW ? (unsigned)(S.fl[SW ? srow : 0][SW ? sl : 0] | S.fl[SW ? srow : 0][SW ? sl + 1 : 0]) : 0u, f);
+    flux<0>(A, wl, wr, SW ? (unsigned)(S.fl[b][SW ? srow : 0][SW ? sl : 0] | S.fl[b][SW ? srow : 0][SW ? sl + 1 : 0]) : 0u,
+            f);
 #pragma unroll
     for (int v = 0; v < NV; ++v) S.fx[v][frow][face] = f[v];
   }
 
-  static __device__ __forceinline__ void y_face(const StageArgs<T>& A, Smem& S, int b0, int face, int scol) {
+  static __device__ __forceinline__ void y_face(const StageArgs<T>& A, Smem& S, int b, int face, int scol) {
     const int sl = face + 1;
-    const Geo<T> gl = S.gy[face + 1], gr = S.gy[face + 2];
     T wl[NV], wr[NV], f[NV];
+    if constexpr (PRE) {
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      const T w0 = S.w[v][sl - 1][scol], w1 = S.w[v][sl][scol], w2 = S.w[v][sl + 1][scol],
-              w3 = S.w[v][sl + 2][scol];
-      wl[v] = fma(limited_slope(w0, w1, w2, gl), gl.h, w1);
-      wr[v] = fma(-limited_slope(w1, w2, w3, gr), gr.h, w2);
+      for (int v = 0; v < NV; ++v) {
+        wl[v] = S.ys[1][v][face][scol - 2];
+        wr[v] = S.ys[0][v][face + 1][scol - 2];
+      }
+    } else {
+      const Geo<T> gl = S.gy[face + 1], gr = S.gy[face + 2];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const T w0 = S.w[b][v][sl - 1][scol], w1 = S.w[b][v][sl][scol], w2 = S.w[b][v][sl + 1][scol],
+                w3 = S.w[b][v][sl + 2][scol];
+        wl[v] = fma(limited_slope(w0, w1, w2, gl), gl.h, w1);
+        wr[v] = fma(-limited_slope(w1, w2, w3, gr), gr.h, w2);
+      }
     }
-    flux<1>(A, wl, wr, SW ? (unsigned)(S.fl[SW ? sl : 0][SW ? scol : 0] | S.fl[SW ? sl + 1 : 0][SW ? scol : 0]) : 0u, f);
+    flux<1>(A, wl, wr, SW ? (unsigned)(S.fl[b][SW ? sl : 0][SW ? scol : 0] | S.fl[b][SW ? sl + 1 : 0][SW ? scol : 0]) : 0u,
+            f);
 #pragma unroll
     for (int v = 0; v < NV; ++v) S.fy[v][face][scol - 2] = f[v];
   }
@@ -194,6 +233,114 @@ struct StageKernel {
                                                 const T (&wp)[NV], const Geo<T>& g, T (&s)[NV]) {
 #pragma unroll
     for (int v = 0; v < NV; ++v) s[v] = limited_slope(wm[v], wc[v], wp[v], g);
+  }
+
+  // PRE: the reconstructed values at the in-plane faces of the own cell (W in
+  // registers, neighbours from the shared plane), and the one-sided value of
+  // the halo cell that job tid - (NT - NJ) names.  The formulas are those of
+  // the face routines without PRE, so that both forms give the same bits.
+  static __device__ __forceinline__ void face_states(Smem& S, int b, int tid, int tx, int ty, const T (&wc)[NV]) {
+    const int sy = HAS_Y ? ty + 2 : 0;
+    {
+      const Geo<T> g = S.gx[tx + 2];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const T sv = limited_slope(S.w[b][v][sy][tx + 1], wc[v], S.w[b][v][sy][tx + 3], g);
+        S.xs[0][v][ty][tx + 1] = fma(-sv, g.h, wc[v]);
+        S.xs[1][v][ty][tx + 1] = fma(sv, g.h, wc[v]);
+      }
+    }
+    if constexpr (HAS_Y) {
+      const Geo<T> g = S.gy[ty + 2];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const T sv = limited_slope(S.w[b][v][ty + 1][tx + 2], wc[v], S.w[b][v][ty + 3][tx + 2], g);
+        S.ys[0][v][ty + 1][tx] = fma(-sv, g.h, wc[v]);
+        S.ys[1][v][ty + 1][tx] = fma(sv, g.h, wc[v]);
+      }
+    }
+    const int j = tid - (NT - NJ);
+    if (j < 0) return;
+    if (j < 2 * (HAS_Y ? TY : 1)) {
+      // x: column -1 (upper face value) or column TX (lower face value) of row j / 2
+      const int r = j >> 1;
+      const bool up = j & 1;
+      const int srow = HAS_Y ? r + 2 : 0;
+      const int slot = up ? TX + 2 : 1;
+      const Geo<T> g = S.gx[slot];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const T w1 = S.w[b][v][srow][slot];
+        const T sv = limited_slope(S.w[b][v][srow][slot - 1], w1, S.w[b][v][srow][slot + 1], g);
+        if (up) S.xs[0][v][r][TX + 1] = fma(-sv, g.h, w1);
+        else S.xs[1][v][r][0] = fma(sv, g.h, w1);
+      }
+    } else if constexpr (HAS_Y) {
+      // y: row -1 (upper face value) or row TY (lower face value) of column c
+      const int jj = j - 2 * TY;
+      const bool up = jj >= TX;
+      const int c = up ? jj - TX : jj;
+      const int slot = up ? TY + 2 : 1;
+      const Geo<T> g = S.gy[slot];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const T w1 = S.w[b][v][slot][c + 2];
+        const T sv = limited_slope(S.w[b][v][slot - 1][c + 2], w1, S.w[b][v][slot + 1][c + 2], g);
+        if (up) S.ys[0][v][TY + 1][c] = fma(-sv, g.h, w1);
+        else S.ys[1][v][0][c] = fma(sv, g.h, w1);
+      }
+    }
+  }
+
+  // The own cell (primitives wo, shock bits fo) and this thread's halo cells
+  // of plane m into buffer b of the shared plane.
+  static __device__ __forceinline__ void put_plane(const StageArgs<T>& A, Smem& S, int b, int m, int tid, int tx,
+                                                   int ty, const T (&wo)[NV], unsigned char fo,
+                                                   const ColRef (&halo)[HSLOTS], const int (&hsx)[HSLOTS],
+                                                   const int (&hsy)[HSLOTS], T dt, size_t vs) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) S.w[b][v][HAS_Y ? ty + 2 : 0][tx + 2] = wo[v];
+    if constexpr (SW) S.fl[b][HAS_Y ? ty + 2 : 0][tx + 2] = fo;
+#pragma unroll
+    for (int k = 0; k < HSLOTS; ++k) {
+      if (tid + k * NT < NHALO) {
+        T wh[NV];
+        unsigned char fh = 0;
+        load_col(A, halo[k], m, dt, vs, wh, fh);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) S.w[b][v][hsy[k]][hsx[k]] = wh[v];
+        if constexpr (SW) S.fl[b][hsy[k]][hsx[k]] = fh;
+      }
+    }
+  }
+
+  // In-plane faces, each computed once, one call site per axis.  Whole
+  // rounds of NT faces go to all threads; the REM faces left over go to the
+  // last threads, which load no halo cells, so that no warp does both a halo
+  // load and an extra face.
+  static __device__ __forceinline__ void faces(const StageArgs<T>& A, Smem& S, int b, int tid) {
+    constexpr int NXF = (TX + 1) * TY;
+    constexpr int NYF = HAS_Y ? TX * (TY + 1) : 0;
+    constexpr int NF = NXF + NYF, ROUNDS = NF / NT, REM = NF - ROUNDS * NT;
+    for (int k = 0; k <= ROUNDS; ++k) {
+      int f = tid + k * NT;
+      if (k == ROUNDS) {
+        if (REM == 0 || tid < NT - REM) break;
+        f = ROUNDS * NT + (tid - (NT - REM));
+      }
+      if (f < NXF) {
+        const int row = f / (TX + 1);
+        const int face = f - row * (TX + 1);
+        x_face(A, S, b, face, HAS_Y ? row + 2 : 0, row);
+      } else {
+        if constexpr (HAS_Y) {
+          const int g = f - NXF;
+          const int face = g / TX;
+          const int col = g - face * TX;
+          y_face(A, S, b, face, col + 2);
+        }
+      }
+    }
   }
 
   static __device__ __forceinline__ bool nonphysical(const T (&w)[NV], T gm1) {
@@ -306,51 +453,22 @@ struct StageKernel {
       } else {
         load_col(A, own, 0, dt, vs, wown, fown);
       }
-      // own cell into the shared plane
-#pragma unroll
-      for (int v = 0; v < NV; ++v) S.w[v][HAS_Y ? ty + 2 : 0][tx + 2] = wown[v];
-      if constexpr (SW) S.fl[HAS_Y ? ty + 2 : 0][tx + 2] = fown;
-      // cross-shaped in-plane halo
-#pragma unroll
-      for (int k = 0; k < HSLOTS; ++k) {
-        if (tid + k * NT < NHALO) {
-          T wh[NV];
-          unsigned char fh = 0;
-          load_col(A, halo[k], m, dt, vs, wh, fh);
-#pragma unroll
-          for (int v = 0; v < NV; ++v) S.w[v][hsy[k]][hsx[k]] = wh[v];
-          if constexpr (SW) S.fl[hsy[k]][hsx[k]] = fh;
-        }
+      // Without PRE: plane m into the shared plane; barrier; faces; barrier.
+      // With PRE the plane was put into buffer `buf` during the faces of the
+      // previous plane (the first plane of the chunk here): face states;
+      // barrier; faces, and plane m + 1 into the other buffer; barrier.
+      const int buf = PRE ? ((m - m0) & 1) : 0;
+      if (!PRE || m == m0) {
+        put_plane(A, S, buf, m, tid, tx, ty, wown, fown, halo, hsx, hsy, dt, vs);
+        __syncthreads();
       }
-      __syncthreads();
-
-      // in-plane faces, each computed once, one call site per axis.  Whole
-      // rounds of NT faces go to all threads; the REM faces left over go to
-      // the last threads, which load no halo cells, so that no warp does
-      // both a halo load and an extra face.
-      {
-        constexpr int NXF = (TX + 1) * TY;
-        constexpr int NYF = HAS_Y ? TX * (TY + 1) : 0;
-        constexpr int NF = NXF + NYF, ROUNDS = NF / NT, REM = NF - ROUNDS * NT;
-        for (int k = 0; k <= ROUNDS; ++k) {
-          int f = tid + k * NT;
-          if (k == ROUNDS) {
-            if (REM == 0 || tid < NT - REM) break;
-            f = ROUNDS * NT + (tid - (NT - REM));
-          }
-          if (f < NXF) {
-            const int row = f / (TX + 1);
-            const int face = f - row * (TX + 1);
-            x_face(A, S, a0, face, HAS_Y ? row + 2 : 0, row);
-          } else {
-            if constexpr (HAS_Y) {
-              const int g = f - NXF;
-              const int face = g / TX;
-              const int col = g - face * TX;
-              y_face(A, S, b0, face, col + 2);
-            }
-          }
-        }
+      if constexpr (PRE) {
+        face_states(S, buf, tid, tx, ty, wown);
+        __syncthreads();
+      }
+      faces(A, S, buf, tid);
+      if constexpr (PRE) {
+        if (m + 1 < m1) put_plane(A, S, buf ^ 1, m + 1, tid, tx, ty, wk1, fk1, halo, hsx, hsy, dt, vs);
       }
       __syncthreads();
 
@@ -462,9 +580,9 @@ struct StageKernel {
 };
 
 // MINB: CTAs per SM the register allocation must allow (__launch_bounds__).
-template <int NDIM, class T, int SOLVER, int STAGE, int TX, int TY, int MINB>
+template <int NDIM, class T, int SOLVER, int STAGE, int TX, int TY, int MINB, bool PRE>
 __global__ void __launch_bounds__(TX * TY, MINB) hydro_stage_kernel(const StageArgs<T> A) {
-  StageKernel<NDIM, T, SOLVER, STAGE, TX, TY>::run(A);
+  StageKernel<NDIM, T, SOLVER, STAGE, TX, TY, PRE>::run(A);
 }
 
 }  // namespace gh
