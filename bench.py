@@ -155,8 +155,8 @@ PEAK_FP64_TFLOPS = 1.25
 # DRAM bytes (read + write) per cell of the FP32 HLLC 3D stage kernels, from
 # one ncu capture of the same kernels at 192^3 (summary under profiles/),
 # scaled to the bench's cell count (traffic grows with the cells).
-TRAFFIC_PER_CELL_FP32_HLLC = {"stage1": (148.504832e6 + 104.506624e6) / 192 ** 3,
-                              "stage2": (299.108608e6 + 119.765504e6) / 192 ** 3}
+TRAFFIC_PER_CELL_FP32_HLLC = {"stage1": (148.547072e6 + 104.710144e6) / 192 ** 3,
+                              "stage2": (298.134016e6 + 120.053760e6) / 192 ** 3}
 
 
 def cpu_baseline(n_sample=256, steps=3):
@@ -387,6 +387,7 @@ def run_ours(args):
                 hv = H.Hydro.from_problem(pr, precision=pc, stream=stream.cuda_stream)
                 hv.set_step_totals(totals)
                 del pr
+                hv.autotune(trial_steps=2)
                 kv = 3 if pc == H.FP64 else 5
                 for _ in range(2):
                     hv.advance(1, cfl, sync=False)

@@ -180,78 +180,72 @@ __device__ __forceinline__ void recover(const float (&u)[NDIM + 2], float (&w)[N
 //                once the factor 1 / (S_K - alpha_m) of the (unused) middle
 //                state is replaced by 0 to keep it finite.
 // ---------------------------------------------------------------------------
+// Conserved state U(W) and physical flux F^Q(U) of one side of a face
+// (Sec. 3.5): p is its pressure, w[1 + Q] its normal velocity.
+template <class T, int NDIM, int Q>
+__device__ __forceinline__ void side_state(const T (&w)[NDIM + 2], T p, T (&u)[NDIM + 2], T (&f)[NDIM + 2]) {
+  constexpr int NV = NDIM + 2;
+  const T n = w[0], vq = w[1 + Q];
+  T v2 = T(0);
+#pragma unroll
+  for (int q = 0; q < NDIM; ++q) v2 += w[1 + q] * w[1 + q];
+  u[0] = n;
+#pragma unroll
+  for (int q = 0; q < NDIM; ++q) u[1 + q] = n * w[1 + q];
+  u[NV - 1] = w[NV - 1] + T(0.5) * n * v2;
+#pragma unroll
+  for (int v = 0; v < NV - 1; ++v) f[v] = u[v] * vq;
+  f[1 + Q] += p;
+  f[NV - 1] = (u[NV - 1] + p) * vq;
+}
+
 template <class T, int NDIM, int Q, int SOLVER>
 __device__ __forceinline__ void face_flux(const T (&wl)[NDIM + 2], const T (&wr)[NDIM + 2],
                                           T gamma, T gm1, T (&F)[NDIM + 2]) {
   constexpr int NV = NDIM + 2;
   const T nl = wl[0], nr = wr[0];
   const T pl = gm1 * wl[NV - 1], pr = gm1 * wr[NV - 1];
-  T v2l = T(0), v2r = T(0);
-#pragma unroll
-  for (int q = 0; q < NDIM; ++q) {
-    v2l += wl[1 + q] * wl[1 + q];
-    v2r += wr[1 + q] * wr[1 + q];
-  }
-  T ul[NV], ur[NV];
-  ul[0] = nl;
-  ur[0] = nr;
-#pragma unroll
-  for (int q = 0; q < NDIM; ++q) {
-    ul[1 + q] = nl * wl[1 + q];
-    ur[1 + q] = nr * wr[1 + q];
-  }
-  ul[NV - 1] = wl[NV - 1] + T(0.5) * nl * v2l;
-  ur[NV - 1] = wr[NV - 1] + T(0.5) * nr * v2r;
-
   const T vl = wl[1 + Q], vr = wr[1 + Q];
-  T fl[NV], fr[NV];
-#pragma unroll
-  for (int v = 0; v < NV - 1; ++v) {
-    fl[v] = ul[v] * vl;
-    fr[v] = ur[v] * vr;
-  }
-  fl[1 + Q] += pl;
-  fr[1 + Q] += pr;
-  fl[NV - 1] = (ul[NV - 1] + pl) * vl;
-  fr[NV - 1] = (ur[NV - 1] + pr) * vr;
-
   const T cl = fsqrt(gamma * fdiv(pl, nl));
   const T cr = fsqrt(gamma * fdiv(pr, nr));
   const T ap = fmax(T(0), fmax(vl + cl, vr + cr));
   const T am = fmax(T(0), fmax(cl - vl, cr - vr));
 
-  if (SOLVER == SOLVER_HLL) {
+  if constexpr (SOLVER == SOLVER_HLL) {
+    T ul[NV], ur[NV], fl[NV], fr[NV];
+    side_state<T, NDIM, Q>(wl, pl, ul, fl);
+    side_state<T, NDIM, Q>(wr, pr, ur, fr);
     const T inv = frcp(ap + am);
     const T apam = ap * am;
 #pragma unroll
     for (int v = 0; v < NV; ++v) F[v] = (ap * fl[v] + am * fr[v] - apam * (ur[v] - ul[v])) * inv;
-    return;
-  }
-
-  // HLLC
-  const T sl = am + vl;  // = -(S_L - v_L) > 0
-  const T sr = ap - vr;  // =   S_R - v_R  > 0
-  const T alpha_m = fdiv(ur[1 + Q] * sr + ul[1 + Q] * sl - (pr - pl), nr * sr + nl * sl);
-  const bool left = am == T(0) || (ap != T(0) && alpha_m >= T(0));
-  const T SK = left ? -am : ap;
-  const T nK = left ? nl : nr;
-  const T vK = left ? vl : vr;
-  const T pK = left ? pl : pr;
-  const T dK = SK - vK;                       // S_K - v_K
-  const T rden = SK == T(0) ? T(0) : frcp(SK - alpha_m);
-  const T Ds = nK * dK * rden;
-  const T ps = pK + nK * dK * (alpha_m - vK);
-  T us[NV];
-  us[0] = Ds;
+  } else {
+    // HLLC.  Only the selected side K enters F* = F_K + S_K (U* - U_K), so
+    // its primitives are selected first and U_K, F_K formed once.
+    const T sl = am + vl;  // = -(S_L - v_L) > 0
+    const T sr = ap - vr;  // =   S_R - v_R  > 0
+    const T ml = nl * vl, mr = nr * vr;  // normal momenta
+    const T alpha_m = fdiv(mr * sr + ml * sl - (pr - pl), nr * sr + nl * sl);
+    const bool left = am == T(0) || (ap != T(0) && alpha_m >= T(0));
+    const T SK = left ? -am : ap;
+    const T pK = left ? pl : pr;
+    T wK[NV];
 #pragma unroll
-  for (int q = 0; q < NDIM; ++q) us[1 + q] = Ds * (q == Q ? alpha_m : (left ? wl[1 + q] : wr[1 + q]));
-  const T GK = left ? ul[NV - 1] : ur[NV - 1];
-  us[NV - 1] = (dK * GK - pK * vK + ps * alpha_m) * rden;
+    for (int v = 0; v < NV; ++v) wK[v] = left ? wl[v] : wr[v];
+    const T nK = wK[0], vK = wK[1 + Q];
+    T uK[NV], fK[NV];
+    side_state<T, NDIM, Q>(wK, pK, uK, fK);
+    const T dK = SK - vK;  // S_K - v_K
+    const T rden = SK == T(0) ? T(0) : frcp(SK - alpha_m);
+    const T Ds = nK * dK * rden;
+    const T ps = pK + nK * dK * (alpha_m - vK);
+    T us[NV];
+    us[0] = Ds;
 #pragma unroll
-  for (int v = 0; v < NV; ++v) {
-    const T fK = left ? fl[v] : fr[v];
-    const T uK = left ? ul[v] : ur[v];
-    F[v] = fK + SK * (us[v] - uK);
+    for (int q = 0; q < NDIM; ++q) us[1 + q] = Ds * (q == Q ? alpha_m : wK[1 + q]);
+    us[NV - 1] = (dK * uK[NV - 1] - pK * vK + ps * alpha_m) * rden;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) F[v] = fK[v] + SK * (us[v] - uK[v]);
   }
 }
 
