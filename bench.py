@@ -153,10 +153,16 @@ FLOPS_3D["hllc_switch"] = FLOPS_3D["hllc"]  # away from shocks; the detector's o
 PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 PEAK_FP64_TFLOPS = 1.25
 # DRAM bytes (read + write) per cell of the FP32 HLLC 3D stage kernels, from
-# one ncu capture of the same kernels at 192^3 (summary under profiles/),
-# scaled to the bench's cell count (traffic grows with the cells).
-TRAFFIC_PER_CELL_FP32_HLLC = {"stage1": (148.547072e6 + 104.710144e6) / 192 ** 3,
-                              "stage2": (298.134016e6 + 120.053760e6) / 192 ** 3}
+# one ncu capture of the same kernels at 192^3 for each launch configuration
+# (tile, planes per CTA) the autotuner picks at 256^3 (summary under
+# profiles/), scaled to the bench's cell count (traffic grows with the cells).
+# Other configurations report no traffic.
+TRAFFIC_PER_CELL_FP32_HLLC = {
+    (0, 48): {"stage1": (148.528128e6 + 104.334592e6) / 192 ** 3,
+              "stage2": (297.726720e6 + 119.101952e6) / 192 ** 3},
+    (7, 24): {"stage1": (159.187200e6 + 111.706880e6) / 192 ** 3,
+              "stage2": (324.736000e6 + 122.215680e6) / 192 ** 3},
+}
 
 
 def cpu_baseline(n_sample=256, steps=3):
@@ -294,8 +300,8 @@ def run_ours(args):
     # operations are measured against the FP32 vector peak
     peak_f = PEAK_FP64_TFLOPS if prec == H.FP64 else PEAK_FP32_TFLOPS
     achieved_f = flops / (dom_ms * 1e-3) / 1e12
-    traffic = (TRAFFIC_PER_CELL_FP32_HLLC[dom] * cells
-               if b == 4 and args.solver == "hllc" else None)
+    per_cell = TRAFFIC_PER_CELL_FP32_HLLC.get((tile["tile"], tile["kchunk"]))
+    traffic = (per_cell[dom] * cells if per_cell and b == 4 and args.solver == "hllc" else None)
     # The stage kernel is bound by instruction issue on the vector pipes (ncu),
     # not by DRAM: the roofline is the vector-arithmetic one; the HBM figure of
     # the metric is reported beside it.
@@ -306,7 +312,8 @@ def run_ours(args):
                 "peak_source": ("nominal FP64 1.25 TFLOP/s" if prec == H.FP64
                                 else "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"),
                 "algorithmic_flops_per_cell": FLOPS_3D[args.solver], "traffic": traffic,
-                "traffic_source": ("ncu dram bytes at 192^3 scaled by cells" if traffic else None),
+                "traffic_source": (f"ncu dram bytes at 192^3, tile {tile['tile']}, {tile['kchunk']} planes "
+                                   "per CTA, scaled by cells" if traffic else None),
                 "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                         "peak_source": f"{peak_kind} hbm_gbs", "algorithmic_bytes_per_cell": dom_bytes // cells,
                         "step_frac": (bytes1 + bytes2) / ((st1 + fin + st2) * 1e-3) / 1e9 / peak},
