@@ -630,6 +630,8 @@ def run_fmr(args):
             U[4, o:o + 2, o:o + 2, o:o + 2] = 1.0 / (8 * h ** 3)
         g.set_level(l, U)
         del U
+    if not args.no_autotune:
+        g.autotune(2)
     # warm-up; the first global step also restricts the deposit onto the covered coarse cells
     g.step(max(args.warmup, 3), 0.3)  # also captures the two-step graph
     torch.cuda.synchronize()

@@ -431,6 +431,11 @@ int genasis_fmr_get_level(genasis_fmr_t f, int level, double *U);
  * is non-NULL it synchronises, stores the time reached and reports
  * ENONPHYS if any level met a non-physical state. */
 int genasis_fmr_step(genasis_fmr_t f, int nsteps, double cfl, double *t_out);
+/* Autotune each level's launch configuration (genasis_hydro_autotune on the
+ * level's mesh and current state, which is restored; trial_steps >= 1).  Call
+ * after the levels are set; results are bitwise those of any other
+ * configuration.  Synchronises. */
+int genasis_fmr_autotune(genasis_fmr_t f, int trial_steps);
 
 #ifdef __cplusplus
 }

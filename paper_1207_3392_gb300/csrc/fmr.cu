@@ -156,7 +156,7 @@ __global__ void fmr_speed_kernel(const T* __restrict__ U, LevelGeo g, double gam
   const unsigned N = g.N, np = g.npad;
   const unsigned ni = N * (NDIM > 1 ? N : 1) * (NDIM > 2 ? N : 1);
   const size_t vs = (size_t)np * (NDIM > 1 ? np : 1) * (NDIM > 2 ? np : 1);
-  double best = 0.0;
+  T best = T(0);  // a max is exact in the state precision; widened once below
   for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < ni; t += gridDim.x * blockDim.x) {
     const unsigned t1 = t / N;
     const int i = (int)(t - t1 * N) + g.off, j = NDIM > 1 ? (int)(t1 % N) + g.off : 0,
@@ -166,10 +166,10 @@ __global__ void fmr_speed_kernel(const T* __restrict__ U, LevelGeo g, double gam
     for (int v = 0; v < NV; ++v) u[v] = U[v * vs + c];
     recover<NDIM>(u, w);
     const T cs = fsqrt((T)gamma * fdiv((T)(gamma - 1.0) * w[NV - 1], w[0]));
-    for (int q = 0; q < NDIM; ++q) best = fmax(best, (double)(fabs(w[1 + q]) + cs));
+    for (int q = 0; q < NDIM; ++q) best = fmax(best, fabs(w[1 + q]) + cs);
   }
-  best = warp_max(best);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = best;
+  const double bw = warp_max((double)best);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = bw;
   __syncthreads();
   if (threadIdx.x == 0) {
     double acc = red[0];
@@ -303,55 +303,52 @@ __global__ void fmr_parent_faces_kernel(StageArgs<T> A, const T* __restrict__ U0
 
 // This level as child: acc += dt x the mean over the 2^(d-1) fine faces of
 // each parent face of the Heun-effective fluxes through the level's own box
-// boundary (pairs along the slowest transverse axis first).
+// boundary (pairs along the slowest transverse axis first).  One thread per
+// fine face; the 2^(d-1) threads of a parent face are adjacent lanes of one
+// warp and combine their fluxes by shuffles in that pairing order.  Launched
+// with exactly ceil(total / 128) blocks of 128 threads and no early return,
+// so every lane of a warp reaches the shuffles.
 template <class T, int NDIM, int SOLVER>
-__global__ void fmr_child_faces_kernel(StageArgs<T> A, const T* __restrict__ U0, const T* __restrict__ K,
-                                       LevelGeo g, double* __restrict__ acc) {
+__global__ void __launch_bounds__(128) fmr_child_faces_kernel(StageArgs<T> A, const T* __restrict__ U0,
+                                                              const T* __restrict__ K, LevelGeo g,
+                                                              double* __restrict__ acc) {
   constexpr int NV = NDIM + 2;
+  constexpr int G = 1 << (NDIM - 1);  // fine faces per parent face
   const int M = g.N / 2;
   const int per = NDIM == 1 ? 1 : NDIM == 2 ? M : M * M;
   const size_t vs = (size_t)A.n[0] * A.n[1] * A.n[2];
   const double dtd = *A.dt;
   const T dt = (T)dtd;
   const int total = NDIM * 2 * per;
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
-    const int tr = t % per, side = (t / per) % 2, q = t / (2 * per);
-    int base[3] = {0, 0, 0}, ax[2] = {-1, -1}, na = 0;
+  const int tt = blockIdx.x * blockDim.x + threadIdx.x;
+  const int t = tt / G, sub = tt % G;  // parent face, fine face within it
+  const bool act = t < total;
+  double m[NV];
+  for (int v = 0; v < NV; ++v) m[v] = 0.0;
+  int tr = 0, side = 0, q = 0;
+  if (act) {
+    tr = t % per;
+    side = (t / per) % 2;
+    q = t / (2 * per);
+    int c[3] = {0, 0, 0}, na = 0;
     int r0 = tr;
     for (int r = 0; r < NDIM; ++r) {
       if (r == q) continue;
-      base[r] = g.off + 2 * (r0 % M);
+      // transverse axes, fastest first: sub bit 0 along the faster, bit 1 along the slower
+      c[r] = g.off + 2 * (r0 % M) + ((sub >> na) & 1);
       r0 /= M;
-      ax[na++] = r;  // transverse axes, fastest first
+      ++na;
     }
-    base[q] = side == 0 ? g.off : g.off + g.N;
-    double m[NV];
-    if (NDIM == 1) {
-      double Fe[NV];
-      face_eff_q<T, NDIM, SOLVER>(q, A, U0, K, dt, base[0], base[1], base[2], vs, Fe);
-      for (int v = 0; v < NV; ++v) m[v] = Fe[v];
-    } else if (NDIM == 2) {
-      double F0[NV], F1[NV];
-      int c1[3] = {base[0], base[1], base[2]};
-      c1[ax[0]] += 1;
-      face_eff_q<T, NDIM, SOLVER>(q, A, U0, K, dt, base[0], base[1], base[2], vs, F0);
-      face_eff_q<T, NDIM, SOLVER>(q, A, U0, K, dt, c1[0], c1[1], c1[2], vs, F1);
-      for (int v = 0; v < NV; ++v) m[v] = (F0[v] + F1[v]) / 2.0;
-    } else {
-      // transverse axes ax[0] (faster) and ax[1] (slower): pair along the slower first
-      double b[2][NV];
-      for (int a0 = 0; a0 < 2; ++a0) {
-        double Fa[NV], Fb[NV];
-        int ca[3] = {base[0], base[1], base[2]}, cb[3];
-        ca[ax[0]] += a0;
-        for (int r = 0; r < 3; ++r) cb[r] = ca[r];
-        cb[ax[1]] += 1;
-        face_eff_q<T, NDIM, SOLVER>(q, A, U0, K, dt, ca[0], ca[1], ca[2], vs, Fa);
-        face_eff_q<T, NDIM, SOLVER>(q, A, U0, K, dt, cb[0], cb[1], cb[2], vs, Fb);
-        for (int v = 0; v < NV; ++v) b[a0][v] = (Fa[v] + Fb[v]) / 2.0;
-      }
-      for (int v = 0; v < NV; ++v) m[v] = (b[0][v] + b[1][v]) / 2.0;
-    }
+    c[q] = side == 0 ? g.off : g.off + g.N;
+    face_eff_q<T, NDIM, SOLVER>(q, A, U0, K, dt, c[0], c[1], c[2], vs, m);
+  }
+  if constexpr (NDIM == 3) {
+    for (int v = 0; v < NV; ++v) m[v] = (m[v] + __shfl_xor_sync(0xffffffffu, m[v], 2)) / 2.0;  // slower axis
+  }
+  if constexpr (NDIM >= 2) {
+    for (int v = 0; v < NV; ++v) m[v] = (m[v] + __shfl_xor_sync(0xffffffffu, m[v], 1)) / 2.0;  // faster axis
+  }
+  if (act && sub == 0) {
     for (int v = 0; v < NV; ++v) {
       const size_t o = cf_index(NDIM, M, q, side, v, tr);
       acc[o] = acc[o] + dtd * m[v];
@@ -526,7 +523,9 @@ struct FmrRun {
     fmr_advance_time_kernel<<<1, 32, 0, st>>>(f->ltime, f->ldt, i);
     GH_CK(cudaGetLastError());
     if (acc) {
-      fmr_child_faces_kernel<T, NDIM, SOLVER><<<nfc, 128, 0, st>>>(A, U0, (const T*)h->K, f->geo[i], acc);
+      const size_t nfine = (f->cf_count / (NDIM + 2)) << (NDIM - 1);  // fine faces on the box boundary
+      fmr_child_faces_kernel<T, NDIM, SOLVER>
+          <<<(unsigned)((nfine + 127) / 128), 128, 0, st>>>(A, U0, (const T*)h->K, f->geo[i], acc);
       GH_CK(cudaGetLastError());
     }
     return GENASIS_OK;
@@ -680,6 +679,22 @@ int genasis_fmr_get_level(genasis_fmr_t f, int level, double* U) {
   if (!f || !U) return fail(GENASIS_EINVAL, "NULL argument");
   if (level < 0 || level >= f->L) return fail(GENASIS_EINVAL, "fmr: level out of range");
   return genasis_hydro_get_conserved(f->lev[level], U, GENASIS_FP64);
+}
+
+int genasis_fmr_autotune(genasis_fmr_t f, int trial_steps) {
+  if (!f) return fail(GENASIS_EINVAL, "NULL handle");
+  if (trial_steps < 1) return fail(GENASIS_EINVAL, "fmr_autotune: trial_steps must be >= 1");
+  // each level's tile and plane count, timed on its own mesh and state (which
+  // the level's autotune restores); the captured steps hold the old launches
+  for (genasis_hydro* h : f->lev) {
+    const int rc = genasis_hydro_autotune(h, trial_steps, nullptr);
+    if (rc) return rc;
+  }
+  if (f->graph) {
+    cudaGraphExecDestroy(f->graph);
+    f->graph = nullptr;
+  }
+  return GENASIS_OK;
 }
 
 int genasis_fmr_step(genasis_fmr_t f, int nsteps, double cfl, double* t_out) {

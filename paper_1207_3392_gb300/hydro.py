@@ -71,6 +71,7 @@ SIGNATURES = {
     "genasis_fmr_set_level": [_P, _I, _P],
     "genasis_fmr_get_level": [_P, _I, _P],
     "genasis_fmr_step": [_P, _I, ctypes.c_double, _P],
+    "genasis_fmr_autotune": [_P, _I],
     "genasis_hydro_set_tile": [_P, _I, _I],
     "genasis_hydro_get_tile": [_P, _P],
     "genasis_hydro_autotune": [_P, _I, ctypes.c_char_p],
@@ -395,6 +396,10 @@ class Fmr:
         out = np.empty(self.stored_shape(level))
         check(load().genasis_fmr_get_level(self._h, int(level), out.ctypes.data))
         return out
+
+    def autotune(self, trial_steps=2):
+        """Autotune every level's launch configuration on its current state."""
+        check(load().genasis_fmr_autotune(self._h, int(trial_steps)))
 
     def step(self, nsteps, cfl):
         t = ctypes.c_double()

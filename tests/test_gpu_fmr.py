@@ -65,6 +65,27 @@ def test_fmr_graph_replay_equals_stepwise():
     b.close()
 
 
+def test_fmr_autotune_keeps_results():
+    """Autotuning the levels restores their states, and the tuned launch
+    configurations step to bitwise the same levels."""
+    nd, N, L = 3, 32, 3
+    M = F.sedov(nd, N, L)
+    a = H.Fmr(nd, N, L, 1.0, 1, precision=H.FP32_MIXED)
+    b = H.Fmr(nd, N, L, 1.0, 1, precision=H.FP32_MIXED)
+    for l in range(L):
+        a.set_level(l, np.ascontiguousarray(M.U[l]))
+        b.set_level(l, np.ascontiguousarray(M.U[l]))
+    b.autotune(1)
+    for l in range(L):
+        np.testing.assert_array_equal(b.get_level(l), a.get_level(l))
+    ta, tb = a.step(4, 0.3), b.step(4, 0.3)
+    assert ta == tb
+    for l in range(L):
+        np.testing.assert_array_equal(b.get_level(l), a.get_level(l))
+    a.close()
+    b.close()
+
+
 def test_fmr_hll_and_leaf_conservation():
     nd, N, L = 2, 32, 3
     M, out, _, _ = _run(nd, N, L, 10, H.FP64, solver=0)
