@@ -434,7 +434,13 @@ struct StageKernel {
         load_col(A, own, m + 2, dt, vs, wk2, fk2);
         const Geo<T> g0 = geo(A, AM, m), g1 = geo(A, AM, m + 1);
         slopes(A, wk, wk1, wk2, g1, sk1);
-        m_face(A, wk, sk, g0.h, wk1, sk1, g1.h, (unsigned)(fk | fk1), fhi);
+        // the face m0 - 3/2 of the first warm-up plane is never used
+        if (m > m0 - 2) {
+          m_face(A, wk, sk, g0.h, wk1, sk1, g1.h, (unsigned)(fk | fk1), fhi);
+        } else {
+#pragma unroll
+          for (int v = 0; v < NV; ++v) fhi[v] = T(0);
+        }
         if (m < m0) {  // warm-up planes: advance the ring only
 #pragma unroll
           for (int v = 0; v < NV; ++v) {
