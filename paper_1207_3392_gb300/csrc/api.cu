@@ -443,8 +443,8 @@ int genasis_hydro_create(const genasis_hydro_desc* d, genasis_hydro_t* out) {
   }
   GH_CK_CREATE(cudaMalloc(&h->K, bytes));
   if (h->solver == GENASIS_HLLC_SWITCH) GH_CK_CREATE(cudaMalloc(&h->flags, h->ncell));
-  GH_CK_CREATE(cudaMalloc(&h->scal, SCAL_COUNT * sizeof(double)));
-  GH_CK_CREATE(cudaMemsetAsync(h->scal, 0, SCAL_COUNT * sizeof(double), h->stream));
+  GH_CK_CREATE(cudaMalloc(&h->scal, SCAL_ALLOC * sizeof(double)));
+  GH_CK_CREATE(cudaMemsetAsync(h->scal, 0, SCAL_ALLOC * sizeof(double), h->stream));
   GH_CK_CREATE(cudaMalloc(&h->status, sizeof(unsigned)));
   GH_CK_CREATE(cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream));
   rc = h->prec == GENASIS_FP64         ? upload_geometry<double>(h, d)

@@ -104,41 +104,69 @@ __global__ void totals_kernel(ReduceArgs<T> A) {
   }
 }
 
-// One CTA of 256 threads: fold the per-CTA partials in a fixed order (strided
-// per-thread sums, then a fixed tree), then set dt and t.
+// Fold the per-CTA partials in a fixed order, spread over FIN_CTAS CTAs of one
+// warp (FP64 arithmetic is slow on this GPU: a single CTA spent ~17 us here).
+// CTA g folds slice g of the partials sequentially: lane v < nv the totals of
+// variable v, lane 5 the largest speed, compared as bit patterns (positive
+// doubles order like them).  The last CTA to finish folds the FIN_CTAS slice
+// results in order, then sets dt and t:
 //   mode FIN_FIXED : dt = fixed_dt
 //   mode FIN_CFL   : dt = cfl / max speed            (Eq. courantTimeStep x C_CFL)
 //   mode FIN_REDUCE: only store dt_CFL and totals
-// With t_end > 0 the step is clamped so that t never passes t_end.
-__global__ void __launch_bounds__(256) finalize_kernel(FinalizeArgs A) {
-  __shared__ double red[32];
-  __shared__ double tsum[5][256];
-  const int tid = threadIdx.x;
-  double best = 0.0;
-  if (A.part_speed)
-    for (int i = tid; i < A.nblk; i += blockDim.x) best = fmax(best, A.part_speed[i]);
-  best = warp_max(best);
-  if ((tid & 31) == 0) red[tid >> 5] = best;
-  if (A.part_tot) {
-    // thread t sums partials t, t + 256, ... in order; then a fixed tree
-    for (int v = 0; v < A.nv; ++v) {
-      double s = 0.0;
-      for (int i = tid; i < A.nblk; i += blockDim.x) s += A.part_tot[(size_t)i * A.nv + v];
-      tsum[v][tid] = s;
+// With t_end > 0 the step is clamped so that t never passes t_end.  No CTA
+// waits for another: the last one to take a ticket does the fold.
+__global__ void __launch_bounds__(32) finalize_kernel(FinalizeArgs A) {
+  constexpr unsigned long long SIGNLESS = 0x7fffffffffffffffull;  // a -0.0 compares as +0.0
+  const int lane = threadIdx.x, g = blockIdx.x;
+  double* work = A.scal + SCAL_COUNT;  // [FIN_CTAS][6]: totals 0..4, speed bits 5
+  unsigned* ticket = reinterpret_cast<unsigned*>(A.scal + SCAL_COUNT + FIN_CTAS * 6);
+  const bool tot = A.part_tot != nullptr, spd = A.part_speed != nullptr;
+  const long long lo = (long long)A.nblk * g / FIN_CTAS, hi = (long long)A.nblk * (g + 1) / FIN_CTAS;
+  double val = 0.0;
+  // (unrolled so that eight loads are in flight: the folds are latency-bound)
+  if (lane < A.nv && tot) {
+#pragma unroll 8
+    for (long long i = lo; i < hi; ++i) val += A.part_tot[i * A.nv + lane];
+  } else if (lane == 5 && spd) {
+    unsigned long long m = 0;
+#pragma unroll 8
+    for (long long i = lo; i < hi; ++i) {
+      const unsigned long long b = (unsigned long long)__double_as_longlong(A.part_speed[i]) & SIGNLESS;
+      m = b > m ? b : m;
     }
+    val = __longlong_as_double((long long)m);
   }
-  __syncthreads();
-  if (A.part_tot) {
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-      if (tid < w)
-        for (int v = 0; v < A.nv; ++v) tsum[v][tid] += tsum[v][tid + w];
-      __syncthreads();
+  // lane 0 publishes the slice, then takes a ticket
+  double mine[6];
+#pragma unroll
+  for (int v = 0; v < 6; ++v) mine[v] = __shfl_sync(0xffffffffu, val, v);
+  unsigned t = 0;
+  if (lane == 0) {
+#pragma unroll
+    for (int v = 0; v < 6; ++v) work[g * 6 + v] = mine[v];
+    __threadfence();
+    t = atomicAdd(ticket, 1u);
+  }
+  t = __shfl_sync(0xffffffffu, t, 0);
+  if (t != FIN_CTAS - 1) return;
+  __threadfence();
+  double fold = 0.0;
+  if (lane < A.nv && tot) {
+#pragma unroll 8
+    for (int k = 0; k < FIN_CTAS; ++k) fold += __ldcg(work + k * 6 + lane);
+    A.scal[SCAL_TOT + lane] = fold;
+  } else if (lane == 5 && spd) {
+    unsigned long long m = 0;
+#pragma unroll 8
+    for (int k = 0; k < FIN_CTAS; ++k) {
+      const unsigned long long b = (unsigned long long)__double_as_longlong(__ldcg(work + k * 6 + 5)) & SIGNLESS;
+      m = b > m ? b : m;
     }
-    if (tid < A.nv) A.scal[SCAL_TOT + tid] = tsum[tid][0];
+    fold = __longlong_as_double((long long)m);
   }
-  if (tid == 0) {
-    double m = red[0];
-    for (int i = 1; i < (int)(blockDim.x >> 5); ++i) m = fmax(m, red[i]);
+  const double m = __shfl_sync(0xffffffffu, fold, 5);
+  if (lane == 0) {
+    *ticket = 0;  // for the next launch on this scalar block
     if (A.part_speed) A.scal[SCAL_DTCFL] = 1.0 / m;
     if (A.mode != FIN_REDUCE) {
       double dt = A.mode == FIN_CFL ? A.cfl * (1.0 / m) : A.fixed_dt;
@@ -256,7 +284,7 @@ cudaError_t launch_shock_flags(int ndim, const FlagArgs<T>& A, cudaStream_t s) {
 }
 
 cudaError_t launch_finalize(const FinalizeArgs& A, cudaStream_t s) {
-  finalize_kernel<<<1, 256, 0, s>>>(A);
+  finalize_kernel<<<FIN_CTAS, 32, 0, s>>>(A);
   return cudaGetLastError();
 }
 

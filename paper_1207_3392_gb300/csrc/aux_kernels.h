@@ -9,6 +9,12 @@ namespace gh {
 // Slots of the per-handle device scalar block.
 enum { SCAL_DT = 0, SCAL_T = 1, SCAL_DTCFL = 2, SCAL_TOT = 3, SCAL_COUNT = 8 };
 enum { FIN_FIXED = 0, FIN_CFL = 1, FIN_REDUCE = 2 };
+// The finalize kernel folds the per-CTA partials over FIN_CTAS CTAs.  Its
+// workspace follows the scalar block: FIN_CTAS x 6 doubles (slice results),
+// then a ticket counter (zero between launches).  A scalar block that a
+// finalize launch uses holds SCAL_ALLOC doubles, zeroed at allocation.
+constexpr int FIN_CTAS = 32;
+constexpr int SCAL_ALLOC = SCAL_COUNT + FIN_CTAS * 6 + 1;
 
 template <class T>
 struct ReduceArgs {

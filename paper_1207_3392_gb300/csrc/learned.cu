@@ -1018,8 +1018,8 @@ int genasis_learned_create(const genasis_hydro_desc* d, genasis_learned_t* out) 
     LCK(cudaMemsetAsync(l->flag[b], 0, l->ncell, l->stream));
   }
   LCK(cudaMalloc((void**)&l->params, mlp::NPARAM * sizeof(float)));
-  LCK(cudaMalloc((void**)&l->scal, SCAL_COUNT * sizeof(double)));
-  LCK(cudaMemsetAsync(l->scal, 0, SCAL_COUNT * sizeof(double), l->stream));
+  LCK(cudaMalloc((void**)&l->scal, SCAL_ALLOC * sizeof(double)));
+  LCK(cudaMemsetAsync(l->scal, 0, SCAL_ALLOC * sizeof(double), l->stream));
   LCK(cudaMalloc((void**)&l->part_speed, 1024 * sizeof(double)));
   LCK(cudaMalloc((void**)&l->status, sizeof(unsigned)));
   LCK(cudaMemsetAsync(l->status, 0, sizeof(unsigned), l->stream));

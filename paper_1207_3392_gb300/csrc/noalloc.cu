@@ -31,8 +31,8 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH
 
 // Scratch layout (byte offsets, each region 256-byte aligned).
 static constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
-static constexpr size_t OFF_SCAL = 0;                                                   // SCAL_COUNT doubles
-static constexpr size_t OFF_STATUS = align256(OFF_SCAL + SCAL_COUNT * sizeof(double));  // unsigned
+static constexpr size_t OFF_SCAL = 0;                                                   // SCAL_ALLOC doubles
+static constexpr size_t OFF_STATUS = align256(OFF_SCAL + SCAL_ALLOC * sizeof(double));  // unsigned
 static constexpr size_t OFF_SPEED = align256(OFF_STATUS + sizeof(unsigned));
 static constexpr size_t OFF_TOT = align256(OFF_SPEED + NOALLOC_MAX_CTAS * sizeof(double));
 static constexpr size_t GEO_N = NOALLOC_MAX_N + 4;
@@ -144,7 +144,7 @@ static int noalloc_step_t(const genasis_hydro_desc* d, unsigned char* base, cons
   T* K = (T*)(base + OFF_K);
 
   // clear what must start at zero; the previous call's contents stay otherwise
-  GH_CK(cudaMemsetAsync(scal, 0, SCAL_COUNT * sizeof(double), st));
+  GH_CK(cudaMemsetAsync(scal, 0, SCAL_ALLOC * sizeof(double), st));
   GH_CK(cudaMemsetAsync(status, 0, sizeof(unsigned), st));
   for (int q = 0; q < ndim; ++q) {
     GH_CK(cudaMemcpyAsync(wd + (size_t)q * NOALLOC_MAX_N, d->widths[q], (size_t)n[q] * sizeof(double),

@@ -105,7 +105,7 @@ struct StageKernel {
   // Boundary-mapped in-plane part of a cell address (fixed for a tile): the
   // march coordinate is mapped per plane by load_col.
   struct ColRef {
-    size_t off;
+    unsigned off;  // in-plane offset: below n0 n1 (< 2^32 for any plane held in memory)
     bool fa, fb;
   };
 
@@ -116,7 +116,7 @@ struct StageKernel {
     int sb = 0;
     if constexpr (HAS_Y) sb = bc_map(b, A.n[1], A.bc_lo[1], A.bc_hi[1], fb);
     r.fb = fb;
-    r.off = HAS_Y ? (size_t)sb * A.n[0] + sa : (size_t)sa;
+    r.off = HAS_Y ? (unsigned)sb * (unsigned)A.n[0] + (unsigned)sa : (unsigned)sa;
     return r;
   }
 
