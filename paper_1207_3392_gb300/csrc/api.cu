@@ -799,7 +799,7 @@ int genasis_hydro_autotune(genasis_hydro_t h, int trial_steps, const char* cache
     if (!stage_variant(h->ndim, h->prec, h->solver, 1, tile, &probe)) continue;  // not compiled for this solver
     std::vector<int> kcs = {0};
     if (h->ndim >= 2)
-      for (int kc : {12, 16, 24, 32, 48, 64})
+      for (int kc : {12, 16, 24, 32, 40, 48, 64})
         if (kc < nm) kcs.push_back(kc);
     for (int kc : kcs) {
       rc = configure(h, tile, kc);
