@@ -106,66 +106,77 @@ __global__ void totals_kernel(ReduceArgs<T> A) {
 
 // Fold the per-CTA partials in a fixed order, spread over FIN_CTAS CTAs of one
 // warp (FP64 arithmetic is slow on this GPU: a single CTA spent ~17 us here).
-// CTA g folds slice g of the partials sequentially: lane v < nv the totals of
-// variable v, lane 5 the largest speed, compared as bit patterns (positive
-// doubles order like them).  The last CTA to finish folds the FIN_CTAS slice
-// results in order, then sets dt and t:
+// CTA g takes slice g of the partials: lane j the partials j, j + 32, ... of
+// the slice in order (the totals of every variable, and the largest speed,
+// compared as bit patterns, which order like positive doubles), then a fixed
+// butterfly across the lanes.  The last CTA to finish folds the FIN_CTAS slice
+// results the same way (one per lane), then sets dt and t:
 //   mode FIN_FIXED : dt = fixed_dt
 //   mode FIN_CFL   : dt = cfl / max speed            (Eq. courantTimeStep x C_CFL)
 //   mode FIN_REDUCE: only store dt_CFL and totals
 // With t_end > 0 the step is clamped so that t never passes t_end.  No CTA
 // waits for another: the last one to take a ticket does the fold.
+namespace {
+// Fixed butterfly over the warp: every lane ends with the same sum / max.
+__device__ __forceinline__ void fold_warp(double (&s)[5], unsigned long long& m) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) s[v] += __shfl_xor_sync(0xffffffffu, s[v], o);
+    const unsigned long long b = __shfl_xor_sync(0xffffffffu, m, o);
+    m = b > m ? b : m;
+  }
+}
+}  // namespace
+
 __global__ void __launch_bounds__(32) finalize_kernel(FinalizeArgs A) {
   constexpr unsigned long long SIGNLESS = 0x7fffffffffffffffull;  // a -0.0 compares as +0.0
+  static_assert(FIN_CTAS <= 32, "one slice result per lane in the last fold");
   const int lane = threadIdx.x, g = blockIdx.x;
   double* work = A.scal + SCAL_COUNT;  // [FIN_CTAS][6]: totals 0..4, speed bits 5
   unsigned* ticket = reinterpret_cast<unsigned*>(A.scal + SCAL_COUNT + FIN_CTAS * 6);
   const bool tot = A.part_tot != nullptr, spd = A.part_speed != nullptr;
   const long long lo = (long long)A.nblk * g / FIN_CTAS, hi = (long long)A.nblk * (g + 1) / FIN_CTAS;
-  double val = 0.0;
-  // (unrolled so that eight loads are in flight: the folds are latency-bound)
-  if (lane < A.nv && tot) {
-#pragma unroll 8
-    for (long long i = lo; i < hi; ++i) val += A.part_tot[i * A.nv + lane];
-  } else if (lane == 5 && spd) {
-    unsigned long long m = 0;
-#pragma unroll 8
-    for (long long i = lo; i < hi; ++i) {
-      const unsigned long long b = (unsigned long long)__double_as_longlong(A.part_speed[i]) & SIGNLESS;
-      m = b > m ? b : m;
-    }
-    val = __longlong_as_double((long long)m);
-  }
-  // lane 0 publishes the slice, then takes a ticket
-  double mine[6];
+  double s[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  unsigned long long mb = 0;
+#pragma unroll 2
+  for (long long i = lo + lane; i < hi; i += 32) {
+    if (tot) {
 #pragma unroll
-  for (int v = 0; v < 6; ++v) mine[v] = __shfl_sync(0xffffffffu, val, v);
+      for (int v = 0; v < 5; ++v)
+        if (v < A.nv) s[v] += A.part_tot[i * A.nv + v];
+    }
+    if (spd) {
+      const unsigned long long b = (unsigned long long)__double_as_longlong(A.part_speed[i]) & SIGNLESS;
+      mb = b > mb ? b : mb;
+    }
+  }
+  fold_warp(s, mb);
+  // lane 0 publishes the slice, then takes a ticket
   unsigned t = 0;
   if (lane == 0) {
 #pragma unroll
-    for (int v = 0; v < 6; ++v) work[g * 6 + v] = mine[v];
+    for (int v = 0; v < 5; ++v) work[g * 6 + v] = s[v];
+    work[g * 6 + 5] = __longlong_as_double((long long)mb);
     __threadfence();
     t = atomicAdd(ticket, 1u);
   }
   t = __shfl_sync(0xffffffffu, t, 0);
   if (t != FIN_CTAS - 1) return;
   __threadfence();
-  double fold = 0.0;
-  if (lane < A.nv && tot) {
-#pragma unroll 8
-    for (int k = 0; k < FIN_CTAS; ++k) fold += __ldcg(work + k * 6 + lane);
-    A.scal[SCAL_TOT + lane] = fold;
-  } else if (lane == 5 && spd) {
-    unsigned long long m = 0;
-#pragma unroll 8
-    for (int k = 0; k < FIN_CTAS; ++k) {
-      const unsigned long long b = (unsigned long long)__double_as_longlong(__ldcg(work + k * 6 + 5)) & SIGNLESS;
-      m = b > m ? b : m;
-    }
-    fold = __longlong_as_double((long long)m);
+#pragma unroll
+  for (int v = 0; v < 5; ++v) s[v] = lane < FIN_CTAS ? __ldcg(work + lane * 6 + v) : 0.0;
+  mb = lane < FIN_CTAS ? (unsigned long long)__double_as_longlong(__ldcg(work + lane * 6 + 5)) : 0ull;
+  fold_warp(s, mb);
+  if (tot && lane < A.nv) {
+    double tv = s[0];
+#pragma unroll
+    for (int v = 1; v < 5; ++v) tv = lane == v ? s[v] : tv;
+    A.scal[SCAL_TOT + lane] = tv;
   }
-  const double m = __shfl_sync(0xffffffffu, fold, 5);
+  const double mx = __longlong_as_double((long long)mb);
   if (lane == 0) {
+    const double m = mx;
     *ticket = 0;  // for the next launch on this scalar block
     if (A.part_speed) A.scal[SCAL_DTCFL] = 1.0 / m;
     if (A.mode != FIN_REDUCE) {
