@@ -104,13 +104,14 @@ __global__ void totals_kernel(ReduceArgs<T> A) {
   }
 }
 
-// Fold the per-CTA partials in a fixed order, spread over FIN_CTAS CTAs of one
-// warp (FP64 arithmetic is slow on this GPU: a single CTA spent ~17 us here).
+// Fold the per-CTA partials in a fixed order, spread over G <= FIN_CTAS CTAs
+// of one warp (FP64 arithmetic is slow on this GPU: a single 256-thread CTA
+// spent ~17 us on 1.5k partials; with few partials one CTA, G = 1, is fastest).
 // CTA g takes slice g of the partials: lane j the partials j, j + 32, ... of
 // the slice in order (the totals of every variable, and the largest speed,
 // compared as bit patterns, which order like positive doubles), then a fixed
 // butterfly across the lanes.  The last CTA to finish folds the FIN_CTAS slice
-// results the same way (one per lane), then sets dt and t:
+// results the same way (one per lane; G = 1 skips this), then sets dt and t:
 //   mode FIN_FIXED : dt = fixed_dt
 //   mode FIN_CFL   : dt = cfl / max speed            (Eq. courantTimeStep x C_CFL)
 //   mode FIN_REDUCE: only store dt_CFL and totals
@@ -136,10 +137,11 @@ __global__ void __launch_bounds__(32) finalize_kernel(FinalizeArgs A) {
   double* work = A.scal + SCAL_COUNT;  // [FIN_CTAS][6]: totals 0..4, speed bits 5
   unsigned* ticket = reinterpret_cast<unsigned*>(A.scal + SCAL_COUNT + FIN_CTAS * 6);
   const bool tot = A.part_tot != nullptr, spd = A.part_speed != nullptr;
-  const long long lo = (long long)A.nblk * g / FIN_CTAS, hi = (long long)A.nblk * (g + 1) / FIN_CTAS;
+  const int G = gridDim.x;
+  const long long lo = (long long)A.nblk * g / G, hi = (long long)A.nblk * (g + 1) / G;
   double s[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
   unsigned long long mb = 0;
-#pragma unroll 2
+#pragma unroll 8
   for (long long i = lo + lane; i < hi; i += 32) {
     if (tot) {
 #pragma unroll
@@ -152,22 +154,24 @@ __global__ void __launch_bounds__(32) finalize_kernel(FinalizeArgs A) {
     }
   }
   fold_warp(s, mb);
-  // lane 0 publishes the slice, then takes a ticket
-  unsigned t = 0;
-  if (lane == 0) {
+  if (G > 1) {
+    // lane 0 publishes the slice, then takes a ticket
+    unsigned t = 0;
+    if (lane == 0) {
 #pragma unroll
-    for (int v = 0; v < 5; ++v) work[g * 6 + v] = s[v];
-    work[g * 6 + 5] = __longlong_as_double((long long)mb);
+      for (int v = 0; v < 5; ++v) work[g * 6 + v] = s[v];
+      work[g * 6 + 5] = __longlong_as_double((long long)mb);
+      __threadfence();
+      t = atomicAdd(ticket, 1u);
+    }
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (t != (unsigned)G - 1) return;
     __threadfence();
-    t = atomicAdd(ticket, 1u);
-  }
-  t = __shfl_sync(0xffffffffu, t, 0);
-  if (t != FIN_CTAS - 1) return;
-  __threadfence();
 #pragma unroll
-  for (int v = 0; v < 5; ++v) s[v] = lane < FIN_CTAS ? __ldcg(work + lane * 6 + v) : 0.0;
-  mb = lane < FIN_CTAS ? (unsigned long long)__double_as_longlong(__ldcg(work + lane * 6 + 5)) : 0ull;
-  fold_warp(s, mb);
+    for (int v = 0; v < 5; ++v) s[v] = lane < G ? __ldcg(work + lane * 6 + v) : 0.0;
+    mb = lane < G ? (unsigned long long)__double_as_longlong(__ldcg(work + lane * 6 + 5)) : 0ull;
+    fold_warp(s, mb);
+  }
   if (tot && lane < A.nv) {
     double tv = s[0];
 #pragma unroll
@@ -295,7 +299,7 @@ cudaError_t launch_shock_flags(int ndim, const FlagArgs<T>& A, cudaStream_t s) {
 }
 
 cudaError_t launch_finalize(const FinalizeArgs& A, cudaStream_t s) {
-  finalize_kernel<<<FIN_CTAS, 32, 0, s>>>(A);
+  finalize_kernel<<<A.nblk <= 512 ? 1 : FIN_CTAS, 32, 0, s>>>(A);
   return cudaGetLastError();
 }
 
