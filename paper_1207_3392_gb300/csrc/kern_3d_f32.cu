@@ -13,7 +13,11 @@ int tile_count_3d_f32() { return 9; }
 // phase); tiles 4 and 5 (512 threads) are in kern_3d_f32_wide.cu.  16 x 16,
 // 32 x 12, 32 x 14, 32 x 13 and 32 x 9 tiles were measured and lost.
 bool stage_variant_3d_f32(int solver, int stage, int tile, StageVariant* out) {
-  if (solver == SOLVER_HLLC_SW) return tile == 0 && pick_switch<3, float, 32, 8, 3>(stage, out);
+  if (solver == SOLVER_HLLC_SW) {
+    if (tile == 0) return pick_switch<3, float, 32, 8, 3>(stage, out);
+    if (tile == 8) return pick_switch<3, float, 32, 7, 4>(stage, out);
+    return false;
+  }
   switch (tile) {
     case 0: return pick_variant<3, float, 32, 8, 3>(solver, stage, out);
     case 1: return pick_variant<3, float, 32, 4, 6>(solver, stage, out);

@@ -222,6 +222,26 @@ def test_shock_switch_matches_oracle_3d(axis):
         _check(Ug, Uo, 3, tol, f"shock switch 3d axis {axis} prec={precision}")
 
 
+def test_shock_switch_tiles_identical():
+    """Every tile compiled with the switch (3D FP32) gives bitwise the same state."""
+    pr = P.planar_shock_3d(n_long=64, n_cross=10, axis=0, solver=P.HLLC_SWITCH)
+    ref, _ = gpu_run(pr, H.FP32_MIXED, steps=10, tile=0, kchunk=0)
+    h = H.Hydro.from_problem(pr, precision=H.FP32_MIXED)
+    count = h.tile_info()["tile_count"]
+    h.close()
+    done = 0
+    for tile in range(1, count):
+        try:
+            U, _ = gpu_run(pr, H.FP32_MIXED, steps=10, tile=tile, kchunk=7)
+        except H.HydroError as e:
+            if e.code != H.EINVAL:
+                raise
+            continue  # not compiled with the switch
+        np.testing.assert_array_equal(U, ref, err_msg=f"tile {tile}")
+        done += 1
+    assert done >= 1
+
+
 def test_shock_switch_suppresses_odd_even_gpu():
     """The odd-even decoupling of HLLC behind a Mach 20 shock (from 1e-6
     noise) on the GPU, and its absence with the switch; shock-free flows are
