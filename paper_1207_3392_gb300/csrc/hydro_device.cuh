@@ -64,6 +64,42 @@ __device__ __forceinline__ float minmod3(float a, float b, float c) {
   return fmaxf(lo, 0.0f) + fminf(hi, 0.0f);
 }
 
+// FP64: the extremes and sign tests on the integer pipe.  GB300's FP64 pipe
+// is the bound of the FP64 path (~2 operations per clock per SM), its integer
+// ALU far from it.  A double's bits, with the magnitude bits flipped when the
+// sign is set, order as signed integers like the doubles (NaN aside); -0.0
+// maps to -1 and +0.0 to 0.  The values returned are the operands themselves.
+__device__ __forceinline__ long long okey(double x) {
+  const long long i = __double_as_longlong(x);
+  return i ^ ((i >> 63) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ double minmod3(double a, double b, double c) {
+  const long long ka = okey(a), kb = okey(b), kc = okey(c);
+  long long klo = ka, khi = ka;
+  double lo = a, hi = a;
+  if (kb < klo) { klo = kb; lo = b; }
+  if (kb > khi) { khi = kb; hi = b; }
+  if (kc < klo) { klo = kc; lo = c; }
+  if (kc > khi) { khi = kc; hi = c; }
+  return klo > 0 ? lo : (khi < -1 ? hi : 0.0);  // strictly positive / strictly negative
+}
+
+// max(0, a, b), x == 0 and x >= 0 for the wave speeds and the HLLC branch:
+// plain for float and double word, on the integer pipe for double.
+template <class T>
+__device__ __forceinline__ T max0(T a, T b) { return fmax(T(0), fmax(a, b)); }
+__device__ __forceinline__ double max0(double a, double b) {
+  const long long ka = okey(a), kb = okey(b);
+  const double m = ka < kb ? b : a;
+  return (ka < kb ? kb : ka) > 0 ? m : 0.0;
+}
+template <class T>
+__device__ __forceinline__ bool is_zero(T x) { return x == T(0); }
+__device__ __forceinline__ bool is_zero(double x) { return ((unsigned long long)__double_as_longlong(x) << 1) == 0; }
+template <class T>
+__device__ __forceinline__ bool nonneg(T x) { return x >= T(0); }
+__device__ __forceinline__ bool nonneg(double x) { return okey(x) >= -1; }
+
 // Limited slope of cell c from its neighbours (Eq. MinMod; theta is in g).
 template <class T>
 __device__ __forceinline__ T limited_slope(T wm, T wc, T wp, const Geo<T>& g) {
@@ -208,8 +244,8 @@ __device__ __forceinline__ void face_flux(const T (&wl)[NDIM + 2], const T (&wr)
   const T vl = wl[1 + Q], vr = wr[1 + Q];
   const T cl = fsqrt(gamma * fdiv(pl, nl));
   const T cr = fsqrt(gamma * fdiv(pr, nr));
-  const T ap = fmax(T(0), fmax(vl + cl, vr + cr));
-  const T am = fmax(T(0), fmax(cl - vl, cr - vr));
+  const T ap = max0(vl + cl, vr + cr);
+  const T am = max0(cl - vl, cr - vr);
 
   if constexpr (SOLVER == SOLVER_HLL) {
     T ul[NV], ur[NV], fl[NV], fr[NV];
@@ -226,7 +262,7 @@ __device__ __forceinline__ void face_flux(const T (&wl)[NDIM + 2], const T (&wr)
     const T sr = ap - vr;  // =   S_R - v_R  > 0
     const T ml = nl * vl, mr = nr * vr;  // normal momenta
     const T alpha_m = fdiv(mr * sr + ml * sl - (pr - pl), nr * sr + nl * sl);
-    const bool left = am == T(0) || (ap != T(0) && alpha_m >= T(0));
+    const bool left = is_zero(am) || (!is_zero(ap) && nonneg(alpha_m));
     const T SK = left ? -am : ap;
     const T pK = left ? pl : pr;
     T wK[NV];
@@ -236,7 +272,7 @@ __device__ __forceinline__ void face_flux(const T (&wl)[NDIM + 2], const T (&wr)
     T uK[NV], fK[NV];
     side_state<T, NDIM, Q>(wK, pK, uK, fK);
     const T dK = SK - vK;  // S_K - v_K
-    const T rden = SK == T(0) ? T(0) : frcp(SK - alpha_m);
+    const T rden = is_zero(SK) ? T(0) : frcp(SK - alpha_m);
     const T Ds = nK * dK * rden;
     const T ps = pK + nK * dK * (alpha_m - vK);
     T us[NV];
