@@ -293,6 +293,74 @@ def short_horizon(params, seeds=range(64, 72), n_coarse=256, factor=4, t_starts=
     return rows, summary
 
 
+def restart_frontier(params, seeds=range(64, 72), n_coarse=256, t_starts=(0.2, 0.6), spans=(0.05, 0.2), cfl=0.5,
+                     solver=P.HLLC, log=None):
+    """The equal-L1 comparison from restarts: from the 4x run's state at t0,
+    restricted to 1x and 2x, the plain 1x and 2x runs and the learned 1x run
+    (FCT) each advance by `span` with their own CFL steps.  L1(rho) against
+    the 4x run restricted to 1x at t0 + span, and each run's GPU time (the 4x
+    run's own time over the span beside them).  Unlike `evaluate`, the runs do
+    not inherit the coarse scheme's drift from t = 0."""
+    torch = _torch()
+    st = _stream()
+    rows = []
+    for seed in seeds:
+        pf = P.kelvin_helmholtz(4 * n_coarse, seed=seed, solver=solver)
+        fine = H.Hydro.from_problem(pf, precision=H.FP32_MIXED, stream=st.cuda_stream)
+        for t0 in t_starts:
+            fine.evolve(cfl, t0)
+            Uf0 = fine.get_conserved(torch.empty((4,) + fine.shape, dtype=torch.float32, device="cuda"))
+            U1 = _restricted(fine, 4).clone()
+            U2 = _restricted(fine, 2).clone()
+            for span in spans:
+                fine.set_conserved(Uf0)
+                fine.time = t0
+                res = {"seed": int(seed), "t0": t0, "span": span}
+                _, res["time_4x"], _ = _timed(lambda: fine.evolve(cfl, t0 + span), st)
+                truth = _restricted(fine, 4).cpu().numpy()[0]
+                for m, U0 in ((1, U1), (2, U2)):
+                    pm = P.kelvin_helmholtz(m * n_coarse, seed=seed, solver=solver)
+                    h = H.Hydro.from_problem(pm, precision=H.FP32_MIXED, set_state=False, stream=st.cuda_stream)
+                    h.set_conserved(U0)
+                    _, res[f"time_{m}x"], _ = _timed(lambda: h.evolve(cfl, span), st)
+                    res[f"l1_{m}x"] = _l1(_restricted(h, m).cpu().numpy()[0], truth)
+                    h.close()
+                pc = P.kelvin_helmholtz(n_coarse, seed=seed, solver=solver)
+                L = H.Learned(pc, params=params, stream=st.cuda_stream)
+                L.set_fct(True)
+                L.set_conserved(U1)
+                try:
+                    t_got, res["time_learned"], _ = _timed(lambda: L.evolve(cfl, span, max_chunks=400), st)
+                    if t_got < span:
+                        raise H.HydroError(0, f"time step collapsed: t = {t_got:.4g}")
+                    res["l1_learned"] = _l1(L.get_conserved()[0], truth)
+                except H.HydroError as e:
+                    res["l1_learned"], res["time_learned"] = math.inf, math.inf
+                    res["error_learned"] = str(e)
+                L.close()
+                rows.append(res)
+                if log:
+                    log(json.dumps(res))
+        fine.close()
+    summary = []
+    for t0 in t_starts:
+        for span in spans:
+            sel = [r for r in rows if r["t0"] == t0 and r["span"] == span]
+            mean = lambda k: float(np.mean([r[k] for r in sel]))
+            pts = [(mean(f"l1_{m}x"), mean(f"time_{m}x")) for m in (1, 2)]
+            row = {"t0": t0, "span": span, "l1_plain": {"1x": pts[0][0], "2x": pts[1][0]},
+                   "time_plain_s": {"1x": pts[0][1], "2x": pts[1][1]}, "time_4x_s": mean("time_4x")}
+            l1l, tl = mean("l1_learned"), mean("time_learned")
+            if math.isfinite(l1l):
+                tf = frontier_time_at(l1l, pts)
+                row["learned_fct"] = {"l1": l1l, "time_s": tl, "frontier_time_at_l1_s": tf, "below_frontier": tl < tf,
+                                      "error_ratio_vs_plain_1x": l1l / pts[0][0]}
+            else:
+                row["learned_fct"] = {"l1": l1l, "failed_runs": sum(1 for r in sel if not math.isfinite(r["l1_learned"]))}
+            summary.append(row)
+    return rows, summary
+
+
 def frontier_time_at(l1, pts):
     """GPU time the plain frontier needs for error l1: log-log interpolation
     between the plain points (l1_m, time_m), extrapolated from the two nearest."""
@@ -347,10 +415,20 @@ def main(argv=None):
                     help="bound on network outputs (< 0: twice the 99.9th percentile of |target|)")
     ap.add_argument("--no-fct", action="store_true", help="also evaluate without the FCT limiter")
     ap.add_argument("--out", default=None, help="write params (.npy) and results (.json) with this prefix")
+    ap.add_argument("--params", default=None,
+                    help="evaluate these trained parameters (.npy) instead of generating data and training")
     a = ap.parse_args(argv)
     from . import build
     build.build()
     log = lambda m: print(m, flush=True)
+    if a.params:
+        params = np.load(a.params)
+        rs_rows, rs_summ = restart_frontier(params, seeds=range(64, 64 + a.eval_seeds), n_coarse=a.n, log=log)
+        print(json.dumps({"restart_frontier": rs_summ}), flush=True)
+        if a.out:
+            with open(a.out + "_restart.json", "w") as f:
+                json.dump({"per_seed": rs_rows, "summary": rs_summ}, f, indent=1)
+        return
     t0 = time.perf_counter()
     X, T = generate(range(a.train_seeds), n_coarse=a.n, t_end=a.t_end, snap_every=a.snap_every,
                     keep_fraction=a.keep, log=log)
@@ -364,6 +442,8 @@ def main(argv=None):
     log(f"output limit {limit:.4e}")
     sh_rows, sh_summ = short_horizon(params, seeds=range(64, 64 + a.eval_seeds), n_coarse=a.n, log=log)
     print(json.dumps({"short_horizon": sh_summ}), flush=True)
+    rs_rows, rs_summ = restart_frontier(params, seeds=range(64, 64 + a.eval_seeds), n_coarse=a.n, log=log)
+    print(json.dumps({"restart_frontier": rs_summ}), flush=True)
     variants = [("learned_fct", True, math.inf), ("learned_fct_bounded", True, limit)]
     if a.no_fct:
         variants.append(("learned_bounded", False, limit))
@@ -371,7 +451,8 @@ def main(argv=None):
     summ = summarize(rows, [v[0] for v in variants])
     result = {"samples": int(X.shape[0]), "gen_s": t_gen, "train_s": t_train, "loss_history": hist,
               "output_limit": limit, "per_seed": rows, "summary": summ,
-              "short_horizon_per_seed": sh_rows, "short_horizon": sh_summ}
+              "short_horizon_per_seed": sh_rows, "short_horizon": sh_summ,
+              "restart_frontier_per_seed": rs_rows, "restart_frontier": rs_summ}
     print(json.dumps({"summary": summ}), flush=True)
     if a.out:
         np.save(a.out + "_params.npy", params)
