@@ -318,7 +318,21 @@ struct StageKernel {
   // rounds of NT faces go to all threads; the REM faces left over go to the
   // last threads, which load no halo cells, so that no warp does both a halo
   // load and an extra face.
-  static __device__ __forceinline__ void faces(const StageArgs<T>& A, Smem& S, int b, int tid) {
+  static __device__ __forceinline__ void faces(const StageArgs<T>& A, Smem& S, int b, int tid, int tx, int ty) {
+    if constexpr (PRE && HAS_Y && TX % 32 == 0) {
+      // Cell-aligned: thread (tx, ty) takes the lower x face of its cell, then
+      // its lower y face; the TY upper x faces of the last column and the TX
+      // upper y faces of the last row go to the last TX + TY threads.  A warp
+      // lies in one row, so every warp runs one flux routine per round.
+      x_face(A, S, b, tx, ty + 2, ty);
+      y_face(A, S, b, ty, tx + 2);
+      const int j = tid - (NT - (TX + TY));
+      if (j >= 0) {
+        if (j < TY) x_face(A, S, b, TX, j + 2, j);
+        else y_face(A, S, b, TY, j - TY + 2);
+      }
+      return;
+    }
     constexpr int NXF = (TX + 1) * TY;
     constexpr int NYF = HAS_Y ? TX * (TY + 1) : 0;
     constexpr int NF = NXF + NYF, ROUNDS = NF / NT, REM = NF - ROUNDS * NT;
@@ -472,7 +486,7 @@ struct StageKernel {
         face_states(S, buf, tid, tx, ty, wown);
         __syncthreads();
       }
-      faces(A, S, buf, tid);
+      faces(A, S, buf, tid, tx, ty);
       if constexpr (PRE) {
         if (m + 1 < m1) put_plane(A, S, buf ^ 1, m + 1, tid, tx, ty, wk1, fk1, halo, hsx, hsy, dt, vs);
       }
