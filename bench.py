@@ -158,12 +158,8 @@ PEAK_FP64_TFLOPS = 1.25
 # profiles/), scaled to the bench's cell count (traffic grows with the cells).
 # Other configurations report no traffic.
 TRAFFIC_PER_CELL_FP32_HLLC = {
-    (0, 48): {"stage1": (148.528128e6 + 104.334592e6) / 192 ** 3,
-              "stage2": (297.726720e6 + 119.101952e6) / 192 ** 3},
-    (7, 24): {"stage1": (159.187200e6 + 111.706880e6) / 192 ** 3,
-              "stage2": (324.736000e6 + 122.215680e6) / 192 ** 3},
-    (8, 40): {"stage1": (151.107840e6 + 104.604672e6) / 192 ** 3,
-              "stage2": (307.858944e6 + 120.326656e6) / 192 ** 3},
+    (8, 40): {"stage1": (151.177984e6 + 104.669696e6) / 192 ** 3,
+              "stage2": (307.413248e6 + 119.982848e6) / 192 ** 3},
 }
 
 
