@@ -26,6 +26,8 @@
 // Boundary conditions are applied by index mapping on load (bc_map).
 #pragma once
 
+#include <type_traits>
+
 #include "hydro_device.cuh"
 
 namespace gh {
@@ -319,11 +321,13 @@ struct StageKernel {
   // last threads, which load no halo cells, so that no warp does both a halo
   // load and an extra face.
   static __device__ __forceinline__ void faces(const StageArgs<T>& A, Smem& S, int b, int tid, int tx, int ty) {
-    if constexpr (PRE && HAS_Y && TX % 32 == 0) {
+    if constexpr (PRE && HAS_Y && TX % 32 == 0 && !std::is_same<T, dw>::value) {
       // Cell-aligned: thread (tx, ty) takes the lower x face of its cell, then
       // its lower y face; the TY upper x faces of the last column and the TX
       // upper y faces of the last row go to the last TX + TY threads.  A warp
-      // lies in one row, so every warp runs one flux routine per round.
+      // lies in one row, so every warp runs one flux routine per round.  (The
+      // double-word flux is large enough that its four inlined copies cost
+      // more than the straddling warp saves: it keeps the numbered loop.)
       x_face(A, S, b, tx, ty + 2, ty);
       y_face(A, S, b, ty, tx + 2);
       const int j = tid - (NT - (TX + TY));
