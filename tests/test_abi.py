@@ -80,7 +80,32 @@ def test_invalid_descriptors_rejected_on_host(lib):
 
 
 def test_null_handle_calls_fail_cleanly(lib):
+    """Every call on a NULL handle returns GENASIS_EINVAL before touching a
+    device (destroy accepts NULL); the calls run here without a GPU."""
+    import ctypes
     from paper_1207_3392_gb300 import hydro as H
     L = H.load()
-    assert L.genasis_hydro_step(None, 0.1) == H.EINVAL
-    assert L.genasis_hydro_destroy(None) == H.OK
+    d = ctypes.c_double()
+    buf = (ctypes.c_double * 16)()
+    fbuf = (ctypes.c_float * 16)()
+    ibuf = (ctypes.c_int * 8)()
+    calls = {
+        "genasis_hydro_step": (0.1,), "genasis_hydro_sync": (), "genasis_hydro_status": (),
+        "genasis_hydro_clear_status": (), "genasis_hydro_compute_dt": (0.5, ctypes.byref(d)),
+        "genasis_hydro_advance": (1, 0.5, 0.0, None), "genasis_hydro_get_time": (ctypes.byref(d),),
+        "genasis_hydro_set_time": (0.0,), "genasis_hydro_get_totals": (buf,),
+        "genasis_hydro_set_tile": (0, 0), "genasis_hydro_get_tile": (ibuf,),
+        "genasis_hydro_autotune": (1, None), "genasis_hydro_set_potential_gradient": (buf,),
+        "genasis_hydro_get_step_totals": (buf,), "genasis_hydro_profile_step": (0.5, fbuf),
+        "genasis_hydro_get_conserved": (buf, H.FP64), "genasis_hydro_set_conserved": (buf, H.FP64),
+        "genasis_learned_step": (0.1,), "genasis_learned_set_fct": (1,), "genasis_learned_get_conserved": (fbuf,),
+        "genasis_learned_advance": (1, 0.5, 0.0, None),
+        "genasis_batch_run": (1, 0.5, 0.0), "genasis_batch_get_times": (buf,), "genasis_batch_get_tile": (ibuf,),
+        "genasis_batch_set_tile": (0, 32), "genasis_batch_autotune": (1, None),
+        "genasis_fmr_step": (1, 0.3, None), "genasis_fmr_autotune": (1,), "genasis_fmr_get_level": (0, buf),
+        "genasis_fmr_set_level": (0, buf),
+    }
+    for name, args in calls.items():
+        assert getattr(L, name)(None, *args) == H.EINVAL, name
+    for name in ("genasis_hydro_destroy", "genasis_learned_destroy", "genasis_batch_destroy", "genasis_fmr_destroy"):
+        assert getattr(L, name)(None) == H.OK, name
