@@ -24,7 +24,7 @@
  *   external-force source         the source vector of the Rayleigh-Taylor test (Sec. 4.3.2),
  *                                 potential at cell centres, gradient by centred differences
  *
- * Readings where the paper is garbled or silent (each also listed in the design doc):
+ * Readings where the paper is garbled or silent:
  *   - Eq. PressureMiddle as printed violates p*_L = p*_R (stated right after
  *     Eq. EnergyMiddle).  Re-deriving it from the normal-momentum jump condition
  *     Eq. JumpConditionHLLCMinus/Plus gives
