@@ -165,7 +165,7 @@ __global__ void fmr_speed_kernel(const T* __restrict__ U, LevelGeo g, double gam
     T u[NV], w[NV];
     for (int v = 0; v < NV; ++v) u[v] = U[v * vs + c];
     recover<NDIM>(u, w);
-    const T cs = fsqrt((T)gamma * fdiv((T)(gamma - 1.0) * w[NV - 1], w[0]));
+    const T cs = sound_speed((T)gamma, (T)(gamma - 1.0) * w[NV - 1], w[0]);
     for (int q = 0; q < NDIM; ++q) best = fmax(best, fabs(w[1 + q]) + cs);
   }
   const double bw = warp_max((double)best);

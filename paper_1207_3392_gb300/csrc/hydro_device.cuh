@@ -127,6 +127,16 @@ __device__ __forceinline__ dw frcp(dw x) { return dw(1.0f, 0.0f) / x; }
 __device__ __forceinline__ dw fsqrt(dw x) { return sqrt(x); }
 __device__ __forceinline__ dw add_rn(dw a, dw b) { return a + b; }
 
+// Sound speed c = sqrt(gamma p / n) (Sec. 3.5).  FP64: gamma p rsqrt(gamma p n),
+// one reciprocal square root (CUDA's rsqrt, 1 ulp) in place of an IEEE division
+// and an IEEE square root on the slow FP64 pipe; 0 where gamma p is not positive.
+template <class T>
+__device__ __forceinline__ T sound_speed(T gamma, T p, T n) { return fsqrt(gamma * fdiv(p, n)); }
+__device__ __forceinline__ double sound_speed(double gamma, double p, double n) {
+  const double gp = gamma * p;
+  return okey(gp) > 0 ? gp * rsqrt(gp * n) : 0.0;
+}
+
 // ---------------------------------------------------------------------------
 // Conserved -> primitive recovery.
 //
@@ -242,8 +252,8 @@ __device__ __forceinline__ void face_flux(const T (&wl)[NDIM + 2], const T (&wr)
   const T nl = wl[0], nr = wr[0];
   const T pl = gm1 * wl[NV - 1], pr = gm1 * wr[NV - 1];
   const T vl = wl[1 + Q], vr = wr[1 + Q];
-  const T cl = fsqrt(gamma * fdiv(pl, nl));
-  const T cr = fsqrt(gamma * fdiv(pr, nr));
+  const T cl = sound_speed(gamma, pl, nl);
+  const T cr = sound_speed(gamma, pr, nr);
   const T ap = max0(vl + cl, vr + cr);
   const T am = max0(cl - vl, cr - vr);
 

@@ -523,7 +523,7 @@ struct StageKernel {
 #pragma unroll
           for (int v = 0; v < NV; ++v) A.out[v * vs + c] = L[v];
           // CFL speed (Eq. courantTimeStep) on U^n at the cell centre
-          const T cs = fsqrt(A.gamma * fdiv(A.gm1 * wown[NV - 1], wown[0]));
+          const T cs = sound_speed(A.gamma, A.gm1 * wown[NV - 1], wown[0]);
           T s = (fabs(wown[1]) + cs) * iwx;
           if constexpr (HAS_Y) s = fmax(s, (fabs(wown[2]) + cs) * iwy);
           if constexpr (MARCH) s = fmax(s, (fabs(wown[1 + AM]) + cs) * iwm);
