@@ -129,9 +129,16 @@ __device__ __forceinline__ dw add_rn(dw a, dw b) { return a + b; }
 
 // Sound speed c = sqrt(gamma p / n) (Sec. 3.5).  FP64: gamma p rsqrt(gamma p n),
 // one reciprocal square root (CUDA's rsqrt, 1 ulp) in place of an IEEE division
-// and an IEEE square root on the slow FP64 pipe; 0 where gamma p is not positive.
+// and an IEEE square root on the slow FP64 pipe; 0 where gamma p is not
+// positive.  FP32: the same form with the hardware approximation (one
+// multi-function-unit operation instead of two).  Double word: the quotient
+// and square root of dword.cuh.
 template <class T>
 __device__ __forceinline__ T sound_speed(T gamma, T p, T n) { return fsqrt(gamma * fdiv(p, n)); }
+__device__ __forceinline__ float sound_speed(float gamma, float p, float n) {
+  const float gp = gamma * p;
+  return gp * rsqrtf(gp * n);
+}
 __device__ __forceinline__ double sound_speed(double gamma, double p, double n) {
   const double gp = gamma * p;
   return okey(gp) > 0 ? gp * rsqrt(gp * n) : 0.0;
