@@ -158,8 +158,8 @@ PEAK_FP64_TFLOPS = 1.25
 # profiles/), scaled to the bench's cell count (traffic grows with the cells).
 # Other configurations report no traffic.
 TRAFFIC_PER_CELL_FP32_HLLC = {
-    (8, 40): {"stage1": (151.177984e6 + 104.669696e6) / 192 ** 3,
-              "stage2": (307.413248e6 + 119.982848e6) / 192 ** 3},
+    (8, 40): {"stage1": (150.860544e6 + 104.290304e6) / 192 ** 3,
+              "stage2": (306.705920e6 + 120.133632e6) / 192 ** 3},
 }
 
 
