@@ -129,8 +129,13 @@ struct BatchKernel {
   }
 };
 
+// FP32: 64 registers, so that 2,048 threads (8 CTAs of 128) stay resident;
+// the FP64 and double-word bodies would spill at that limit.
+template <class T, int TX>
+constexpr int batch_min_blocks() { return std::is_same<T, float>::value ? 1024 / TX : 1; }
+
 template <class T, int SOLVER, int STAGE, int TX>
-__global__ void __launch_bounds__(TX) hydro_batch_kernel(const BatchArgs<T> B) {
+__global__ void __launch_bounds__(TX, (batch_min_blocks<T, TX>())) hydro_batch_kernel(const BatchArgs<T> B) {
   BatchKernel<T, SOLVER, STAGE, TX>::run(B);
 }
 

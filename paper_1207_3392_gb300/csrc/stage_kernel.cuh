@@ -80,6 +80,12 @@ struct StageKernel {
   // PRE double-buffers the shared plane: the next plane is loaded while the
   // faces of this one are computed.
   static constexpr int NB = PRE ? 2 : 1;
+  // 1D/2D tiles are one row of many warps: in the partial last tile of a
+  // small problem whole warps lie past the domain.  Their columns, beyond the
+  // two ghost cells the last cell's slopes read, skip the loads, slopes and
+  // march-axis faces, and x faces past the last cell are skipped, so that such
+  // warps only take the barriers.  (Nothing skipped is ever read.)
+  static constexpr bool SKIP = !HAS_Y;
 
   struct Smem {
     Geo<T> gx[TX + 4];                 // geometry of cells a0 - 2 .. a0 + TX + 1
@@ -320,7 +326,8 @@ struct StageKernel {
   // rounds of NT faces go to all threads; the REM faces left over go to the
   // last threads, which load no halo cells, so that no warp does both a halo
   // load and an extra face.
-  static __device__ __forceinline__ void faces(const StageArgs<T>& A, Smem& S, int b, int tid, int tx, int ty) {
+  static __device__ __forceinline__ void faces(const StageArgs<T>& A, Smem& S, int b, int tid, int tx, int ty,
+                                               int xlast) {
     if constexpr (PRE && HAS_Y && TX % 32 == 0 && !std::is_same<T, dw>::value) {
       // Cell-aligned: thread (tx, ty) takes the lower x face of its cell, then
       // its lower y face; the TY upper x faces of the last column and the TX
@@ -349,6 +356,7 @@ struct StageKernel {
       if (f < NXF) {
         const int row = f / (TX + 1);
         const int face = f - row * (TX + 1);
+        if (SKIP && face > xlast) continue;
         x_face(A, S, b, face, HAS_Y ? row + 2 : 0, row);
       } else {
         if constexpr (HAS_Y) {
@@ -384,6 +392,7 @@ struct StageKernel {
     const int b0 = HAS_Y ? by * TY : 0;
     const int ca = a0 + tx, cb = b0 + ty;
     const bool own_valid = ca < nx && cb < ny;
+    const bool live = !SKIP || ca < nx + 2;
     const int m0 = MARCH ? bz * A.kchunk : 0;
     const int m1 = MARCH ? min(nm, m0 + A.kchunk) : 1;
     const T dt = STAGE == 2 ? (T)(*A.dt) : T(0);
@@ -439,8 +448,13 @@ struct StageKernel {
     }
     int mstart = m0;
     if constexpr (MARCH) {
-      load_col(A, own, m0 - 2, dt, vs, wk, fk);
-      load_col(A, own, m0 - 1, dt, vs, wk1, fk1);
+      if (live) {
+        load_col(A, own, m0 - 2, dt, vs, wk, fk);
+        load_col(A, own, m0 - 1, dt, vs, wk1, fk1);
+      } else {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) wk[v] = wk1[v] = T(0);
+      }
       mstart = m0 - 2;
     }
 
@@ -449,15 +463,20 @@ struct StageKernel {
       T wown[NV];
       unsigned char fk2 = 0, fown = 0;
       if constexpr (MARCH) {
-        load_col(A, own, m + 2, dt, vs, wk2, fk2);
-        const Geo<T> g0 = geo(A, AM, m), g1 = geo(A, AM, m + 1);
-        slopes(A, wk, wk1, wk2, g1, sk1);
-        // the face m0 - 3/2 of the first warm-up plane is never used
-        if (m > m0 - 2) {
-          m_face(A, wk, sk, g0.h, wk1, sk1, g1.h, (unsigned)(fk | fk1), fhi);
+        if (live) {
+          load_col(A, own, m + 2, dt, vs, wk2, fk2);
+          const Geo<T> g0 = geo(A, AM, m), g1 = geo(A, AM, m + 1);
+          slopes(A, wk, wk1, wk2, g1, sk1);
+          // the face m0 - 3/2 of the first warm-up plane is never used
+          if (m > m0 - 2) {
+            m_face(A, wk, sk, g0.h, wk1, sk1, g1.h, (unsigned)(fk | fk1), fhi);
+          } else {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) fhi[v] = T(0);
+          }
         } else {
 #pragma unroll
-          for (int v = 0; v < NV; ++v) fhi[v] = T(0);
+          for (int v = 0; v < NV; ++v) wk2[v] = sk1[v] = fhi[v] = T(0);
         }
         if (m < m0) {  // warm-up planes: advance the ring only
 #pragma unroll
@@ -474,8 +493,11 @@ struct StageKernel {
 #pragma unroll
         for (int v = 0; v < NV; ++v) wown[v] = wk[v];
         fown = fk;
-      } else {
+      } else if (live) {
         load_col(A, own, 0, dt, vs, wown, fown);
+      } else {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) wown[v] = T(0);
       }
       // Without PRE: plane m into the shared plane; barrier; faces; barrier.
       // With PRE the plane was put into buffer `buf` during the faces of the
@@ -490,7 +512,7 @@ struct StageKernel {
         face_states(S, buf, tid, tx, ty, wown);
         __syncthreads();
       }
-      faces(A, S, buf, tid, tx, ty);
+      faces(A, S, buf, tid, tx, ty, nx - a0);
       if constexpr (PRE) {
         if (m + 1 < m1) put_plane(A, S, buf ^ 1, m + 1, tid, tx, ty, wk1, fk1, halo, hsx, hsy, dt, vs);
       }
