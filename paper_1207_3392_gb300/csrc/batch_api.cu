@@ -138,7 +138,7 @@ int configure(genasis_batch* b, int tile, int chunk) {
       : b->prec == GENASIS_FP32_MIXED ? batch_variant_f32(b->solver, 1, tile, &v1) && batch_variant_f32(b->solver, 2, tile, &v2)
                                       : batch_variant_dw(b->solver, 1, tile, &v1) && batch_variant_dw(b->solver, 2, tile, &v2);
   if (!ok) return fail(GENASIS_EINVAL, "no compiled batch kernel for this configuration");
-  const int tx = v1.tx;
+  const int cols = v1.cols;
   if (chunk == 0) chunk = 32;
   // work items: (problem, x tile, y chunk), largest first
   struct Item {
@@ -148,11 +148,11 @@ int configure(genasis_batch* b, int tile, int chunk) {
   std::vector<Item> items;
   for (int p = 0; p < b->nprob; ++p) {
     const HostProblem& h = b->hp[p];
-    const int gx = (h.n[0] + tx - 1) / tx;
+    const int gx = (h.n[0] + cols - 1) / cols;
     const int gz = h.ndim == 2 ? (h.n[1] + chunk - 1) / chunk : 1;
     for (int x = 0; x < gx; ++x)
       for (int z = 0; z < gz; ++z) {
-        const long w = std::min(tx, h.n[0] - x * tx);
+        const long w = std::min(cols, h.n[0] - x * cols);
         const long rows = h.ndim == 2 ? std::min(chunk, h.n[1] - z * chunk) + 4 : 1;
         items.push_back({w * rows, {p, x, z, 0}});
       }
@@ -168,8 +168,8 @@ int configure(genasis_batch* b, int tile, int chunk) {
   int occ1 = 0, occ2 = 0;
   for (BatchVariant* v : {&v1, &v2})
     if (v->smem > 48 * 1024) GH_CK(cudaFuncSetAttribute(v->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v->smem));
-  GH_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, v1.fn, tx, v1.smem));
-  GH_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, v2.fn, tx, v2.smem));
+  GH_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, v1.fn, v1.tx, v1.smem));
+  GH_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, v2.fn, v2.tx, v2.smem));
   int occ = std::max(1, std::min(occ1, occ2));
   b->ctas = std::min(b->nitems, occ * b->num_sms);
   if (b->ctas < 1) b->ctas = 1;

@@ -9,6 +9,7 @@ static void fill(BatchVariant* out) {
   out->fn = reinterpret_cast<const void*>(&hydro_batch_kernel<float, SOLVER, STAGE, TX>);
   out->smem = BatchKernel<float, SOLVER, STAGE, TX>::SMEM;
   out->tx = TX;
+  out->cols = BatchKernel<float, SOLVER, STAGE, TX>::K2::OWN;
 }
 
 template <int TX>

@@ -47,6 +47,7 @@ template <class T, int SOLVER, int STAGE, int TX>
 struct BatchKernel {
   using K1 = StageKernel<1, T, SOLVER, STAGE, TX, 1>;
   using K2 = StageKernel<2, T, SOLVER, STAGE, TX, 1>;
+  static_assert(K1::OWN == K2::OWN, "1D and 2D items share the x tiling");
   static constexpr size_t SMEM = sizeof(typename K1::Smem) > sizeof(typename K2::Smem) ? sizeof(typename K1::Smem)
                                                                                           : sizeof(typename K2::Smem);
 

@@ -8,7 +8,8 @@ namespace gh {
 struct BatchVariant {
   const void* fn;
   size_t smem;
-  int tx;
+  int tx;    // threads per CTA (one tile row)
+  int cols;  // columns of cells a tile owns (tx - 1)
 };
 
 int batch_tile_count();

@@ -13,7 +13,7 @@ inline void fill_variant(StageVariant* out) {
   using K = StageKernel<NDIM, T, SOLVER, STAGE, TX, TY, PRE>;
   out->fn = reinterpret_cast<const void*>(&hydro_stage_kernel<NDIM, T, SOLVER, STAGE, TX, TY, MINB, PRE>);
   out->smem = sizeof(typename K::Smem);
-  out->tx = TX;
+  out->tx = K::OWN;  // columns of cells per tile (TX - 1 in 1D/2D)
   out->ty = TY;
   out->threads = TX * TY;
 }

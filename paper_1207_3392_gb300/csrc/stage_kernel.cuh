@@ -86,6 +86,13 @@ struct StageKernel {
   // march-axis faces, and x faces past the last cell are skipped, so that such
   // warps only take the barriers.  (Nothing skipped is ever read.)
   static constexpr bool SKIP = !HAS_Y;
+  // Columns of cells a tile owns.  A 1D/2D tile is one row of TX threads; it
+  // would have TX + 1 x faces, and one warp would run a second flux round for
+  // a single face every plane.  Owning TX - 1 cells instead (the last
+  // thread's cell is the next tile's first, loaded only as a neighbour) gives
+  // exactly TX faces, one per thread.
+  static constexpr int OWN = HAS_Y ? TX : TX - 1;
+  static constexpr int NXR = OWN + 1;  // x faces per tile row
 
   struct Smem {
     Geo<T> gx[TX + 4];                 // geometry of cells a0 - 2 .. a0 + TX + 1
@@ -344,7 +351,7 @@ struct StageKernel {
       }
       return;
     }
-    constexpr int NXF = (TX + 1) * TY;
+    constexpr int NXF = NXR * TY;
     constexpr int NYF = HAS_Y ? TX * (TY + 1) : 0;
     constexpr int NF = NXF + NYF, ROUNDS = NF / NT, REM = NF - ROUNDS * NT;
     for (int k = 0; k <= ROUNDS; ++k) {
@@ -354,8 +361,8 @@ struct StageKernel {
         f = ROUNDS * NT + (tid - (NT - REM));
       }
       if (f < NXF) {
-        const int row = f / (TX + 1);
-        const int face = f - row * (TX + 1);
+        const int row = f / NXR;
+        const int face = f - row * NXR;
         if (SKIP && face > xlast) continue;
         x_face(A, S, b, face, HAS_Y ? row + 2 : 0, row);
       } else {
@@ -388,10 +395,10 @@ struct StageKernel {
     const int ny = HAS_Y ? A.n[1] : 1;
     const int nm = MARCH ? A.n[AM] : 1;
     const size_t vs = (size_t)A.n[0] * A.n[1] * A.n[2];
-    const int a0 = bx * TX;
+    const int a0 = bx * OWN;
     const int b0 = HAS_Y ? by * TY : 0;
     const int ca = a0 + tx, cb = b0 + ty;
-    const bool own_valid = ca < nx && cb < ny;
+    const bool own_valid = ca < nx && cb < ny && (HAS_Y || tx < OWN);
     const bool live = !SKIP || ca < nx + 2;
     const int m0 = MARCH ? bz * A.kchunk : 0;
     const int m1 = MARCH ? min(nm, m0 + A.kchunk) : 1;
