@@ -167,7 +167,10 @@ int genasis_hydro_clear_status(genasis_hydro_t h);
 
 /* Launch configuration: tile index (0 .. tile_count - 1 for this ndim) and
  * planes per CTA along the march axis (0 = automatic).  info[0..5] receives
- * (tile index, tile x, tile y, planes per CTA, CTAs per stage, tile count). */
+ * (tile index, tile x, tile y, planes per CTA, CTAs per stage, tile count).
+ * Tile x and y count the cells a CTA owns: in 1D/2D a CTA of n threads owns
+ * n - 1 columns (its last thread loads the next tile's first cell as a
+ * neighbour only). */
 int genasis_hydro_set_tile(genasis_hydro_t h, int tile, int kchunk);
 int genasis_hydro_get_tile(genasis_hydro_t h, int *info);
 

@@ -8,8 +8,9 @@
 // so that the CFL reduction (Eq. courantTimeStep) and the conserved totals can
 // be taken from the primitive recovery stage 1 already does on U^n.
 //
-// Tiling: a CTA owns a TX x TY tile of the "plane" axes and marches along the
-// last axis (z in 3D, y in 2D; 1D has one plane).  Per plane it
+// Tiling: a CTA owns a TX x TY tile of the "plane" axes (1D/2D: one row of
+// TX - 1 cells, see OWN) and marches along the last axis (z in 3D, y in 2D;
+// 1D has one plane).  Per plane it
 //   1. loads + recovers the plane two ahead for its own columns (register ring
 //      of W along the march axis; limited slopes and the march-axis face flux
 //      are computed once per cell per stage),
