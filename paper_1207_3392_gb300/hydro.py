@@ -13,8 +13,6 @@ import os
 
 import numpy as np
 
-from . import problems as _problems
-
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_lib", "libgenasis_hydro.so")
 
