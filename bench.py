@@ -163,9 +163,42 @@ TRAFFIC_PER_CELL_FP32_HLLC = {
 }
 
 
+def _sample_parity(pr, U_ref, steps):
+    """The GPU path on the cpu_baseline sample: the same problem for the same
+    number of device-CFL RK2 steps in both precisions, against the oracle's
+    result U_ref.  Relative L1 per conserved variable (Eq. L1ErrorNorm; the
+    momenta against the L1 norm of the whole momentum field) and relative
+    L-infinity over all variables.  Errors are reported, never raised."""
+    import numpy as np
+    from paper_1207_3392_gb300 import hydro as H
+    out = {"sample_steps": steps}
+    try:
+        ref = np.asarray(U_ref, dtype=np.float64)
+        nd = pr.ndim
+        mom = float(np.sum(np.abs(ref[1:1 + nd])))
+        for name, prec in (("fp32_mixed", H.FP32_MIXED), ("fp64", H.FP64)):
+            h = H.Hydro.from_problem(pr, precision=prec)
+            try:
+                h.advance(steps, pr.cfl)
+                Ug = h.get_conserved(precision=H.FP64)
+            finally:
+                h.close()
+            l1 = []
+            for v in range(nd + 2):
+                den = mom if 1 <= v <= nd else float(np.sum(np.abs(ref[v])))
+                l1.append(float(np.sum(np.abs(Ug[v] - ref[v])) / den))
+            linf = float(np.max(np.abs(Ug - ref)) / np.max(np.abs(ref)))
+            out[name] = {"rel_l1": l1, "linf_rel": linf}
+            del Ug
+    except Exception as e:  # report, do not fail the bench
+        out["error"] = str(e)[:200]
+    return out
+
+
 def cpu_baseline(n_sample=256, steps=3):
     """The oracle, as it stands, on a bounded sample of the workload: the same
-    point blast at n_sample^3 for `steps` RK2 steps, all host cores."""
+    point blast at n_sample^3 for `steps` RK2 steps, all host cores.  The
+    oracle's result on that sample is also the reference of `parity`."""
     import oracle as O
     from paper_1207_3392_gb300 import problems as P
     cores = os.cpu_count() or 1
@@ -179,6 +212,8 @@ def cpu_baseline(n_sample=256, steps=3):
     out = {"value": pr.ncells * 2 * done / dt, "unit": UNIT, "cores": int(os.environ["OMP_NUM_THREADS"]),
            "kind": "oracle",
            "sample": f"FP64 oracle, same point blast at {n_sample}^3 for {done} RK2 steps ({dt:.1f} s)"}
+    out["parity"] = _sample_parity(pr, U, done)
+    del U
     # one host core: a smaller sample of the same blast, in a child process so
     # that the OpenMP runtime starts with one thread
     code = ("import json, time, oracle as O; from paper_1207_3392_gb300 import problems as P; "
