@@ -2,6 +2,9 @@
 library and through the oracle, and compare them element by element."""
 from __future__ import annotations
 
+import json
+import os
+
 import numpy as np
 
 import oracle as O
@@ -10,6 +13,13 @@ from paper_1207_3392_gb300 import hydro as H
 # Tolerances (relative L1 per conserved variable against the FP64 oracle).
 TOL_FP64 = 1e-10
 TOL_FP32 = 1e-5
+# L-infinity bars (largest cell difference over the largest magnitude of the
+# variable): ten times the L1 bar.  Rounding differences spread over the whole
+# field keep L-infinity near L1 (a relative rounding error is at most a few
+# units in the last place in any cell); one wrong cell, as a halo or tile-seam
+# fault makes, shows as an O(1e-2 .. 1) L-infinity while moving L1 by only
+# its share of the cells, so it fails this bar at any mesh size.
+LINF_FACTOR = 10.0
 
 
 def rel_l1(gpu, ref, ndim):
@@ -28,6 +38,44 @@ def rel_l1(gpu, ref, ndim):
             den = dens
         out[v] = np.sum(np.abs(gpu[v] - ref[v])) / den
     return out
+
+
+def linf_rel_per_var(gpu, ref, ndim):
+    """Largest cell difference per conserved variable over the largest
+    magnitude of that variable (momenta: over the whole momentum field)."""
+    gpu = np.asarray(gpu, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    nv = ndim + 2
+    out = np.zeros(nv)
+    mom = np.max(np.abs(ref[1:1 + ndim])) if ndim > 0 else 0.0
+    dens = np.max(np.abs(ref[0]))
+    for v in range(nv):
+        den = mom if 1 <= v <= ndim else np.max(np.abs(ref[v]))
+        if den == 0.0:
+            den = dens
+        out[v] = np.max(np.abs(gpu[v] - ref[v])) / den
+    return out
+
+
+def check(gpu, ref, ndim, tol, what="", tol_linf=None):
+    """Assert the relative L1 bar and the L-infinity bar per conserved variable.
+    tol and tol_linf are scalars or per-variable arrays; tol_linf defaults to
+    LINF_FACTOR x tol.  With PARITY_LOG set, every comparison is appended to
+    that file as one JSON line (test, what, L1, L-infinity, bars)."""
+    e = rel_l1(gpu, ref, ndim)
+    li = linf_rel_per_var(gpu, ref, ndim)
+    tol = np.broadcast_to(np.asarray(tol, dtype=np.float64), e.shape)
+    tol_linf = LINF_FACTOR * tol if tol_linf is None else np.broadcast_to(np.asarray(tol_linf, dtype=np.float64),
+                                                                          e.shape)
+    log = os.environ.get("PARITY_LOG")
+    if log:
+        with open(log, "a") as f:
+            f.write(json.dumps({"test": os.environ.get("PYTEST_CURRENT_TEST", ""), "what": what,
+                                "l1": e.tolist(), "linf": li.tolist(), "tol": tol.tolist(),
+                                "tol_linf": tol_linf.tolist()}) + "\n")
+    assert np.all(e <= tol), f"{what}: rel L1 {e} above {tol}; rel Linf {li}"
+    assert np.all(li <= tol_linf), f"{what}: rel Linf {li} above {tol_linf}; rel L1 {e}"
+    return e, li
 
 
 def linf_rel(gpu, ref):

@@ -6,7 +6,7 @@ import pytest
 
 from oracle import fmr as F
 from paper_1207_3392_gb300 import hydro as H
-from parity_util import TOL_FP32, TOL_FP64, rel_l1
+from parity_util import TOL_FP32, TOL_FP64, check
 
 pytestmark = pytest.mark.gpu
 
@@ -40,8 +40,7 @@ def test_fmr_matches_reference(nd, N, L, steps, precision, tol):
     for l in range(L):
         a = out[l][M.interior(l)]
         b = M.U[l][M.interior(l)]
-        e = rel_l1(a, b, nd)
-        assert np.all(e <= tol), (l, e)
+        check(a, b, nd, tol, f"level {l}")
 
 
 def test_fmr_graph_replay_equals_stepwise():
