@@ -76,7 +76,10 @@ __global__ void noalloc_geometry_kernel(int n, int lo, int hi, double theta, con
 }
 
 // First call on a device: look up the device address of the scratch array
-// with that device current.
+// with that device current.  The address is cached for the life of the
+// process; a cudaDeviceReset of that device unloads the module and leaves the
+// cached address stale, so the entry point must not be used on a device after
+// a reset in the same process.
 static int scratch_for_current_device(unsigned char** out) {
   int dev = 0;
   GH_CK(cudaGetDevice(&dev));
@@ -212,6 +215,14 @@ using namespace gh;
 
 extern "C" int genasis_hydro_step_noalloc(const genasis_hydro_desc* d, const void* U_in, void* U_out, double dt) {
   if (!d || !U_in || !U_out) return fail(GENASIS_EINVAL, "step_noalloc: NULL argument");
+  {
+    // the step copies the widths from pageable memory and synchronises the
+    // stream, neither of which a capturing stream allows
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    GH_CK(cudaStreamIsCapturing((cudaStream_t)d->stream, &cap));
+    if (cap != cudaStreamCaptureStatusNone)
+      return fail(GENASIS_EINVAL, "step_noalloc: the stream is capturing; this call synchronises and cannot be captured");
+  }
   if (d->ndim < 1 || d->ndim > 3) return fail(GENASIS_EINVAL, "step_noalloc: ndim must be 1, 2 or 3");
   if (d->precision != GENASIS_FP64 && d->precision != GENASIS_FP32_MIXED)
     return fail(GENASIS_EINVAL, "step_noalloc: bad precision");
@@ -241,10 +252,10 @@ extern "C" int genasis_hydro_step_noalloc(const genasis_hydro_desc* d, const voi
   const char* a = (const char*)U_in;
   const char* b = (const char*)U_out;
   if (a < b + bytes && b < a + bytes) return fail(GENASIS_EINVAL, "step_noalloc: U_in and U_out overlap");
+  cudaStream_t st = (cudaStream_t)d->stream;
   unsigned char* base = nullptr;
   int rc = scratch_for_current_device(&base);
   if (rc) return rc;
-  cudaStream_t st = (cudaStream_t)d->stream;
   return d->precision == GENASIS_FP64 ? noalloc_step_t<double>(d, base, (const double*)U_in, (double*)U_out, dt, st)
                                       : noalloc_step_t<float>(d, base, (const float*)U_in, (float*)U_out, dt, st);
 }
