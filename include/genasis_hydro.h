@@ -83,6 +83,10 @@ typedef struct genasis_hydro *genasis_hydro_t;
  *   ndim        1, 2 or 3
  *   n[q]        cells along axis q (>= 2 on active axes; ignored beyond ndim)
  *   widths[q]   host pointer to n[q] strictly positive cell widths along q
+ *   origin[q]   coordinate of the low face of cell 0 along q; the update does
+ *               not depend on it (Eq. BalanceEquationAverage needs only the
+ *               widths); genasis_hydro_get_centers returns the cell centres
+ *               measured from it
  *   bc_lo/hi[q] GENASIS_BC_* at the low / high end of axis q (periodic must be
  *               set on both ends)
  *   gamma       adiabatic index of p = (gamma - 1) e (> 1)
@@ -94,6 +98,7 @@ typedef struct {
   int ndim;
   int n[3];
   const double *widths[3];
+  double origin[3];
   int bc_lo[3];
   int bc_hi[3];
   double gamma;
@@ -210,6 +215,67 @@ int genasis_hydro_profile_step(genasis_hydro_t h, double cfl, float *ms);
 /* Text of the last error of the calling thread (never NULL). */
 const char *genasis_hydro_last_error(void);
 
+/* Geometric cell centres along axis q (0 .. ndim - 1) of a single-mesh
+ * handle: x[i] = origin[q] + sum_{j < i} widths[q][j] + widths[q][i] / 2
+ * (Sec. 3.1: the reconstruction is about the geometric centre), n[q] doubles
+ * into host memory. */
+int genasis_hydro_get_centers(genasis_hydro_t h, int axis, double *x);
+
+/* Vector FMA throughput of the current GPU in TFLOP/s (2 operations per
+ * FMA), measured with independent FMA chains on every SM under CUDA events:
+ * kind 0 FP64, 1 FP32, 2 FP32 with the packed two-lane FMA of sm_100+.  The
+ * paper has no counterpart: it is the measured denominator of the arithmetic
+ * roofline that the update's kernels are reported against.  Allocates and
+ * frees a small buffer, uses a private stream, takes ~0.5 s; synchronises. */
+int genasis_measure_fma_rate(int kind, double *tflops);
+
+/* ---------------------------------------------------------------------------
+ * The batched and learned workloads behind genasis_hydro_t.
+ *
+ * genasis_hydro_batch_create makes one handle for nprob independent 1D or 2D
+ * problems, each described by its own genasis_hydro_desc (ndim 1 or 2, n,
+ * widths, boundaries, gamma); solver, theta, precision and stream must be the
+ * same in every desc (EINVAL otherwise).  Each problem follows the update of
+ * a single-mesh handle (Secs. 3.1-3.6) with its own CFL time step; the whole
+ * set runs as one persistent kernel launch per RK stage, nsteps steps as one
+ * CUDA graph (the genasis_batch_* calls below are the same engine).  A batch
+ * handle takes only the genasis_hydro_batch_* calls, genasis_hydro_status
+ * (returns ENONPHYS if any problem met a non-physical state) and
+ * genasis_hydro_destroy; the single-mesh calls return EINVAL for it.
+ * ------------------------------------------------------------------------- */
+int genasis_hydro_batch_create(int nprob, const genasis_hydro_desc *descs, genasis_hydro_t *out);
+/* Initial state of problem iprob from FP64 primitives (host or device):
+ * rho[ncell], vel[ndim * ncell], p[ncell] in that problem's layout; resets
+ * its time to 0. */
+int genasis_hydro_batch_set_primitive(genasis_hydro_t h, int iprob, const double *rho, const double *vel,
+                                      const double *p);
+/* nsteps RK2 steps of every problem (Eqs. RungeKutta1-3), each with its own
+ * dt = cfl * dt_CFL (Eq. courantTimeStep) taken on the device; t_end > 0
+ * stops each problem exactly at t_end (0: no end time).  Asynchronous. */
+int genasis_hydro_batch_run(genasis_hydro_t h, int nsteps, double cfl, double t_end);
+/* Conserved state of problem iprob, (ndim + 2) * ncell values in
+ * `precision` (GENASIS_FP64 or GENASIS_FP32_MIXED), host or device;
+ * synchronises.  get_times stores the nprob problem times (host). */
+int genasis_hydro_batch_get_conserved(genasis_hydro_t h, int iprob, void *U, int precision);
+int genasis_hydro_batch_get_times(genasis_hydro_t h, double *t);
+
+/* Attach a trained flux-correction network to a 2D GENASIS_FP32_MIXED
+ * single-mesh handle (HLL or HLLC, n[q] >= 6).  The paper has no learned
+ * term: the correction, its features, the flux-corrected-transport limiter
+ * and the positivity fallback are those of genasis_learned_* below, added to
+ * the face flux of Sec. 3.2 so that the update stays in conservation form.
+ *   bf16_weights  host or device pointer to the genasis_mlp_param_count()
+ *                 parameters (W1 [64][24], b1 [64], W2 [64][64], b2 [64],
+ *                 W3 [4][64], b3 [4]) as BF16 values (uint16 bit patterns,
+ *                 the upper half of the FP32 value); copied
+ *   bytes         2 * genasis_mlp_param_count(); a NULL pointer with
+ *                 bytes = 0 detaches the network (plain scheme again)
+ * While a network is attached, genasis_hydro_step and genasis_hydro_advance
+ * run the corrected scheme on the handle's state and time (same stream);
+ * every other call is unchanged.  Returns EINVAL for another kind of handle
+ * or a wrong size. */
+int genasis_hydro_set_flux_mlp(genasis_hydro_t h, const void *bf16_weights, size_t bytes);
+
 /* ---------------------------------------------------------------------------
  * Learned flux correction (2D).  Not in the paper: the benchmark adds to the
  * face flux of Sec. 3.2 (HLL or HLLC) a correction predicted by a small network
@@ -319,11 +385,14 @@ int genasis_mlp_opt_get_params(genasis_mlp_opt_t o, float *params);
  * 31 MiB (for example 1.5 M cells in 3D FP32, 0.78 M in 3D FP64), at most
  * 4096 CTAs per stage; larger sizes return GENASIS_EINVAL with a message.
  * The first call on a device looks up the device address of the static array
- * (cudaGetSymbolAddress) with that device current, so make the first call
- * before any stream capture.  All calls share the array and it keeps the last
- * call's contents: calls that overlap on the GPU (other streams, other host
- * threads) race on it.  Synchronises the stream; returns GENASIS_ENONPHYS if
- * the step met a non-physical state. */
+ * (cudaGetSymbolAddress) with that device current and caches it for the life
+ * of the process: do not call it on a device after a cudaDeviceReset of that
+ * device.  All calls share the array and it keeps the last call's contents:
+ * calls that overlap on the GPU (other streams, other host threads) race on
+ * it.  Every call copies the widths from host memory and synchronises the
+ * stream, so it cannot be made while that stream is capturing (it returns
+ * GENASIS_EINVAL then).  Returns GENASIS_ENONPHYS if the step met a
+ * non-physical state. */
 int genasis_hydro_step_noalloc(const genasis_hydro_desc *desc, const void *U_in, void *U_out, double dt);
 
 /* ---------------------------------------------------------------------------

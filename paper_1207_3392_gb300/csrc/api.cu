@@ -369,6 +369,8 @@ int export_array(genasis_hydro* h, void* U, int precision) {
 }
 
 int free_all(genasis_hydro* h) {
+  if (h->batch) genasis_batch_destroy(h->batch);
+  if (h->lf) genasis_learned_destroy(h->lf);
   if (h->stream) cudaStreamSynchronize(h->stream);
   for (int b = 0; b < 2; ++b)
     if (h->graph[b]) cudaGraphExecDestroy(h->graph[b]);
@@ -411,6 +413,10 @@ int genasis_hydro_create(const genasis_hydro_desc* d, genasis_hydro_t* out) {
     h->bc_lo[q] = q < d->ndim ? d->bc_lo[q] : GENASIS_BC_OUTFLOW;
     h->bc_hi[q] = q < d->ndim ? d->bc_hi[q] : GENASIS_BC_OUTFLOW;
     h->ncell *= (size_t)h->n[q];
+  }
+  for (int q = 0; q < d->ndim; ++q) {
+    h->origin[q] = d->origin[q];
+    h->hw[q].assign(d->widths[q], d->widths[q] + d->n[q]);
   }
   h->gamma = d->gamma;
   h->theta = d->theta;
@@ -467,6 +473,7 @@ int genasis_hydro_destroy(genasis_hydro_t h) {
 }
 
 int genasis_hydro_set_primitive(genasis_hydro_t h, const double* rho, const double* vel, const double* p) {
+  GH_SINGLE_MESH(h);
   if (!h || !rho || !vel || !p) return fail(GENASIS_EINVAL, "NULL argument");
   const double* src[3] = {rho, vel, p};
   const size_t cnt[3] = {h->ncell, h->ncell * h->ndim, h->ncell};
@@ -501,6 +508,7 @@ int genasis_hydro_set_primitive(genasis_hydro_t h, const double* rho, const doub
 }
 
 int genasis_hydro_set_conserved(genasis_hydro_t h, const void* U, int precision) {
+  GH_SINGLE_MESH(h);
   if (!h || !U) return fail(GENASIS_EINVAL, "NULL argument");
   if (precision != GENASIS_FP64 && precision != GENASIS_FP32_MIXED) return fail(GENASIS_EINVAL, "bad precision");
   int rc = import_array(h, U, precision, h->ncell * h->nv, h->U[h->cur]);
@@ -510,23 +518,27 @@ int genasis_hydro_set_conserved(genasis_hydro_t h, const void* U, int precision)
 }
 
 int genasis_hydro_set_conserved_async(genasis_hydro_t h, const void* U, int precision) {
+  GH_SINGLE_MESH(h);
   if (!h || !U) return fail(GENASIS_EINVAL, "NULL argument");
   if (precision != GENASIS_FP64 && precision != GENASIS_FP32_MIXED) return fail(GENASIS_EINVAL, "bad precision");
   return import_array(h, U, precision, h->ncell * h->nv, h->U[h->cur]);
 }
 
 int genasis_hydro_get_conserved_async(genasis_hydro_t h, void* U, int precision) {
+  GH_SINGLE_MESH(h);
   if (!h || !U) return fail(GENASIS_EINVAL, "NULL argument");
   if (precision != GENASIS_FP64 && precision != GENASIS_FP32_MIXED) return fail(GENASIS_EINVAL, "bad precision");
   return export_array(h, U, precision);
 }
 
 int genasis_hydro_sync(genasis_hydro_t h) {
+  GH_SINGLE_MESH(h);
   if (!h) return fail(GENASIS_EINVAL, "NULL handle");
   return sync_status(h);
 }
 
 int genasis_hydro_get_conserved(genasis_hydro_t h, void* U, int precision) {
+  GH_SINGLE_MESH(h);
   if (!h || !U) return fail(GENASIS_EINVAL, "NULL argument");
   if (precision != GENASIS_FP64 && precision != GENASIS_FP32_MIXED) return fail(GENASIS_EINVAL, "bad precision");
   int rc = export_array(h, U, precision);
@@ -536,6 +548,7 @@ int genasis_hydro_get_conserved(genasis_hydro_t h, void* U, int precision) {
 
 
 int genasis_hydro_compute_dt(genasis_hydro_t h, double cfl, double* dt) {
+  GH_SINGLE_MESH(h);
   if (!h || !dt) return fail(GENASIS_EINVAL, "NULL argument");
   if (!(cfl > 0.0)) return fail(GENASIS_EINVAL, "cfl must be > 0");
   int rc = reduce_now(h, true);
@@ -549,16 +562,22 @@ int genasis_hydro_compute_dt(genasis_hydro_t h, double cfl, double* dt) {
 }
 
 int genasis_hydro_step(genasis_hydro_t h, double dt) {
+  GH_SINGLE_MESH(h);
   if (!h) return fail(GENASIS_EINVAL, "NULL handle");
   if (!(dt > 0.0) || !isfinite(dt)) return fail(GENASIS_EINVAL, "dt must be positive and finite");
+  if (h->lf) return learned_run_on(h->lf, h->U[h->cur], h->scal + SCAL_T, h->status, 0, 0.0, 0.0, dt);
   return enqueue_step(h, FIN_FIXED, dt, 0.0, 0.0);
 }
 
 int genasis_hydro_advance(genasis_hydro_t h, int nsteps, double cfl, double t_end, double* t_out) {
+  GH_SINGLE_MESH(h);
   if (!h) return fail(GENASIS_EINVAL, "NULL handle");
   if (nsteps < 0) return fail(GENASIS_EINVAL, "nsteps < 0");
   if (!(cfl > 0.0)) return fail(GENASIS_EINVAL, "cfl must be > 0");
-  if (nsteps > 0) {
+  if (h->lf && nsteps > 0) {
+    int rc = learned_run_on(h->lf, h->U[h->cur], h->scal + SCAL_T, h->status, nsteps, cfl, t_end, 0.0);
+    if (rc) return rc;
+  } else if (nsteps > 0) {
     const int cur0 = h->cur;
     if (h->g_nsteps != nsteps || h->g_cfl != cfl || h->g_tend != t_end) {
       for (int b = 0; b < 2; ++b)
@@ -597,6 +616,7 @@ int genasis_hydro_advance(genasis_hydro_t h, int nsteps, double cfl, double t_en
 }
 
 int genasis_hydro_get_time(genasis_hydro_t h, double* t) {
+  GH_SINGLE_MESH(h);
   if (!h || !t) return fail(GENASIS_EINVAL, "NULL argument");
   GH_CK(cudaMemcpyAsync(t, h->scal + SCAL_T, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   GH_CK(cudaStreamSynchronize(h->stream));
@@ -604,6 +624,7 @@ int genasis_hydro_get_time(genasis_hydro_t h, double* t) {
 }
 
 int genasis_hydro_set_time(genasis_hydro_t h, double t) {
+  GH_SINGLE_MESH(h);
   if (!h || !isfinite(t)) return fail(GENASIS_EINVAL, "bad argument");
   GH_CK(cudaMemcpyAsync(h->scal + SCAL_T, &t, sizeof(double), cudaMemcpyHostToDevice, h->stream));
   GH_CK(cudaStreamSynchronize(h->stream));
@@ -611,6 +632,7 @@ int genasis_hydro_set_time(genasis_hydro_t h, double t) {
 }
 
 int genasis_hydro_get_totals(genasis_hydro_t h, double* totals) {
+  GH_SINGLE_MESH(h);
   if (!h || !totals) return fail(GENASIS_EINVAL, "NULL argument");
   int rc = reduce_now(h, false);
   if (rc) return rc;
@@ -620,10 +642,12 @@ int genasis_hydro_get_totals(genasis_hydro_t h, double* totals) {
 
 int genasis_hydro_status(genasis_hydro_t h) {
   if (!h) return fail(GENASIS_EINVAL, "NULL handle");
+  if (h->batch) return genasis_batch_status(h->batch, nullptr);
   return sync_status(h);
 }
 
 int genasis_hydro_clear_status(genasis_hydro_t h) {
+  GH_SINGLE_MESH(h);
   if (!h) return fail(GENASIS_EINVAL, "NULL handle");
   GH_CK(cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream));
   GH_CK(cudaStreamSynchronize(h->stream));
@@ -631,6 +655,7 @@ int genasis_hydro_clear_status(genasis_hydro_t h) {
 }
 
 int genasis_hydro_set_tile(genasis_hydro_t h, int tile, int kchunk) {
+  GH_SINGLE_MESH(h);
   if (!h) return fail(GENASIS_EINVAL, "NULL handle");
   if (kchunk < 0) return fail(GENASIS_EINVAL, "kchunk < 0");
   GH_CK(cudaStreamSynchronize(h->stream));
@@ -638,6 +663,7 @@ int genasis_hydro_set_tile(genasis_hydro_t h, int tile, int kchunk) {
 }
 
 int genasis_hydro_get_tile(genasis_hydro_t h, int* info) {
+  GH_SINGLE_MESH(h);
   if (!h || !info) return fail(GENASIS_EINVAL, "NULL argument");
   info[0] = h->tile;
   info[1] = h->v1.tx;
@@ -649,6 +675,7 @@ int genasis_hydro_get_tile(genasis_hydro_t h, int* info) {
 }
 
 int genasis_hydro_set_option(genasis_hydro_t h, int option, int value) {
+  GH_SINGLE_MESH(h);
   if (!h) return fail(GENASIS_EINVAL, "NULL handle");
   if (option == GENASIS_OPT_STEP_TOTALS) {
     if (value != 0 && value != 1) return fail(GENASIS_EINVAL, "GENASIS_OPT_STEP_TOTALS takes 0 or 1");
@@ -666,6 +693,7 @@ int genasis_hydro_set_option(genasis_hydro_t h, int option, int value) {
 }
 
 int genasis_hydro_set_potential_gradient(genasis_hydro_t h, const double* grad_phi) {
+  GH_SINGLE_MESH(h);
   if (!h || !grad_phi) return fail(GENASIS_EINVAL, "NULL argument");
   for (int q = 0; q < 3; ++q)
     if (!(fabs(grad_phi[q]) < INFINITY)) return fail(GENASIS_EINVAL, "potential gradient must be finite");
@@ -684,6 +712,7 @@ int genasis_hydro_set_potential_gradient(genasis_hydro_t h, const double* grad_p
 }
 
 int genasis_hydro_get_step_totals(genasis_hydro_t h, double* totals) {
+  GH_SINGLE_MESH(h);
   if (!h || !totals) return fail(GENASIS_EINVAL, "NULL argument");
   GH_CK(cudaMemcpyAsync(totals, h->scal + SCAL_TOT, h->nv * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   return sync_status(h);
@@ -706,6 +735,7 @@ static int mesh2_of(genasis_hydro* h, Mesh2* M) {
 }
 
 int genasis_hydro_accumulate_face_flux(genasis_hydro_t h, int stride, double weight, double* F) {
+  GH_SINGLE_MESH(h);
   if (!h || !F) return fail(GENASIS_EINVAL, "NULL argument");
   Mesh2 M;
   int rc = mesh2_of(h, &M);
@@ -719,6 +749,7 @@ int genasis_hydro_accumulate_face_flux(genasis_hydro_t h, int stride, double wei
 }
 
 int genasis_hydro_restrict(genasis_hydro_t h, int factor, float* U_coarse) {
+  GH_SINGLE_MESH(h);
   if (!h || !U_coarse) return fail(GENASIS_EINVAL, "NULL argument");
   Mesh2 M;
   int rc = mesh2_of(h, &M);
@@ -731,11 +762,13 @@ int genasis_hydro_restrict(genasis_hydro_t h, int factor, float* U_coarse) {
 }
 
 int genasis_hydro_launches_per_step(genasis_hydro_t h) {
+  GH_SINGLE_MESH(h);
   if (!h) return fail(GENASIS_EINVAL, "NULL handle");
   return h->solver == GENASIS_HLLC_SWITCH ? 5 : 3;
 }
 
 int genasis_hydro_profile_step(genasis_hydro_t h, double cfl, float* ms) {
+  GH_SINGLE_MESH(h);
   if (!h || !ms) return fail(GENASIS_EINVAL, "NULL argument");
   if (!(cfl > 0.0)) return fail(GENASIS_EINVAL, "cfl must be > 0");
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -756,6 +789,7 @@ int genasis_hydro_profile_step(genasis_hydro_t h, double cfl, float* ms) {
 }
 
 int genasis_hydro_autotune(genasis_hydro_t h, int trial_steps, const char* cache_path) {
+  GH_SINGLE_MESH(h);
   if (!h || trial_steps < 1) return fail(GENASIS_EINVAL, "bad argument");
   char key[160];
   snprintf(key, sizeof(key), "ndim=%d n=%d,%d,%d prec=%d solver=%d", h->ndim, h->n[0], h->n[1], h->n[2], h->prec,

@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <type_traits>
+#include <vector>
 
 #include "aux_kernels.h"
 #include "registry.h"
@@ -43,7 +44,23 @@ struct genasis_hydro {
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   int g_nsteps = -1;
   double g_cfl = 0, g_tend = 0;
+  // mesh as described at creation (host): low corner and widths
+  double origin[3] = {0.0, 0.0, 0.0};
+  std::vector<double> hw[3];
+  // a batch handle (genasis_hydro_batch_create) holds only this
+  genasis_batch_t batch = nullptr;
+  // attached flux-correction network (genasis_hydro_set_flux_mlp): step and
+  // advance run the corrected scheme of this learned solver on the state
+  genasis_learned_t lf = nullptr;
 };
+
+// Single-mesh entry points refuse batch handles.
+#define GH_SINGLE_MESH(h)                                                                          \
+  do {                                                                                             \
+    if ((h) && (h)->batch)                                                                         \
+      return ::gh::fail(GENASIS_EINVAL, "%s: not a call for a batch handle (genasis_hydro_batch_*)", \
+                        __func__);                                                                 \
+  } while (0)
 
 namespace gh {
 

@@ -957,6 +957,26 @@ int learned_enqueue_step(genasis_learned* l, double cfl, double t_end, double fi
 
 }  // namespace
 
+namespace gh {
+
+__global__ void or_status_kernel(unsigned* dst, const unsigned* src) { *dst |= *src; }
+
+int learned_run_on(genasis_learned_t l, void* U, double* t, unsigned* status, int nsteps, double cfl, double t_end,
+                   double dt_fixed) {
+  const size_t bytes = l->ncell * 4 * sizeof(float);
+  GH_CK(cudaMemcpyAsync(l->U[l->cur], U, bytes, cudaMemcpyDeviceToDevice, l->stream));
+  GH_CK(cudaMemcpyAsync(l->scal + SCAL_T, t, sizeof(double), cudaMemcpyDeviceToDevice, l->stream));
+  const int rc = nsteps > 0 ? genasis_learned_advance(l, nsteps, cfl, t_end, nullptr) : genasis_learned_step(l, dt_fixed);
+  if (rc) return rc;
+  GH_CK(cudaMemcpyAsync(U, l->U[l->cur], bytes, cudaMemcpyDeviceToDevice, l->stream));
+  GH_CK(cudaMemcpyAsync(t, l->scal + SCAL_T, sizeof(double), cudaMemcpyDeviceToDevice, l->stream));
+  or_status_kernel<<<1, 1, 0, l->stream>>>(status, l->status);
+  GH_CK(cudaGetLastError());
+  return GENASIS_OK;
+}
+
+}  // namespace gh
+
 extern "C" {
 
 int genasis_learned_create(const genasis_hydro_desc* d, genasis_learned_t* out) {

@@ -35,7 +35,7 @@ class NonPhysicalState(HydroError):
 
 class Desc(ctypes.Structure):
     _fields_ = [("ndim", ctypes.c_int), ("n", ctypes.c_int * 3), ("widths", ctypes.c_void_p * 3),
-                ("bc_lo", ctypes.c_int * 3), ("bc_hi", ctypes.c_int * 3), ("gamma", ctypes.c_double),
+                ("origin", ctypes.c_double * 3), ("bc_lo", ctypes.c_int * 3), ("bc_hi", ctypes.c_int * 3), ("gamma", ctypes.c_double),
                 ("solver", ctypes.c_int), ("theta", ctypes.c_double), ("precision", ctypes.c_int),
                 ("stream", ctypes.c_void_p)]
 
@@ -111,6 +111,14 @@ SIGNATURES = {
     "genasis_batch_get_tile": [_P, _P],
     "genasis_batch_autotune": [_P, _I, ctypes.c_char_p],
     "genasis_batch_profile_step": [_P, _D, _P],
+    "genasis_hydro_get_centers": [_P, _I, _P],
+    "genasis_hydro_batch_create": [_I, _P, ctypes.POINTER(_P)],
+    "genasis_hydro_batch_set_primitive": [_P, _I, _P, _P, _P],
+    "genasis_hydro_batch_run": [_P, _I, _D, _D],
+    "genasis_hydro_batch_get_conserved": [_P, _I, _P, _I],
+    "genasis_hydro_batch_get_times": [_P, _P],
+    "genasis_hydro_set_flux_mlp": [_P, _P, ctypes.c_size_t],
+    "genasis_measure_fma_rate": [_I, _P],
 }
 
 
@@ -161,7 +169,7 @@ class Hydro:
     """One mesh + state on the GPU (a genasis_hydro_t handle)."""
 
     def __init__(self, ndim, n, widths, bc_lo, bc_hi, gamma=1.4, solver=HLLC, theta=1.4,
-                 precision=FP64, stream=None):
+                 precision=FP64, stream=None, origin=(0.0, 0.0, 0.0)):
         lib = load()
         self.ndim = int(ndim)
         self.n = tuple(int(x) for x in (list(n) + [1, 1, 1])[:3])
@@ -177,6 +185,7 @@ class Hydro:
             d.widths[q] = self._widths[q].ctypes.data if q < self.ndim else None
             d.bc_lo[q] = int(bc_lo[q]) if q < self.ndim else 0
             d.bc_hi[q] = int(bc_hi[q]) if q < self.ndim else 0
+            d.origin[q] = float(origin[q]) if q < len(origin) else 0.0
         d.gamma, d.solver, d.theta, d.precision = float(gamma), int(solver), float(theta), self.precision
         # stream: a cudaStream_t handle (int) or torch.cuda.Stream; None or 0
         # (the legacy default stream) gives the handle a stream of its own
@@ -191,7 +200,8 @@ class Hydro:
     @classmethod
     def from_problem(cls, prob, precision=FP64, solver=None, stream=None, set_state=True):
         h = cls(prob.ndim, prob.n, prob.widths, prob.bc_lo, prob.bc_hi, prob.gamma,
-                prob.solver if solver is None else solver, prob.theta, precision, stream)
+                prob.solver if solver is None else solver, prob.theta, precision, stream,
+                origin=getattr(prob, "origin", (0.0, 0.0, 0.0)))
         if any(getattr(prob, "grad_phi", (0.0, 0.0, 0.0))):
             h.set_potential_gradient(prob.grad_phi)
         if set_state:
@@ -252,6 +262,27 @@ class Hydro:
         g = np.zeros(3)
         g[: len(grad_phi)] = grad_phi
         check(load().genasis_hydro_set_potential_gradient(self._h, g.ctypes.data))
+
+    def centers(self, axis):
+        """Geometric cell centres along `axis` measured from the origin."""
+        out = np.empty(self.n[axis])
+        check(load().genasis_hydro_get_centers(self._h, int(axis), out.ctypes.data))
+        return out
+
+    def set_flux_mlp(self, weights_bf16):
+        """Attach the flux-correction network from its BF16 parameters (uint16
+        bit patterns, numpy or torch, host or CUDA); None detaches it.  With a
+        network attached, step/advance run the corrected scheme."""
+        if weights_bf16 is None:
+            check(load().genasis_hydro_set_flux_mlp(self._h, None, 0))
+            return
+        if hasattr(weights_bf16, "data_ptr"):
+            ptr, nbytes = weights_bf16.data_ptr(), weights_bf16.numel() * weights_bf16.element_size()
+            keep = weights_bf16
+        else:
+            keep = np.ascontiguousarray(weights_bf16, dtype=np.uint16)
+            ptr, nbytes = keep.ctypes.data, keep.nbytes
+        check(load().genasis_hydro_set_flux_mlp(self._h, ptr, nbytes))
 
     # -- stepping -------------------------------------------------------------
     def compute_dt(self, cfl):
@@ -541,6 +572,71 @@ def step_noalloc(prob, U_in, U_out, dt, precision=FP64, solver=None, stream=None
     check(load().genasis_hydro_step_noalloc(ctypes.byref(d), pin, pout, float(dt)))
 
 
+class HydroBatch:
+    """Many independent 1D/2D problems behind one genasis_hydro_t
+    (genasis_hydro_batch_create from one genasis_hydro_desc per problem)."""
+
+    def __init__(self, probs, precision=FP64, solver=None, theta=None, stream=None):
+        self._keep = []
+        arr = (Desc * len(probs))()
+        for i, pr in enumerate(probs):
+            d, keep = _desc(pr, precision, solver, stream)
+            if theta is not None:
+                d.theta = float(theta)
+            arr[i] = d
+            self._keep.append(keep)
+        self._h = ctypes.c_void_p()
+        check(load().genasis_hydro_batch_create(len(probs), ctypes.cast(arr, ctypes.c_void_p), ctypes.byref(self._h)))
+        self.probs = [(int(pr.ndim), tuple(int(x) for x in pr.n)) for pr in probs]
+        self.precision = int(precision)
+
+    def set_primitive(self, i, rho, vel, p):
+        nd, n = self.probs[i]
+        nc = int(np.prod(n[:nd]))
+        pr, a = _ptr(rho, np.float64, nc, "rho")
+        pv, b = _ptr(vel, np.float64, nd * nc, "vel")
+        pp, c = _ptr(p, np.float64, nc, "p")
+        check(load().genasis_hydro_batch_set_primitive(self._h, int(i), pr, pv, pp))
+
+    def run(self, nsteps, cfl, t_end=0.0):
+        check(load().genasis_hydro_batch_run(self._h, int(nsteps), float(cfl), float(t_end)))
+
+    def get_conserved(self, i, precision=None):
+        nd, n = self.probs[i]
+        precision = FP64 if precision is None else precision
+        dt = np.float64 if precision == FP64 else np.float32
+        out = np.empty((nd + 2,) + tuple(reversed(n[:nd])), dtype=dt)
+        check(load().genasis_hydro_batch_get_conserved(self._h, int(i), out.ctypes.data, int(precision)))
+        return out
+
+    def times(self):
+        out = np.empty(len(self.probs))
+        check(load().genasis_hydro_batch_get_times(self._h, out.ctypes.data))
+        return out
+
+    def status(self):
+        return check(load().genasis_hydro_status(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load().genasis_hydro_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def measure_fma_rate(kind):
+    """Measured vector FMA rate of this GPU in TFLOP/s: kind 0 FP64, 1 FP32,
+    2 FP32 with the packed two-lane FMA."""
+    out = ctypes.c_double()
+    check(load().genasis_measure_fma_rate(int(kind), ctypes.byref(out)))
+    return out.value
+
+
 def _desc(prob, precision, solver=None, stream=None):
     d = Desc()
     d.ndim = int(prob.ndim)
@@ -550,6 +646,7 @@ def _desc(prob, precision, solver=None, stream=None):
         d.widths[q] = keep[q].ctypes.data if q < prob.ndim else None
         d.bc_lo[q] = int(prob.bc_lo[q]) if q < prob.ndim else 0
         d.bc_hi[q] = int(prob.bc_hi[q]) if q < prob.ndim else 0
+        d.origin[q] = float(getattr(prob, "origin", (0.0, 0.0, 0.0))[q]) if q < prob.ndim else 0.0
     d.gamma = float(prob.gamma)
     d.solver = int(prob.solver if solver is None else solver)
     d.theta = float(prob.theta)

@@ -104,8 +104,44 @@ def test_null_handle_calls_fail_cleanly(lib):
         "genasis_batch_set_tile": (0, 32), "genasis_batch_autotune": (1, None),
         "genasis_fmr_step": (1, 0.3, None), "genasis_fmr_autotune": (1,), "genasis_fmr_get_level": (0, buf),
         "genasis_fmr_set_level": (0, buf),
+        "genasis_hydro_get_centers": (0, buf), "genasis_hydro_batch_run": (1, 0.5, 0.0),
+        "genasis_hydro_batch_get_times": (buf,), "genasis_hydro_batch_get_conserved": (0, buf, H.FP64),
+        "genasis_hydro_batch_set_primitive": (0, buf, buf, buf), "genasis_hydro_set_flux_mlp": (buf, 16),
     }
     for name, args in calls.items():
         assert getattr(L, name)(None, *args) == H.EINVAL, name
     for name in ("genasis_hydro_destroy", "genasis_learned_destroy", "genasis_batch_destroy", "genasis_fmr_destroy"):
         assert getattr(L, name)(None) == H.OK, name
+
+
+def test_batch_descriptions_validated_on_host(lib):
+    """genasis_hydro_batch_create refuses 3D problems and descriptions whose
+    solver, theta or precision differ, before any CUDA call."""
+    from paper_1207_3392_gb300 import hydro as H
+    L = H.load()
+    w = np.full(8, 0.125)
+    arr = (H.Desc * 2)()
+    for d in arr:
+        d.ndim, d.n[0], d.n[1], d.n[2] = 1, 8, 1, 1
+        d.widths[0] = w.ctypes.data
+        d.gamma, d.solver, d.theta, d.precision = 1.4, 1, 1.4, 0
+        d.bc_lo[0] = d.bc_hi[0] = 2
+    out = ctypes.c_void_p()
+    arr[1].theta = 1.5
+    assert L.genasis_hydro_batch_create(2, ctypes.cast(arr, ctypes.c_void_p), ctypes.byref(out)) == H.EINVAL
+    assert b"theta" in L.genasis_hydro_last_error()
+    arr[1].theta = 1.4
+    arr[1].ndim = 3
+    assert L.genasis_hydro_batch_create(2, ctypes.cast(arr, ctypes.c_void_p), ctypes.byref(out)) == H.EINVAL
+    assert L.genasis_hydro_batch_create(0, None, ctypes.byref(out)) == H.EINVAL
+
+
+def test_descriptor_layout_matches_the_header():
+    """The binding's genasis_hydro_desc has the header's fields in order."""
+    from paper_1207_3392_gb300 import hydro as H
+    with open(os.path.join(ROOT, "include", "genasis_hydro.h")) as f:
+        text = f.read()
+    body = text[text.index("typedef struct {\n  int ndim;"):]
+    body = body[: body.index("} genasis_hydro_desc;")]
+    fields = re.findall(r"\*?(\w+)(?:\[\d\])?;", body)
+    assert fields == [name for name, _ in H.Desc._fields_], fields
