@@ -70,9 +70,7 @@ def _config(args, n):
     return {"workload": f"sedov3d_{n}^3_{args.solver}_{args.precision}",
             "cells": n ** 3, "domain": "[-1,1]^3", "gamma": 1.4, "bc": "reflecting",
             "solver": args.solver.upper(),
-            "precision": {"fp32": "fp32 storage and fluxes, fp64 internal-energy recovery and reductions",
-                          "fp64": "fp64",
-                          "fp64dw": "double-word FP32 pairs (~48 bits) on the FP32 pipes, FP64 parity"}[args.precision],
+            "precision": PRECISION_LABEL[args.precision],
             "cfl": 0.3, "step": "one TVD-RK2 step: 2 stage kernels + dt/totals finalize",
             "l2": f"inputs larger than L2 (state {n**3 * 5 * (4 if args.precision == 'fp32' else 8) / 1e6:.0f} MB)",
             "parallelism": "replicas" if args.gpus > 1 else "single GPU"}
@@ -139,27 +137,34 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-# Algorithmic floating-point operations per cell per RK stage of the 3D update,
-# counted from the formulas (an FMA-able a*b+c as 2; division, square root,
-# min, max and abs as 1; compares and selects as 0).  Both stages come to the
-# same total; the per-item derivation is in the design notes.
-#   recovery 12, limited slopes 15 x 10, face values 15 x 4, 3 face fluxes
-#   (HLLC 96 / HLL 90 each), divergence 40, stage combine (stage 2: U^1 on
-#   load 10 + final 15; stage 1: CFL speed 15 + totals 10)
-FLOPS_3D = {"hllc": 12 + 150 + 60 + 3 * 96 + 40 + 25, "hll": 12 + 150 + 60 + 3 * 90 + 40 + 25}
-FLOPS_3D["hllc_switch"] = FLOPS_3D["hllc"]  # away from shocks; the detector's own work is not counted
-# Vector peak of this GPU: 152 SMs x 128 lanes x 2 (FMA) x 2.07 GHz (FP32);
-# FP64 at the nominal 1.25 TFLOP/s.
-PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-PEAK_FP64_TFLOPS = 1.25
-# DRAM bytes (read + write) per cell of the FP32 HLLC 3D stage kernels, from
-# one ncu capture of the same kernels at 192^3 for each launch configuration
-# (tile, planes per CTA) the autotuner picks at 256^3 (summary under
-# profiles/), scaled to the bench's cell count (traffic grows with the cells).
-# Other configurations report no traffic.
-TRAFFIC_PER_CELL_FP32_HLLC = {
-    (8, 40): {"stage1": (150.860544e6 + 104.290304e6) / 192 ** 3,
-              "stage2": (306.705920e6 + 120.133632e6) / 192 ** 3},
+# Floating-point operations per cell of the 3D update, counted by running the
+# oracle's own code with an operation-counting scalar (oracle/opcount.cpp; the
+# test tests/test_oracle_opcount.py fixes these numbers from the counter).
+# Rule: +, -, *, / each 1 (a product feeding a sum 2), sqrt, min, max, fabs 1.
+# Stage 1 (the dominant kernel) = L[U^n] + the CFL speed + the conserved
+# totals; a step = the oracle's RK2 step + CFL + totals.  The oracle forms
+# both sides' states and fluxes at every HLLC face and divides where the
+# kernel multiplies by stored reciprocals, so these counts are the method's
+# operations as the plain definition writes them.
+FLOPS_STAGE1_3D = {"hllc": 744, "hll": 720}
+FLOPS_STEP_3D = {"hllc": 1469, "hll": 1421}
+FLOPS_STAGE1_3D["hllc_switch"] = FLOPS_STAGE1_3D["hllc"]  # away from shocks; the detector is not counted
+FLOPS_STEP_3D["hllc_switch"] = FLOPS_STEP_3D["hllc"]
+# DRAM bytes (read + write) per launch of the FP32 HLLC 3D stage kernels at
+# 256^3, from one ncu capture of the bench's own launch configuration (tile
+# 8, 40 planes per CTA; profiles/stage_fp32_hllc_sedov256_ncu.md).  Other
+# configurations, precisions and sizes report no traffic.
+TRAFFIC_FP32_HLLC_256 = {
+    (8, 40): {"stage1": 356.879360e6 + 299.414272e6, "stage2": 731.254016e6 + 311.632896e6},
+}
+PRECISION_LABEL = {
+    "fp32": ("FP32 storage, FP32 fluxes and FP32 per-cell CFL speeds; the internal-energy recovery "
+             "e = G - |S|^2/(2D) in FP64 only where the kinetic energy exceeds half of G; per-column "
+             "conserved totals as compensated FP32 pairs; the dt and totals reductions across threads "
+             "and CTAs in FP64"),
+    "fp64": "FP64 throughout",
+    "fp64dw": ("double-word FP32 pairs (~48 significant bits) for every value and operation, on the FP32 "
+               "pipes; FP64 parity"),
 }
 
 
@@ -249,6 +254,9 @@ def run_reference(args):
     el = time.perf_counter() - t0
     val = pr.ncells * 2 * done / el
     cfg = _config(args, args.n)
+    # the same workload; the arm's own arithmetic and hardware
+    cfg["precision"] = PRECISION_LABEL["fp64"] + " (the plain CPU oracle)"
+    cfg["implementation"] = f"FP64 CPU oracle, OpenMP over cells on {os.environ['OMP_NUM_THREADS']} host cores"
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / max(done, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -258,6 +266,67 @@ def run_reference(args):
                              "sample": f"FP64 oracle, the same {n_sample}^3 point blast, {done} timed RK2 steps"},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def _fma_peaks():
+    """Measured vector FMA rates of this GPU (TFLOP/s) from the library's FMA
+    chain kernel: FP64, FP32 and FP32 pairs."""
+    from paper_1207_3392_gb300 import hydro as H
+    out = {}
+    for name, kind in (("fp64", 0), ("fp32", 1), ("fp32x2", 2)):
+        try:
+            out[name] = H.measure_fma_rate(kind)
+        except Exception as e:  # report, do not fail the bench
+            out[name + "_error"] = str(e)[:200]
+    return out
+
+
+_PEAKS = {}
+
+
+def _stage_roofline(args, prec, cells, tile, st1, fin, st2):
+    """Roofline of the dominant stage kernel (the slower of the two).  The
+    metric's roofline is HBM: algorithmic bytes per launch (stage 1 reads U^n
+    and writes K, 2 nv b per cell; stage 2 reads U^n and K and writes
+    U^{n+1}, 3 nv b) over the launch's event-timed duration, against the
+    measured copy bandwidth.  Beside it, the arithmetic roofline: the
+    oracle-counted operations per cell over the same duration, against the
+    FMA rate measured on this GPU (FP32 pipes for FP32 and double word, FP64
+    pipe for FP64)."""
+    from paper_1207_3392_gb300 import hydro as H
+    b = 4 if prec == H.FP32_MIXED else 8
+    nv = 5
+    bytes1, bytes2 = 2 * nv * b * cells, 3 * nv * b * cells
+    peak, peak_kind = _peaks()
+    dom = "stage2" if st2 >= st1 else "stage1"
+    dom_ms, dom_bytes = (st2, bytes2) if dom == "stage2" else (st1, bytes1)
+    achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
+    per_launch = TRAFFIC_FP32_HLLC_256.get((tile["tile"], tile["kchunk"]))
+    traffic = (per_launch[dom] if per_launch and b == 4 and args.solver == "hllc" and cells == 256 ** 3
+               else None)
+    if not _PEAKS:
+        _PEAKS.update(_fma_peaks())
+    fkey = "fp64" if prec == H.FP64 else "fp32"
+    flops_cell = FLOPS_STAGE1_3D[args.solver] if dom == "stage1" else FLOPS_STEP_3D[args.solver] - FLOPS_STAGE1_3D[
+        args.solver]
+    achieved_f = flops_cell * cells / (dom_ms * 1e-3) / 1e12
+    peak_f = _PEAKS.get(fkey)
+    tname = {H.FP32_MIXED: "float", H.FP64: "double", H.FP64_DW: "dw"}[prec]
+    return {"bound": "hbm", "kernel": f"hydro_stage_kernel<3,{tname},{args.solver.upper()},{dom[-1]}>",
+            "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)" if peak_kind == "measured"
+            else "fallback 6800 GB/s",
+            "algorithmic_bytes_per_cell": dom_bytes // cells, "traffic": traffic,
+            "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of this launch configuration "
+                               "at 256^3" if traffic else None),
+            "step_frac": (bytes1 + bytes2) / ((st1 + fin + st2) * 1e-3) / 1e9 / peak,
+            "alu": {"achieved": achieved_f, "peak": peak_f, "unit": "TFLOP/s",
+                    "frac": achieved_f / peak_f if peak_f else None,
+                    "peak_source": f"measured {fkey} FMA chains on this GPU (genasis_measure_fma_rate)",
+                    "flops_per_cell": flops_cell,
+                    "flops_source": "the oracle's own code run with an operation-counting scalar"},
+            "fma_rates_tflops": dict(_PEAKS),
+            "kernel_ms": {"stage1": st1, "finalize": fin, "stage2": st2}}
 
 
 def run_ours(args):
@@ -321,36 +390,8 @@ def run_ours(args):
     st1 = float(np.mean([k[0] for k in ks]))
     fin = float(np.mean([k[1] for k in ks]))
     st2 = float(np.mean([k[2] for k in ks]))
+    roofline = _stage_roofline(args, prec, cells, tile, st1, fin, st2)
     b = 4 if prec == H.FP32_MIXED else 8
-    nv = 5
-    bytes1, bytes2 = 2 * nv * b * cells, 3 * nv * b * cells
-    peak, peak_kind = _peaks()
-    dom = "stage2" if st2 >= st1 else "stage1"
-    dom_ms, dom_bytes = (st2, bytes2) if dom == "stage2" else (st1, bytes1)
-    achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
-    flops = FLOPS_3D[args.solver] * cells
-    # double-word runs on the FP32 pipes: its algorithmic FP64-equivalent
-    # operations are measured against the FP32 vector peak
-    peak_f = PEAK_FP64_TFLOPS if prec == H.FP64 else PEAK_FP32_TFLOPS
-    achieved_f = flops / (dom_ms * 1e-3) / 1e12
-    per_cell = TRAFFIC_PER_CELL_FP32_HLLC.get((tile["tile"], tile["kchunk"]))
-    traffic = (per_cell[dom] * cells if per_cell and b == 4 and args.solver == "hllc" else None)
-    # The stage kernel is bound by instruction issue on the vector pipes (ncu),
-    # not by DRAM: the roofline is the vector-arithmetic one; the HBM figure of
-    # the metric is reported beside it.
-    tname = {H.FP32_MIXED: "float", H.FP64: "double", H.FP64_DW: "dw"}[prec]
-    roofline = {"bound": "alu", "kernel": f"hydro_stage_kernel<3,{tname},"
-                                          f"{args.solver.upper()},{2 if dom == 'stage2' else 1}>",
-                "achieved": achieved_f, "peak": peak_f, "unit": "TFLOP/s", "frac": achieved_f / peak_f,
-                "peak_source": ("nominal FP64 1.25 TFLOP/s" if prec == H.FP64
-                                else "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"),
-                "algorithmic_flops_per_cell": FLOPS_3D[args.solver], "traffic": traffic,
-                "traffic_source": (f"ncu dram bytes at 192^3, tile {tile['tile']}, {tile['kchunk']} planes "
-                                   "per CTA, scaled by cells" if traffic else None),
-                "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                        "peak_source": f"{peak_kind} hbm_gbs", "algorithmic_bytes_per_cell": dom_bytes // cells,
-                        "step_frac": (bytes1 + bytes2) / ((st1 + fin + st2) * 1e-3) / 1e9 / peak},
-                "kernel_ms": {"stage1": st1, "finalize": fin, "stage2": st2}}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -384,7 +425,7 @@ def run_ours(args):
             hh.sync()
         k = max(2 * nh, min(args.steps, 30))
         reps = []
-        for _ in range(3):  # three timed repetitions; the median is reported
+        for _ in range(5):  # five timed repetitions; the median is reported, with min and max
             torch.cuda.synchronize()
             barrier()
             t0 = time.perf_counter()
@@ -407,6 +448,7 @@ def run_ours(args):
         line["e2e"] = {"value": world * cells * 2 * k / el, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                        "d2h_bytes_per_step": nbytes, "ms_per_step": 1e3 * el / k, "steps": k,
                        "repetitions_ms_per_step": [1e3 * r / k for r in reps],
+                       "min_ms_per_step": 1e3 * min(reps) / k, "max_ms_per_step": 1e3 * max(reps) / k,
                        "pipeline": f"{nh} handles on {nh} streams, page-locked host buffers"}
         for hh in hs:
             hh.close()
@@ -440,7 +482,10 @@ def run_ours(args):
                 torch.cuda.synchronize()
                 mv = a.elapsed_time(z) / kv
                 key = f"{sname}_{pname}" + ("" if totals else "_no_step_totals")
-                variants[key] = {"value": cells * 2 / (mv * 1e-3), "ms_per_step": mv}
+                bv = 4 if pc == H.FP32_MIXED else 8
+                peak, _ = _peaks()
+                variants[key] = {"value": cells * 2 / (mv * 1e-3), "ms_per_step": mv,
+                                 "hbm_frac_step": 5 * 5 * bv * cells / (mv * 1e-3) / 1e9 / peak}
                 hv.close()
         # the centrally refined 320^3 pulse (stretched widths, gamma = 5/3), FP32 HLLC
         pr = P.stretched_pulse_3d(320)
@@ -475,6 +520,15 @@ def run_ours(args):
         mv = a.elapsed_time(z) / 50
         variants["rayleigh_taylor_256x768_hllc_fp32"] = {"value": hv.ncell * 2 / (mv * 1e-3), "ms_per_step": mv}
         hv.close()
+        # the other workloads of the benchmark set, each with its own line
+        for name, fn in (("sod1d_256_hllc_fp64", lambda: measure_sod(stream)),
+                         ("batched_riemann_4096", lambda: measure_batch(("fp32", "fp64dw", "fp64"), 5, 3, stream)),
+                         ("learned_kh2d_256^2_hllc_fct", lambda: measure_learned(50, 3, stream)),
+                         ("sedov3d_fmr_4x128^3_hllc_fp32", lambda: measure_fmr(128, 4, "fp32", "hllc", 10, 3, stream))):
+            try:
+                variants[name] = fn()
+            except Exception as e:  # report, do not fail the bench
+                variants[name] = {"error": str(e)[:300]}
         line["variants"] = variants
 
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -485,99 +539,137 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def run_batch(args):
-    """Batched Riemann set: 4096 independent 1D/2D problems (2.09e8 cells), one
-    persistent launch per RK stage, per-problem CFL dt, graph-captured steps."""
+def _batch_specs(world=1, rank=0):
+    from paper_1207_3392_gb300 import shard
+    all_specs = shard.weak_scaling_specs(world)
+    return all_specs, shard.rank_specs(all_specs, rank, world)
+
+
+class _Mesh:
+    """Mesh-only view of a BatchSpec (the batch needs no arrays at creation)."""
+
+    def __init__(self, sp):
+        from paper_1207_3392_gb300 import problems as P
+        self.ndim, self.gamma = sp.ndim, sp.gamma
+        self.n = (sp.n, sp.n if sp.ndim == 2 else 1, 1)
+        w = P.uniform_widths(sp.n, 0.0, 1.0)
+        self.widths = [w, w][: sp.ndim]
+        self.bc_lo = self.bc_hi = (P.OUTFLOW,) * 3
+
+
+def measure_batch(precisions, steps, warmup, stream, specs=None, autotune=True, sampler=None, barrier=None,
+                  scale_steps=True):
+    """The batched Riemann set (4096 independent 1D/2D problems, 2.09e8 cells)
+    in each precision: one persistent launch per RK stage, per-problem CFL dt,
+    graph-captured steps.  All batches are built first from one pass over the
+    problems (the initial conditions are generated once).  Returns
+    {precision: record}; the record's roofline is that of the dominant stage
+    kernel against the measured HBM bandwidth."""
     import torch
-    from paper_1207_3392_gb300 import build
     from paper_1207_3392_gb300 import hydro as H
     from paper_1207_3392_gb300 import problems as P
+    if specs is None:
+        _, specs = _batch_specs()
+    pc = {"fp32": H.FP32_MIXED, "fp64": H.FP64, "fp64dw": H.FP64_DW}
+    batches = {name: H.Batch([_Mesh(sp) for sp in specs], precision=pc[name], stream=stream.cuda_stream)
+               for name in precisions}
+    for i, sp in enumerate(specs):
+        pr = P.batch_problem(sp)
+        for bb in batches.values():
+            bb.set_primitive(i, pr.rho, pr.vel, pr.p)
+    cells = sum(sp.n ** sp.ndim for sp in specs)
+    cells_nv = sum(sp.n ** sp.ndim * (sp.ndim + 2) for sp in specs)
+    peak, peak_kind = _peaks()
+    out = {}
+    for name in precisions:
+        bb = batches[name]
+        if autotune:
+            bb.autotune(trial_steps=2)
+        # the slower precisions take fewer steps unless the caller asked for this one alone
+        k = steps if (name == "fp32" or not scale_steps) else max(2, steps // (8 if name == "fp64" else 3))
+        for _ in range(max(warmup, 3)):
+            bb.run(1, 0.5)
+        torch.cuda.synchronize()
+        if sampler is not None and name == precisions[0]:
+            sampler.start()
+        if barrier is not None:
+            barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        bb.run(k, 0.5)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if barrier is not None:
+            barrier()
+        clocks = sampler.stop() if sampler is not None and name == precisions[0] else None
+        ms = e0.elapsed_time(e1) / k
+        bb.status()
+        ks = [bb.profile_step(0.5) for _ in range(3)]
+        st1 = float(np.mean([x[0] for x in ks]))
+        fin = float(np.mean([x[1] for x in ks]))
+        st2 = float(np.mean([x[2] for x in ks]))
+        esz = 4 if name == "fp32" else 8
+        dom, dom_ms, dom_bytes = (("stage2", st2, 3 * esz * cells_nv) if st2 >= st1
+                                  else ("stage1", st1, 2 * esz * cells_nv))
+        achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
+        info = bb.tile_info()
+        out[name] = {"value": cells * 2 / (ms * 1e-3), "ms_per_step": ms, "steps": k, "cells": cells,
+                     "dtype": {"fp32": "f32", "fp64": "f64", "fp64dw": "f32x2 double-word"}[name],
+                     "tile": info, "l2": f"inputs larger than L2 (state {cells_nv * esz / 1e9:.2f} GB)",
+                     "roofline": {"bound": "hbm", "kernel": f"hydro_batch_kernel ({dom})", "achieved": achieved,
+                                  "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                                  "peak_source": f"{peak_kind} hbm_gbs",
+                                  "algorithmic_bytes": dom_bytes,
+                                  "step_frac": 5 * esz * cells_nv / ((st1 + fin + st2) * 1e-3) / 1e9 / peak,
+                                  "kernel_ms": {"stage1": st1, "finalize": fin, "stage2": st2}},
+                     "clocks": clocks, "gpu_launches": 3 * k}
+    for bb in batches.values():
+        bb.close()
+    return out
 
-    from paper_1207_3392_gb300 import shard
+
+def run_batch(args):
+    """Batched Riemann set on its own line (--workload batch): `world` draws of
+    4096 problems LPT-sharded by cells x steps, no exchange between ranks."""
+    import torch
     import torch.distributed as dist
+    from paper_1207_3392_gb300 import build
 
     rank, world, local = _dist()
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     build.build()
-    # weak scaling: `world` draws of 4096 problems, LPT-sharded by cells x steps;
-    # ranks share nothing on the data path
-    all_specs = shard.weak_scaling_specs(world)
-    specs = shard.rank_specs(all_specs, rank, world)
+    all_specs, specs = _batch_specs(world, rank)
     total_cells = sum(sp.n ** sp.ndim for sp in all_specs)
-    prec = {"fp32": H.FP32_MIXED, "fp64": H.FP64, "fp64dw": H.FP64_DW}[args.precision]
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-
-    class Mesh:
-        def __init__(self, sp):
-            self.ndim, self.gamma = sp.ndim, sp.gamma
-            self.n = (sp.n, sp.n if sp.ndim == 2 else 1, 1)
-            w = P.uniform_widths(sp.n, 0.0, 1.0)
-            self.widths = [w, w][: sp.ndim]
-            self.bc_lo = self.bc_hi = (P.OUTFLOW,) * 3
-
-    b = H.Batch([Mesh(sp) for sp in specs], precision=prec, stream=stream.cuda_stream)
-    for i, sp in enumerate(specs):
-        pr = P.batch_problem(sp)
-        b.set_primitive(i, pr.rho, pr.vel, pr.p)
-    cells = sum(sp.n ** sp.ndim for sp in specs)
-    cells_nv = sum(sp.n ** sp.ndim * (sp.ndim + 2) for sp in specs)
-    if not args.no_autotune:
-        b.autotune(trial_steps=2)
-    for _ in range(max(args.warmup, 3)):
-        b.run(1, 0.5)
-    torch.cuda.synchronize()
     sampler = ClockSampler(local)
-    sampler.start()
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    b.run(args.steps, 0.5)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    clocks = sampler.stop()
-    ms = e0.elapsed_time(e1) / args.steps
+    rec = measure_batch((args.precision,), args.steps, args.warmup, stream, specs=specs,
+                        autotune=not args.no_autotune, sampler=sampler,
+                        barrier=(lambda: dist.barrier()) if world > 1 else None,
+                        scale_steps=False)[args.precision]
+    ms = rec["ms_per_step"]
     if world > 1:
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-    b.status()
-    ks = [b.profile_step(0.5) for _ in range(3)]
-    st1 = float(np.mean([k[0] for k in ks]))
-    fin = float(np.mean([k[1] for k in ks]))
-    st2 = float(np.mean([k[2] for k in ks]))
-    esz = 4 if prec == H.FP32_MIXED else 8
-    peak, peak_kind = _peaks()
-    bytes2 = 3 * esz * cells_nv
-    achieved = bytes2 / (st2 * 1e-3) / 1e9
-    info = b.tile_info()
     line = {"metric": METRIC, "value": total_cells * 2 / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None,
-            "dtype": {H.FP32_MIXED: "f32", H.FP64: "f64", H.FP64_DW: "f32x2 double-word"}[prec], "data": "synthetic",
+            "steps": rec["steps"], "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": rec["dtype"], "data": "synthetic",
             "config": {"workload": f"batched_riemann_4096_{args.precision}", "problems": len(all_specs),
-                       "cells": total_cells, "rank0_problems": len(specs), "rank0_cells": cells,
+                       "cells": total_cells, "rank0_problems": len(specs), "rank0_cells": rec["cells"],
                        "parallelism": f"{world} GPU(s), problems LPT-sharded by cells x steps, no exchange",
-                       "tile": info, "cfl": 0.5, "solver": "HLLC",
-                       "l2": f"inputs larger than L2 (state {cells_nv * esz / 1e9:.2f} GB)"},
-            "roofline": {"bound": "hbm", "kernel": "hydro_batch_kernel (stage 2)", "achieved": achieved,
-                         "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": f"{peak_kind} hbm_gbs",
-                         "traffic": None, "kernel_ms": {"stage1": st1, "finalize": fin, "stage2": st2}},
-            "clocks": clocks, "gpu_launches": 3 * args.steps}
-    b.close()
+                       "tile": rec["tile"], "cfl": 0.5, "solver": "HLLC", "l2": rec["l2"]},
+            "roofline": rec["roofline"], "clocks": rec["clocks"], "gpu_launches": rec["gpu_launches"]}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
 
 
-def run_learned(args):
+def measure_learned(steps, warmup, stream, sampler=None):
     """Learned flux correction on the 2D periodic shear layer, 256^2 FP32: one
     RK2 step = CFL reduction, and per stage the plain face fluxes and
     features, the BF16 MLP, the FCT ratios, the corrected update (plus the
@@ -585,72 +677,69 @@ def run_learned(args):
     is a seeded random one of the trained shape; the cost does not depend on
     the weights while no cell falls back."""
     import torch
-    from paper_1207_3392_gb300 import build
     from paper_1207_3392_gb300 import hydro as H
-    from paper_1207_3392_gb300 import problems as P
-
-    rank, world, local = _dist()
-    torch.cuda.set_device(local)
-    build.build()
-    stream = torch.cuda.Stream()
-    torch.cuda.set_stream(stream)
-    pr = P.kelvin_helmholtz(256, seed=64)
     from paper_1207_3392_gb300 import learned_flux as LF
+    from paper_1207_3392_gb300 import problems as P
+    pr = P.kelvin_helmholtz(256, seed=64)
     params = LF._init_params(0)
     nlast = 4 * 64 + 4                      # output layer W3, b3 (zero at initialisation)
     params[-nlast:] = np.random.default_rng(0).normal(0.0, 0.02, nlast).astype(np.float32)
     L = H.Learned(pr, params=params, stream=stream.cuda_stream)
     L.set_primitive(pr.rho, pr.vel, pr.p)
-    for _ in range(max(args.warmup, 3)):
+    for _ in range(max(warmup, 3)):
         L.advance(1, 0.5, sync=False)
     torch.cuda.synchronize()
-    sampler = ClockSampler(local)
-    sampler.start()
+    if sampler is not None:
+        sampler.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         L.advance(1, 0.5, sync=False)
     e1.record(stream)
     torch.cuda.synchronize()
-    clocks = sampler.stop()
-    ms = e0.elapsed_time(e1) / args.steps
+    clocks = sampler.stop() if sampler is not None else None
+    ms = e0.elapsed_time(e1) / steps
     fb = L.fallbacks()
     L.close()
     cells = 256 * 256
-    line = {"metric": METRIC, "value": world * cells * 2 / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16", "data": "synthetic",
-            "config": {"workload": "learned_kh2d_256^2_hllc_fct", "cells": cells, "faces": 2 * cells,
-                       "network": "24-64-64-4 SiLU, BF16 mma.sync, FP32 accumulate",
-                       "l2": "inputs smaller than L2 (state 1 MB): the step is launch- and latency-bound",
-                       "fallback_cells": fb},
-            "roofline": None, "clocks": clocks,
+    return {"value": cells * 2 / (ms * 1e-3), "ms_per_step": ms, "steps": steps, "cells": cells,
+            "network": "24-64-64-4 SiLU, BF16 mma.sync, FP32 accumulate", "fallback_cells": fb,
+            "l2": "inputs smaller than L2 (state 1 MB): the step is launch- and latency-bound",
             # per step: CFL speed + finalize, and per stage faces, MLP, FCT,
             # the update, 3 widening passes and the all-plain pass
-            "gpu_launches": args.steps * (2 + 2 * 8)}
+            "gpu_launches": steps * (2 + 2 * 8), "clocks": clocks}
+
+
+def run_learned(args):
+    import torch
+    from paper_1207_3392_gb300 import build
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    build.build()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    rec = measure_learned(args.steps, args.warmup, stream, sampler=ClockSampler(local))
+    line = {"metric": METRIC, "value": world * rec["value"], "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": rec["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16", "data": "synthetic",
+            "config": {"workload": "learned_kh2d_256^2_hllc_fct", "cells": rec["cells"], "faces": 2 * rec["cells"],
+                       "network": rec["network"], "l2": rec["l2"], "fallback_cells": rec["fallback_cells"]},
+            "roofline": None, "clocks": rec["clocks"], "gpu_launches": rec["gpu_launches"]}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
 
-def run_fmr(args):
+def measure_fmr(n, levels, precision, solver, steps, warmup, stream, autotune=True, sampler=None):
     """Point blast on nested levels (multilevel evolution with subcycling,
     Algorithms Evolve / EvolveLevel / StepLevel): `levels` boxes of n^3 cells,
     each covering the central half of its parent at twice its resolution, so
     the finest level has the resolution of a (n 2^(levels-1))^3 single-level
     mesh.  A step is one global step (2^l steps of level l)."""
     import torch
-    from paper_1207_3392_gb300 import build
     from paper_1207_3392_gb300 import hydro as H
-
-    rank, world, local = _dist()
-    torch.cuda.set_device(local)
-    build.build()
-    n = args.n if args.n != 256 else 128
-    L = args.levels
-    prec = {"fp32": H.FP32_MIXED, "fp64": H.FP64, "fp64dw": H.FP64}[args.precision]
-    stream = torch.cuda.Stream()
-    torch.cuda.set_stream(stream)
-    g = H.Fmr(3, n, L, 1.0, 1, solver=H.HLLC if args.solver != "hll" else H.HLL, precision=prec, stream=stream)
+    L = levels
+    prec = {"fp32": H.FP32_MIXED, "fp64": H.FP64, "fp64dw": H.FP64}[precision]
+    g = H.Fmr(3, n, L, 1.0, 1, solver=H.HLLC if solver != "hll" else H.HLL, precision=prec, stream=stream)
     gamma = 1.4
     for l in range(L):
         m = n + (4 if l else 0)
@@ -659,40 +748,94 @@ def run_fmr(args):
         U[4] = 1e-5 / (gamma - 1.0)
         if l == L - 1:
             o = (2 if l else 0) + n // 2 - 1
-            h = 1.0 / n / 2 ** l
-            U[4, o:o + 2, o:o + 2, o:o + 2] = 1.0 / (8 * h ** 3)
+            hh = 1.0 / n / 2 ** l
+            U[4, o:o + 2, o:o + 2, o:o + 2] = 1.0 / (8 * hh ** 3)
         g.set_level(l, U)
         del U
-    if not args.no_autotune:
+    if autotune:
         g.autotune(2)
     # warm-up; the first global step also restricts the deposit onto the covered coarse cells
-    g.step(max(args.warmup, 3), 0.3)  # also captures the two-step graph
+    g.step(max(warmup, 3), 0.3)  # also captures the two-step graph
     torch.cuda.synchronize()
-    sampler = ClockSampler(local)
-    sampler.start()
+    if sampler is not None:
+        sampler.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     lib = H.load()
-    H.check(lib.genasis_fmr_step(g._h, args.steps, 0.3, None))  # replays the captured two-step graph
+    H.check(lib.genasis_fmr_step(g._h, steps, 0.3, None))  # replays the captured two-step graph
     e1.record(stream)
     torch.cuda.synchronize()
-    clocks = sampler.stop()
-    ms = e0.elapsed_time(e1) / args.steps
+    clocks = sampler.stop() if sampler is not None else None
+    ms = e0.elapsed_time(e1) / steps
     t = g.step(0, 0.3)
     g.close()
     cells_per_step = sum(2 ** l * n ** 3 for l in range(L))
-    line = {"metric": METRIC, "value": cells_per_step * 2 / (ms * 1e-3), "unit": UNIT, "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == H.FP32_MIXED else "f64",
-            "data": "synthetic",
-            "config": {"workload": f"sedov3d_fmr_{L}x{n}^3_{args.solver}_{args.precision}", "levels": L,
-                       "cells_per_level": n ** 3, "finest_equivalent": f"{n * 2 ** (L - 1)}^3",
-                       "cell_updates_per_global_step": cells_per_step,
+    return {"value": cells_per_step * 2 / (ms * 1e-3), "ms_per_step": ms, "steps": steps, "levels": L,
+            "cells_per_level": n ** 3, "finest_equivalent": f"{n * 2 ** (L - 1)}^3",
+            "cell_updates_per_global_step": cells_per_step, "time_reached": t, "clocks": clocks,
+            "dtype": "f32" if prec == H.FP32_MIXED else "f64"}
+
+
+def run_fmr(args):
+    import torch
+    from paper_1207_3392_gb300 import build
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    build.build()
+    n = args.n if args.n != 256 else 128
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    rec = measure_fmr(n, args.levels, args.precision, args.solver, args.steps, args.warmup, stream,
+                      autotune=not args.no_autotune, sampler=ClockSampler(local))
+    line = {"metric": METRIC, "value": rec["value"], "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": rec["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": rec["dtype"], "data": "synthetic",
+            "config": {"workload": f"sedov3d_fmr_{args.levels}x{n}^3_{args.solver}_{args.precision}",
+                       "levels": args.levels, "cells_per_level": n ** 3, "finest_equivalent": rec["finest_equivalent"],
+                       "cell_updates_per_global_step": rec["cell_updates_per_global_step"],
                        "step": "one global step: 2^l RK2 steps of level l, prolongation, restriction, "
-                               "flux replacement, provisional coarse substeps", "time_reached": t},
-            "roofline": None, "clocks": clocks, "gpu_launches": None}
+                               "flux replacement, provisional coarse substeps", "time_reached": rec["time_reached"]},
+            "roofline": None, "clocks": rec["clocks"], "gpu_launches": None}
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def measure_sod(stream, n=256):
+    """The 1D benchmark case in full: Sod, 256 cells, HLLC, FP64, C_CFL 0.8,
+    from t = 0 to t = 0.2 with the device CFL step (one graph launch of all
+    steps, the last clamped to t_end).  Reports the time per RK2 step and of
+    the whole run."""
+    import torch
+    from paper_1207_3392_gb300 import hydro as H
+    from paper_1207_3392_gb300 import problems as P
+    pr = P.sod(n)
+    h = H.Hydro.from_problem(pr, precision=H.FP64, stream=stream.cuda_stream)
+    U0 = h.get_conserved()
+    # the number of steps to t_end (same rule as the timed run)
+    nsteps = 0
+    t = 0.0
+    while t < pr.t_end and nsteps < 100000:
+        t = h.advance(1, pr.cfl, pr.t_end)
+        nsteps += 1
+    for _ in range(2):  # warm-up of the nsteps-step graph
+        h.set_conserved(U0)
+        h.time = 0.0
+        h.advance(nsteps, pr.cfl, pr.t_end)
+    h.set_conserved(U0)
+    h.time = 0.0
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    h.advance(nsteps, pr.cfl, pr.t_end, sync=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    t = h.time
+    lps = h.launches_per_step()
+    h.close()
+    return {"value": n * 2 * nsteps / (ms * 1e-3), "ms_per_step": ms / nsteps, "run_ms": ms, "steps": nsteps,
+            "time_reached": t, "cells": n, "dtype": "f64", "gpu_launches": nsteps * lps,
+            "note": "a 256-cell mesh fills one CTA: the step is bound by launch and kernel latency"}
 
 
 def main():

@@ -22,18 +22,30 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIBDIR = os.path.join(_HERE, "_lib")
 _LIB = os.path.join(_LIBDIR, "libhydro_oracle.so")
 _SRC = os.path.join(_HERE, "hydro_oracle.c")
+_COUNT_LIB = os.path.join(_LIBDIR, "libopcount.so")
+_COUNT_SRC = os.path.join(_HERE, "opcount.cpp")
 
 ENONPHYS = -4
 
 
+def _stale(lib, srcs):
+    return not os.path.exists(lib) or any(os.path.getmtime(lib) < os.path.getmtime(s) for s in srcs)
+
+
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (FP contraction off so x86 and Arm agree)."""
+    """Compile the oracle with gcc (FP contraction off so x86 and Arm agree),
+    and its operation counter (opcount.cpp) with g++."""
     os.makedirs(_LIBDIR, exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    if force or _stale(_LIB, [_SRC]):
         tmp = _LIB + f".{os.getpid()}.tmp"
         subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
                                "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
+    if force or _stale(_COUNT_LIB, [_SRC, _COUNT_SRC]):
+        tmp = _COUNT_LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["g++", "-O1", "-std=c++17", "-ffp-contract=off", "-fno-fast-math",
+                               "-shared", "-fPIC", "-o", tmp, _COUNT_SRC, "-lm"])
+        os.replace(tmp, _COUNT_LIB)
     return _LIB
 
 
@@ -257,3 +269,53 @@ def l1_relative(num, ref):
     num = np.asarray(num, dtype=np.float64)
     ref = np.asarray(ref, dtype=np.float64)
     return float(np.sum(np.abs(num - ref)) / np.sum(np.abs(ref)))
+
+
+# ------------------------------------------------------------------ op counts
+_count_lib = None
+OP_KINDS = ("add", "mul", "div", "sqrt", "minmax", "abs", "total")
+
+
+def _load_count():
+    global _count_lib
+    if _count_lib is None:
+        build()
+        lib = ctypes.CDLL(_COUNT_LIB)
+        P = ctypes.c_void_p
+        lib.og_count_ops.argtypes = [ctypes.c_int, ctypes.c_int, P, P, P, P, ctypes.c_double, ctypes.c_double,
+                                     ctypes.c_int, P, ctypes.c_double, P]
+        lib.og_count_ops.restype = ctypes.c_int
+        _count_lib = lib
+    return _count_lib
+
+
+def count_ops(g: Grid, U, what, param=0.0):
+    """Floating-point operations of one oracle call on U, counted by running
+    the oracle's code with a counting scalar (opcount.cpp): what = "rhs",
+    "step" (dt = param), "cfl_dt" or "totals".  Returns {kind: count}."""
+    lib = _load_count()
+    code = {"rhs": 0, "step": 1, "cfl_dt": 2, "totals": 3}[what]
+    U, pu = _arr(U)
+    n = (ctypes.c_int * 3)(*[g.n[q] if q < g.ndim else 1 for q in range(3)])
+    w = (ctypes.c_void_p * 3)(*[g.widths[q].ctypes.data if q < g.ndim else None for q in range(3)])
+    lo = (ctypes.c_int * 3)(*g.bc_lo[:3])
+    hi = (ctypes.c_int * 3)(*g.bc_hi[:3])
+    out = (ctypes.c_longlong * 7)()
+    rc = lib.og_count_ops(code, g.ndim, n, w, lo, hi, g.gamma, g.theta, g.solver, pu, float(param), out)
+    _check(rc, f"count_ops({what})")
+    return dict(zip(OP_KINDS, list(out)))
+
+
+def count_face_flux(solver, gamma, ndim, axis, primL, primR):
+    """Operations of the oracle's face flux for primitive states (rho, v, p)."""
+    lib = _load_count()
+    nv = ndim + 2
+    W = np.zeros(2 * nv)
+    for s, pr in enumerate((primL, primR)):
+        W[s * nv:(s + 1) * nv - 1] = pr[:nv - 1]
+        W[s * nv + nv - 1] = pr[nv - 1] / (gamma - 1.0)  # e from p
+    n = (ctypes.c_int * 3)(axis, 1, 1)
+    out = (ctypes.c_longlong * 7)()
+    rc = lib.og_count_ops(4, ndim, n, None, None, None, float(gamma), 1.4, int(solver), W.ctypes.data, 0.0, out)
+    _check(rc, "count_face_flux")
+    return dict(zip(OP_KINDS, list(out)))

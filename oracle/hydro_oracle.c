@@ -696,6 +696,7 @@ int og_face_fluxes(const og_desc *d, const double *U, double *F0, double *F1, do
   double *Win = (double *)malloc(sizeof(double) * nv * ne);
   double *Wout = (double *)malloc(sizeof(double) * nv * ne);
   double *L = (double *)malloc(sizeof(double) * nv * nin);
+  unsigned char *flag = NULL;
   if (!Ue || !We || !Win || !Wout || !L) { rc = OG_ENOMEM; goto done; }
   /* the divergence is not needed, but og_rhs_grid's flags and face loops are
    * reproduced here face by face */
@@ -712,7 +713,6 @@ int og_face_fluxes(const og_desc *d, const double *U, double *F0, double *F1, do
     og_prim_from_cons(nd, u, w);
     for (int v = 0; v < nv; ++v) We[(size_t)v * ne + t] = w[v];
   }
-  unsigned char *flag = NULL;
   if (d->solver == OG_HLLC_SWITCH) {
     flag = (unsigned char *)calloc(nin, 1);
     if (!flag) { rc = OG_ENOMEM; goto done; }

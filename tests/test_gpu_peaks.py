@@ -1,0 +1,28 @@
+"""The measured vector FMA rates that the arithmetic roofline divides by:
+each within a factor of two of the GPU's nominal rate (GB300: 152 SMs x 128
+FP32 lanes x 2 x ~2 GHz ~ 80 TFLOP/s; FP64 1.25 TFLOP/s nominal)."""
+import pytest
+
+from paper_1207_3392_gb300 import hydro as H
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1207_3392_gb300 import build
+    build.build()
+
+
+def test_fma_rates_are_plausible():
+    fp64 = H.measure_fma_rate(0)
+    fp32 = H.measure_fma_rate(1)
+    fp32x2 = H.measure_fma_rate(2)
+    print(f"FMA rates: FP64 {fp64:.3f}, FP32 {fp32:.1f}, FP32 pairs {fp32x2:.1f} TFLOP/s")
+    assert 0.6 < fp64 < 2.5, fp64
+    assert 40.0 < fp32 < 160.0, fp32
+    assert 40.0 < fp32x2 < 320.0, fp32x2
+    with pytest.raises(H.HydroError):
+        H.measure_fma_rate(3)
