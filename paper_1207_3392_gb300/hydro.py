@@ -265,7 +265,7 @@ class Hydro:
 
     def centers(self, axis):
         """Geometric cell centres along `axis` measured from the origin."""
-        out = np.empty(self.n[axis])
+        out = np.empty(self.n[axis] if 0 <= axis < self.ndim else 1)
         check(load().genasis_hydro_get_centers(self._h, int(axis), out.ctypes.data))
         return out
 

@@ -15,6 +15,13 @@ from parity_util import TOL_FP32, check, oracle_run, rel_l1
 
 pytestmark = pytest.mark.gpu
 
+# Relative L1 bar of the learned step against the oracle with emulated BF16
+# rounding: one BF16 rounding decision taken differently (a tie broken by a
+# different FP32 accumulation order) changes a face correction by up to one
+# BF16 unit (2^-8 of it), far above FP32 rounding but small next to the
+# correction itself.
+TOL_BF16 = 1e-4
+
 
 @pytest.fixture(scope="module", autouse=True)
 def _cuda():
@@ -330,13 +337,14 @@ def test_set_flux_mlp_runs_the_learned_solver_on_the_handle():
     detaching it gives the plain step again."""
     pr = P.kelvin_helmholtz(48, seed=21)
     bits, th = _bf16_bits(_random_net(22, last=0.3))
+    h = H.Hydro.from_problem(pr, precision=H.FP32_MIXED)
+    U0 = h.get_conserved()
     L = H.Learned(pr, params=th)
-    L.set_primitive(pr.rho, pr.vel, pr.p)
+    L.set_conserved(U0)   # both start from the same FP32 state
     tl = L.advance(4, 0.5)
     L.step(1e-3)
     want = L.get_conserved()
     L.close()
-    h = H.Hydro.from_problem(pr, precision=H.FP32_MIXED)
     h.set_flux_mlp(bits)
     th_ = h.advance(4, 0.5)
     h.step(1e-3)
@@ -362,24 +370,28 @@ def test_set_flux_mlp_runs_the_learned_solver_on_the_handle():
 
 def test_trained_network_gains_over_the_plain_scheme():
     """What the trained correction gains: data from this solver's own runs at
-    4x the resolution (64^2 coarse from 256^2 fine, shear layer seeds 0-15,
-    every face of a snapshot every 16 coarse steps to t = 1), trained on the
-    GPU with the library's forward/backward/Adam kernels, then evaluated on
-    held-out seeds 64 and 65.  From the restricted fine state at t0 = 0.2 and
-    0.6, the learned 64^2 run (flux-corrected transport on) and the plain 64^2
-    run take the same steps; against the fine run restricted to 64^2, the
-    learned run's relative L1(rho) must be at most 0.9 x the plain run's,
-    after 1 step and after 16 steps (mean over seeds and start times)."""
+    4x the resolution (128^2 coarse from 512^2 fine, shear layer seeds 0-15,
+    half the faces of a snapshot every 16 coarse steps to t = 1), trained on
+    the GPU with the library's forward/backward/Adam kernels, then evaluated on
+    held-out seeds 64-67.  From the restricted fine state at t0 = 0.4, 0.6 and
+    0.8 (the roll-up, where the coarse mesh under-resolves the flow), the
+    learned 128^2 run (flux-corrected transport on) and the plain 128^2 run
+    take the same steps; against the fine run restricted to 128^2, the learned
+    run's relative L1(rho) must be at most 0.85 x the plain run's after 1 step
+    and after 16 steps (mean over seeds and start times), and at most 0.9 x
+    for every start time.  (In the linear phase, t0 = 0.2, the correction
+    gains nothing: the ratio is ~1.0 there.)"""
     from paper_1207_3392_gb300 import learned_flux as LF
-    X, T = LF.generate(range(16), n_coarse=64, factor=4, t_end=1.0, snap_every=16, keep_fraction=1.0, rng_seed=1)
-    assert X.shape[0] > 500_000
+    X, T = LF.generate(range(16), n_coarse=128, factor=4, t_end=1.0, snap_every=16, keep_fraction=0.5, rng_seed=1)
+    assert X.shape[0] > 5_000_000
     params, hist = LF.train(X, T, epochs=8, batch=16384, lr=2e-3, init_seed=0)
     assert hist[-1][2] < hist[0][2]
-    _, summary = LF.short_horizon(params, seeds=(64, 65), n_coarse=64, factor=4, t_starts=(0.2, 0.6),
+    _, summary = LF.short_horizon(params, seeds=(64, 65, 66, 67), n_coarse=128, factor=4, t_starts=(0.4, 0.6, 0.8),
                                   horizons=(1, 16))
     for m in (1, 16):
         rows = [r for r in summary if r["steps"] == m]
         ratio = float(np.mean([r["ratio_learned_fct"] for r in rows]))
         print(f"learned/plain L1 after {m} step(s): {ratio:.3f} "
               f"({', '.join(f'{r['ratio_learned_fct']:.3f}' for r in rows)})")
-        assert ratio <= 0.9, (m, rows)
+        assert ratio <= 0.85, (m, rows)
+        assert all(r["ratio_learned_fct"] <= 0.9 for r in rows), (m, rows)
