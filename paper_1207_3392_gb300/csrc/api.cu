@@ -2,6 +2,7 @@
 // device memory, geometry tables, launch configuration, CUDA-graph capture of
 // multi-step advances, and the tile autotuner.
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <math.h>
 #include <stdarg.h>
@@ -21,6 +22,7 @@
 #include "hydro_device.cuh"
 #include "registry.h"
 #include "stage_kernel.cuh"
+#include "stage_tma.cuh"
 #include "hydro_handle.h"
 
 namespace gh {
@@ -135,14 +137,45 @@ int upload_geometry(genasis_hydro* h, const genasis_hydro_desc* d) {
   return GENASIS_OK;
 }
 
+// A TMA variant stages 4D boxes of the FP32 state: its rows must start on
+// 16-byte boundaries, so n[0] must be a multiple of 4.
+bool tma_usable(const genasis_hydro* h) { return h->ndim == 3 && h->prec == GENASIS_FP32_MIXED && h->n[0] % 4 == 0; }
+
+// Tensor map of one FP32 state array [5][n2][n1][n0] as a 4D tensor (x, y,
+// z, variable) with the box of one plane of a TMA tile.
+int encode_state_map(CUtensorMap* m, void* base, const int* n, int box_x, int box_y) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    GH_CK(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
+    if (q != cudaDriverEntryPointSuccess || !fn) return fail(GENASIS_ECUDA, "cuTensorMapEncodeTiled not available");
+    encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  }
+  const cuuint64_t dims[4] = {(cuuint64_t)n[0], (cuuint64_t)n[1], (cuuint64_t)n[2], 5};
+  const cuuint64_t strides[3] = {(cuuint64_t)n[0] * 4, (cuuint64_t)n[0] * n[1] * 4, (cuuint64_t)n[0] * n[1] * n[2] * 4};
+  const cuuint32_t box[4] = {(cuuint32_t)box_x, (cuuint32_t)box_y, 1, 5};
+  const cuuint32_t es[4] = {1, 1, 1, 1};
+  const CUresult r = encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box, es,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(GENASIS_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return GENASIS_OK;
+}
+
 int configure(genasis_hydro* h, int tile, int kchunk_req) {
   if (tile < 0 || tile >= tile_count(h->ndim, h->prec)) return fail(GENASIS_EINVAL, "tile %d out of range", tile);
   StageVariant v1, v2;
   if (!stage_variant(h->ndim, h->prec, h->solver, 1, tile, &v1) ||
       !stage_variant(h->ndim, h->prec, h->solver, 2, tile, &v2))
     return fail(GENASIS_EINVAL, "no compiled kernel for this configuration");
+  if ((v1.tma || v2.tma) && !tma_usable(h))
+    return fail(GENASIS_EINVAL, "tile %d stages the state with TMA, which needs a 3D FP32 mesh with n[0] a multiple of 4",
+                tile);
   const int gx = (h->n[0] + v1.tx - 1) / v1.tx;
   const int gy = h->ndim == 3 ? (h->n[1] + v1.ty - 1) / v1.ty : 1;
+  const int gx2 = (h->n[0] + v2.tx - 1) / v2.tx;
+  const int gy2 = h->ndim == 3 ? (h->n[1] + v2.ty - 1) / v2.ty : 1;
   const int nm = h->ndim >= 2 ? h->n[h->ndim - 1] : 1;
   int kchunk = 1, gz = 1;
   if (h->ndim >= 2) {
@@ -182,6 +215,15 @@ int configure(genasis_hydro* h, int tile, int kchunk_req) {
   h->kchunk_req = kchunk_req;
   h->kchunk = kchunk;
   h->grid = dim3(gx, gy, gz);
+  h->grid2 = dim3(gx2, gy2, gz);
+  const StageVariant* vt = v1.tma ? &v1 : (v2.tma ? &v2 : nullptr);
+  if (vt) {
+    void* bufs[3] = {h->U[0], h->U[1], h->K};
+    for (int i = 0; i < 3; ++i) {
+      const int rc = encode_state_map(&h->tmap[i], bufs[i], h->n, vt->box_x, vt->box_y);
+      if (rc) return rc;
+    }
+  }
   for (int b = 0; b < 2; ++b)
     if (h->graph[b]) {
       cudaGraphExecDestroy(h->graph[b]);
@@ -214,15 +256,45 @@ int enqueue_flags(genasis_hydro* h, int stage) {
   return GENASIS_OK;
 }
 
+}  // namespace
+
+namespace gh {
+
+template <class T>
+int launch_stage(genasis_hydro* h, int stage, cudaStream_t st) {
+  const StageVariant& v = stage == 1 ? h->v1 : h->v2;
+  const dim3 grid = stage == 1 ? h->grid : h->grid2;
+  if constexpr (std::is_same<T, float>::value) {
+    if (v.tma) {
+      TmaStageArgs P;
+      P.A = stage_args<float>(h, stage);
+      P.map_u = h->tmap[h->cur];
+      P.map_k = h->tmap[2];
+      void* p[] = {&P};
+      GH_CK(cudaLaunchKernel(v.fn, grid, dim3(v.threads), p, v.smem, st));
+      return GENASIS_OK;
+    }
+  }
+  StageArgs<T> A = stage_args<T>(h, stage);
+  void* p[] = {&A};
+  GH_CK(cudaLaunchKernel(v.fn, grid, dim3(v.threads), p, v.smem, st));
+  return GENASIS_OK;
+}
+template int launch_stage<double>(genasis_hydro*, int, cudaStream_t);
+template int launch_stage<float>(genasis_hydro*, int, cudaStream_t);
+template int launch_stage<dw>(genasis_hydro*, int, cudaStream_t);
+
+}  // namespace gh
+
+namespace {
+
 template <class T>
 int enqueue_step_t(genasis_hydro* h, int mode, double fixed_dt, double cfl, double t_end, cudaEvent_t* ev) {
-  const dim3 block(h->v1.threads);
-  StageArgs<T> a1 = stage_args<T>(h, 1);
-  void* p1[] = {&a1};
   if (ev) GH_CK(cudaEventRecord(ev[0], h->stream));
   int rc = enqueue_flags<T>(h, 1);
   if (rc) return rc;
-  GH_CK(cudaLaunchKernel(h->v1.fn, h->grid, block, p1, h->v1.smem, h->stream));
+  rc = launch_stage<T>(h, 1, h->stream);
+  if (rc) return rc;
   if (ev) GH_CK(cudaEventRecord(ev[1], h->stream));
   FinalizeArgs F;
   F.part_speed = h->part_speed;
@@ -237,11 +309,10 @@ int enqueue_step_t(genasis_hydro* h, int mode, double fixed_dt, double cfl, doub
   F.status = h->status;
   GH_CK(launch_finalize(F, h->stream));
   if (ev) GH_CK(cudaEventRecord(ev[2], h->stream));
-  StageArgs<T> a2 = stage_args<T>(h, 2);
-  void* p2[] = {&a2};
   rc = enqueue_flags<T>(h, 2);
   if (rc) return rc;
-  GH_CK(cudaLaunchKernel(h->v2.fn, h->grid, block, p2, h->v2.smem, h->stream));
+  rc = launch_stage<T>(h, 2, h->stream);
+  if (rc) return rc;
   if (ev) GH_CK(cudaEventRecord(ev[3], h->stream));
   h->cur = 1 - h->cur;
   return GENASIS_OK;
@@ -829,8 +900,11 @@ int genasis_hydro_autotune(genasis_hydro_t h, int trial_steps, const char* cache
   int rc = GENASIS_OK;
   const int nm = h->ndim >= 2 ? h->n[h->ndim - 1] : 1;
   for (int tile = 0; tile < tile_count(h->ndim, h->prec) && !rc; ++tile) {
-    StageVariant probe;
-    if (!stage_variant(h->ndim, h->prec, h->solver, 1, tile, &probe)) continue;  // not compiled for this solver
+    StageVariant probe, probe2;
+    if (!stage_variant(h->ndim, h->prec, h->solver, 1, tile, &probe) ||
+        !stage_variant(h->ndim, h->prec, h->solver, 2, tile, &probe2))
+      continue;  // not compiled for this solver
+    if ((probe.tma || probe2.tma) && !tma_usable(h)) continue;  // TMA tile on an unaligned mesh
     std::vector<int> kcs = {0};
     if (h->ndim >= 2)
       for (int kc : {12, 16, 24, 32, 40, 48, 64})

@@ -425,13 +425,7 @@ namespace {
 
 template <class T, int NDIM, int SOLVER>
 struct FmrRun {
-  static int launch_stage(genasis_hydro* h, int stage, cudaStream_t st) {
-    StageArgs<T> A = stage_args<T>(h, stage);
-    void* p[] = {&A};
-    const StageVariant& v = stage == 1 ? h->v1 : h->v2;
-    GH_CK(cudaLaunchKernel(v.fn, h->grid, dim3(v.threads), p, v.smem, st));
-    return GENASIS_OK;
-  }
+  static int launch_stage(genasis_hydro* h, int stage, cudaStream_t st) { return gh::launch_stage<T>(h, stage, st); }
 
   static int ring_zero(genasis_fmr* f, int l) {
     genasis_hydro* h = f->lev[l];

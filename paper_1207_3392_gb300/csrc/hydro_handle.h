@@ -2,6 +2,7 @@
 // api.cu and the multilevel driver (fmr.cu).  Internal: not part of the C ABI.
 #pragma once
 
+#include <cuda.h>
 #include <string.h>
 
 #include <type_traits>
@@ -38,7 +39,9 @@ struct genasis_hydro {
   // launch configuration
   int tile = 0, kchunk_req = 0, kchunk = 1;
   gh::StageVariant v1{}, v2{};
-  dim3 grid;
+  dim3 grid, grid2;  // stage 1 / stage 2 (the two may use different tile shapes)
+  // tensor maps of U[0], U[1] and K for TMA variants (valid when v1.tma or v2.tma)
+  CUtensorMap tmap[3];
   int want_totals = 1;
   // cached graphs of `advance`, one per starting state buffer
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -104,5 +107,11 @@ inline StageArgs<T> stage_args(genasis_hydro* h, int stage) {
   for (int q = 0; q < 3; ++q) A.grad_phi[q] = (T)h->grad_phi[q];
   return A;
 }
+
+// Launch stage `stage` (1 or 2) of the handle's next step on stream st with
+// its configured variant and grid (every stage launch goes through here, so
+// that TMA variants get their tensor maps).
+template <class T>
+int launch_stage(genasis_hydro* h, int stage, cudaStream_t st);
 
 }  // namespace gh

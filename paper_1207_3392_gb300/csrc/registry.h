@@ -12,6 +12,8 @@ struct StageVariant {
   size_t smem;         // dynamic shared memory per CTA (bytes)
   int tx, ty;          // tile shape in cells
   int threads;         // threads per CTA
+  int tma = 0;         // 1: takes TmaStageArgs (state planes staged by TMA), see stage_tma.cuh
+  int box_x = 0, box_y = 0;  // TMA box of one plane (cells along x and y)
 };
 
 // Tile shapes compiled per dimensionality and precision (GENASIS_FP64,
@@ -27,6 +29,7 @@ bool stage_variant_1d(bool fp64, int solver, int stage, int tile, StageVariant* 
 bool stage_variant_2d(bool fp64, int solver, int stage, int tile, StageVariant* out);
 bool stage_variant_3d_f32(int solver, int stage, int tile, StageVariant* out);
 bool stage_variant_3d_f32_wide(int solver, int stage, int tile, StageVariant* out);
+bool stage_variant_3d_f32_tma(int solver, int stage, int tile, StageVariant* out);
 bool stage_variant_3d_f64(int solver, int stage, int tile, StageVariant* out);
 int tile_count_1d();
 int tile_count_2d();
