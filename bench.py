@@ -834,8 +834,12 @@ def measure_sod(stream, n=256):
     lps = h.launches_per_step()
     h.close()
     return {"value": n * 2 * nsteps / (ms * 1e-3), "ms_per_step": ms / nsteps, "run_ms": ms, "steps": nsteps,
-            "time_reached": t, "cells": n, "dtype": "f64", "gpu_launches": nsteps * lps,
-            "note": "a 256-cell mesh fills one CTA: the step is bound by launch and kernel latency"}
+            "time_reached": t, "cells": n, "dtype": "f64",
+            # launches_per_step() == 1: the whole advance call is one cooperative launch
+            "gpu_launches": 1 if lps == 1 else nsteps * lps,
+            "launch": ("one cooperative launch for all steps (one CTA per 31-cell tile, grid barriers between "
+                       "phases)") if lps == 1 else f"{lps} launches per step",
+            "note": "the step is bound by latency and by each SM's FP64 rate, not by the 256 cells' bytes"}
 
 
 def main():

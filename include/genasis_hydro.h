@@ -190,6 +190,15 @@ int genasis_hydro_autotune(genasis_hydro_t h, int trial_steps, const char *cache
  * with genasis_hydro_get_step_totals); 0 skips that work.  Returns EINVAL for
  * an unknown option or value. */
 #define GENASIS_OPT_STEP_TOTALS 1
+/* GENASIS_OPT_ONE_LAUNCH: 1 (default) runs genasis_hydro_step and
+ * genasis_hydro_advance of a 1D FP64 or FP32-mixed HLL/HLLC mesh of at most
+ * 4088 cells as one cooperative kernel launch (one CTA per tile, bounded grid
+ * barriers between the phases) for all the steps of the call
+ * (the same tile arithmetic and dt fold as the three launches per step, so
+ * bitwise the same states, dt and time; the step totals sum the cells in
+ * tiles of another width and agree to rounding); 0 keeps three launches per
+ * step. */
+#define GENASIS_OPT_ONE_LAUNCH 2
 int genasis_hydro_set_option(genasis_hydro_t h, int option, int value);
 /* External force of a linear potential Phi = grad_phi . x (the uniform force
  * of the Rayleigh-Taylor test, Sec. 4.3.2): each stage adds the source

@@ -288,6 +288,61 @@ template int launch_stage<dw>(genasis_hydro*, int, cudaStream_t);
 
 namespace {
 
+// Small 1D meshes: every step of a call in one cooperative launch of one CTA
+// per tile (kern_1d_advance.cu): 32 threads (31 cells) per CTA in FP64, so
+// the FP64 work spreads over as many SMs as possible (an SM retires ~2 FP64
+// operations per clock), 256 (255 cells) in FP32.
+constexpr int ADV1D_MAX_CELLS = 4088;
+constexpr size_t ADV1D_BYTES = 2048;  // 2 barrier words, then (at 256 B) one double per CTA
+
+bool use_1d_advance(const genasis_hydro* h) {
+  return h->one_launch && h->ndim == 1 && (h->prec == GENASIS_FP64 || h->prec == GENASIS_FP32_MIXED) &&
+         (h->solver == GENASIS_HLL || h->solver == GENASIS_HLLC) && h->n[0] <= ADV1D_MAX_CELLS;
+}
+
+template <class T>
+int launch_1d_advance_t(genasis_hydro* h, int nsteps, int mode, double cfl, double fixed_dt, double t_end) {
+  const int tx = sizeof(T) == 8 ? 32 : 256;
+  size_t smem = 0;
+  const void* fn = advance_1d_kernel(sizeof(T) == 8, h->solver, tx, &smem);
+  if (!fn) return fail(GENASIS_EINVAL, "no compiled one-launch kernel for this configuration");
+  if (smem > 48 * 1024) GH_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (!h->adv) GH_CK(cudaMalloc(&h->adv, ADV1D_BYTES));
+  // barrier words start at zero in every launch (even after one that gave up)
+  GH_CK(cudaMemsetAsync(h->adv, 0, 2 * sizeof(unsigned), h->stream));
+  StageArgs<T> A = stage_args<T>(h, 1);
+  A.k1 = (const T*)h->K;
+  A.kchunk = 1;
+  const int ntiles = (h->n[0] + tx - 2) / (tx - 1);
+  if ((size_t)ntiles * sizeof(double) > ADV1D_BYTES - 256) return fail(GENASIS_EINVAL, "mesh too large for one launch");
+  FinalizeArgs F;
+  memset(&F, 0, sizeof(F));
+  F.part_speed = h->part_speed;
+  F.part_tot = h->want_totals ? h->part_tot : nullptr;
+  F.nblk = ntiles;
+  F.nv = h->nv;
+  F.mode = mode;
+  F.cfl = cfl;
+  F.fixed_dt = fixed_dt;
+  F.t_end = t_end;
+  F.scal = h->scal;
+  F.status = h->status;
+  T* ua = (T*)h->U[h->cur];
+  T* ub = (T*)h->U[1 - h->cur];
+  unsigned* bar = h->adv;
+  double* dts = (double*)((char*)h->adv + 256);
+  void* args[] = {&A, &F, &nsteps, &ua, &ub, &bar, &dts};
+  // cooperative: the CTAs wait on one another, so all must be resident
+  GH_CK(cudaLaunchCooperativeKernel(fn, dim3(ntiles), dim3(tx), args, smem, h->stream));
+  h->cur ^= nsteps & 1;
+  return GENASIS_OK;
+}
+
+int launch_1d_advance(genasis_hydro* h, int nsteps, int mode, double cfl, double fixed_dt, double t_end) {
+  return h->prec == GENASIS_FP64 ? launch_1d_advance_t<double>(h, nsteps, mode, cfl, fixed_dt, t_end)
+                                 : launch_1d_advance_t<float>(h, nsteps, mode, cfl, fixed_dt, t_end);
+}
+
 template <class T>
 int enqueue_step_t(genasis_hydro* h, int mode, double fixed_dt, double cfl, double t_end, cudaEvent_t* ev) {
   if (ev) GH_CK(cudaEventRecord(ev[0], h->stream));
@@ -441,6 +496,7 @@ int export_array(genasis_hydro* h, void* U, int precision) {
 
 int free_all(genasis_hydro* h) {
   if (h->batch) genasis_batch_destroy(h->batch);
+  cudaFree(h->adv);
   if (h->lf) genasis_learned_destroy(h->lf);
   if (h->stream) cudaStreamSynchronize(h->stream);
   for (int b = 0; b < 2; ++b)
@@ -637,6 +693,7 @@ int genasis_hydro_step(genasis_hydro_t h, double dt) {
   if (!h) return fail(GENASIS_EINVAL, "NULL handle");
   if (!(dt > 0.0) || !isfinite(dt)) return fail(GENASIS_EINVAL, "dt must be positive and finite");
   if (h->lf) return learned_run_on(h->lf, h->U[h->cur], h->scal + SCAL_T, h->status, 0, 0.0, 0.0, dt);
+  if (use_1d_advance(h)) return launch_1d_advance(h, 1, FIN_FIXED, 0.0, dt, 0.0);
   return enqueue_step(h, FIN_FIXED, dt, 0.0, 0.0);
 }
 
@@ -647,6 +704,9 @@ int genasis_hydro_advance(genasis_hydro_t h, int nsteps, double cfl, double t_en
   if (!(cfl > 0.0)) return fail(GENASIS_EINVAL, "cfl must be > 0");
   if (h->lf && nsteps > 0) {
     int rc = learned_run_on(h->lf, h->U[h->cur], h->scal + SCAL_T, h->status, nsteps, cfl, t_end, 0.0);
+    if (rc) return rc;
+  } else if (nsteps > 0 && use_1d_advance(h)) {
+    int rc = launch_1d_advance(h, nsteps, FIN_CFL, cfl, 0.0, t_end);
     if (rc) return rc;
   } else if (nsteps > 0) {
     const int cur0 = h->cur;
@@ -760,6 +820,11 @@ int genasis_hydro_set_option(genasis_hydro_t h, int option, int value) {
     }
     return GENASIS_OK;
   }
+  if (option == GENASIS_OPT_ONE_LAUNCH) {
+    if (value != 0 && value != 1) return fail(GENASIS_EINVAL, "GENASIS_OPT_ONE_LAUNCH takes 0 or 1");
+    h->one_launch = value;
+    return GENASIS_OK;
+  }
   return fail(GENASIS_EINVAL, "unknown option %d", option);
 }
 
@@ -835,6 +900,7 @@ int genasis_hydro_restrict(genasis_hydro_t h, int factor, float* U_coarse) {
 int genasis_hydro_launches_per_step(genasis_hydro_t h) {
   GH_SINGLE_MESH(h);
   if (!h) return fail(GENASIS_EINVAL, "NULL handle");
+  if (use_1d_advance(h)) return 1;  // one launch covers all the steps of a call
   return h->solver == GENASIS_HLLC_SWITCH ? 5 : 3;
 }
 
@@ -906,6 +972,9 @@ int genasis_hydro_autotune(genasis_hydro_t h, int trial_steps, const char* cache
       continue;  // not compiled for this solver
     if ((probe.tma || probe2.tma) && !tma_usable(h)) continue;  // TMA tile on an unaligned mesh
     std::vector<int> kcs = {0};
+    if (h->ndim == 2)  // small 2D meshes need short chunks to fill the GPU
+      for (int kc : {2, 4, 8})
+        if (kc < nm) kcs.push_back(kc);
     if (h->ndim >= 2)
       for (int kc : {12, 16, 24, 32, 40, 48, 64})
         if (kc < nm) kcs.push_back(kc);

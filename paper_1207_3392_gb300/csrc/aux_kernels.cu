@@ -2,6 +2,7 @@
 // from primitives, precision conversion, the standalone CFL and totals
 // reductions, and the single-CTA finalisation of dt and totals.
 #include "aux_kernels.h"
+#include "finalize.cuh"
 #include "hydro_device.cuh"
 
 namespace gh {
@@ -117,43 +118,16 @@ __global__ void totals_kernel(ReduceArgs<T> A) {
 //   mode FIN_REDUCE: only store dt_CFL and totals
 // With t_end > 0 the step is clamped so that t never passes t_end.  No CTA
 // waits for another: the last one to take a ticket does the fold.
-namespace {
-// Fixed butterfly over the warp: every lane ends with the same sum / max.
-__device__ __forceinline__ void fold_warp(double (&s)[5], unsigned long long& m) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-    for (int v = 0; v < 5; ++v) s[v] += __shfl_xor_sync(0xffffffffu, s[v], o);
-    const unsigned long long b = __shfl_xor_sync(0xffffffffu, m, o);
-    m = b > m ? b : m;
-  }
-}
-}  // namespace
-
 __global__ void __launch_bounds__(32) finalize_kernel(FinalizeArgs A) {
-  constexpr unsigned long long SIGNLESS = 0x7fffffffffffffffull;  // a -0.0 compares as +0.0
   static_assert(FIN_CTAS <= 32, "one slice result per lane in the last fold");
   const int lane = threadIdx.x, g = blockIdx.x;
   double* work = A.scal + SCAL_COUNT;  // [FIN_CTAS][6]: totals 0..4, speed bits 5
   unsigned* ticket = reinterpret_cast<unsigned*>(A.scal + SCAL_COUNT + FIN_CTAS * 6);
-  const bool tot = A.part_tot != nullptr, spd = A.part_speed != nullptr;
   const int G = gridDim.x;
   const long long lo = (long long)A.nblk * g / G, hi = (long long)A.nblk * (g + 1) / G;
-  double s[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-  unsigned long long mb = 0;
-#pragma unroll 8
-  for (long long i = lo + lane; i < hi; i += 32) {
-    if (tot) {
-#pragma unroll
-      for (int v = 0; v < 5; ++v)
-        if (v < A.nv) s[v] += A.part_tot[i * A.nv + v];
-    }
-    if (spd) {
-      const unsigned long long b = (unsigned long long)__double_as_longlong(A.part_speed[i]) & SIGNLESS;
-      mb = b > mb ? b : mb;
-    }
-  }
-  fold_warp(s, mb);
+  double s[5];
+  unsigned long long mb;
+  fin::fold_slice(A, lo, hi, lane, s, mb);
   if (G > 1) {
     // lane 0 publishes the slice, then takes a ticket
     unsigned t = 0;
@@ -170,34 +144,9 @@ __global__ void __launch_bounds__(32) finalize_kernel(FinalizeArgs A) {
 #pragma unroll
     for (int v = 0; v < 5; ++v) s[v] = lane < G ? __ldcg(work + lane * 6 + v) : 0.0;
     mb = lane < G ? (unsigned long long)__double_as_longlong(__ldcg(work + lane * 6 + 5)) : 0ull;
-    fold_warp(s, mb);
+    fin::fold_warp(s, mb);
   }
-  if (tot && lane < A.nv) {
-    double tv = s[0];
-#pragma unroll
-    for (int v = 1; v < 5; ++v) tv = lane == v ? s[v] : tv;
-    A.scal[SCAL_TOT + lane] = tv;
-  }
-  const double mx = __longlong_as_double((long long)mb);
-  if (lane == 0) {
-    const double m = mx;
-    *ticket = 0;  // for the next launch on this scalar block
-    if (A.part_speed) A.scal[SCAL_DTCFL] = 1.0 / m;
-    if (A.mode != FIN_REDUCE) {
-      double dt = A.mode == FIN_CFL ? A.cfl * (1.0 / m) : A.fixed_dt;
-      const double t = A.scal[SCAL_T];
-      if (A.t_end > 0.0) {
-        if (t + dt > A.t_end) dt = A.t_end - t;
-        if (!(dt > 0.0)) dt = 0.0;
-      }
-      if (!(dt >= 0.0) || !(dt < INFINITY)) {
-        atomicOr(A.status, STATUS_NONPHYS);
-        dt = 0.0;
-      }
-      A.scal[SCAL_DT] = dt;
-      A.scal[SCAL_T] = t + dt;
-    }
-  }
+  fin::finish(A, s, mb, lane);
 }
 
 // Shock detector of the HLLC -> HLL switch (Sec. 3.2 describes the switch, not

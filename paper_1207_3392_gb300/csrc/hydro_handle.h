@@ -43,6 +43,8 @@ struct genasis_hydro {
   // tensor maps of U[0], U[1] and K for TMA variants (valid when v1.tma or v2.tma)
   CUtensorMap tmap[3];
   int want_totals = 1;
+  int one_launch = 1;  // small 1D meshes: a whole advance in one cooperative launch
+  unsigned* adv = nullptr;  // its grid-barrier words [2] (zero between launches), then one dt per CTA
   // cached graphs of `advance`, one per starting state buffer
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   int g_nsteps = -1;

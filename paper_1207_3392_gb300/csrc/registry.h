@@ -32,6 +32,10 @@ bool stage_variant_3d_f32_wide(int solver, int stage, int tile, StageVariant* ou
 bool stage_variant_3d_f32_tma(int solver, int stage, int tile, StageVariant* out);
 bool stage_variant_3d_f64(int solver, int stage, int tile, StageVariant* out);
 int tile_count_1d();
+// One-launch advance of small 1D meshes (kern_1d_advance.cu): the
+// kernel for (precision, solver) on tx threads and its dynamic shared memory,
+// or nullptr if not compiled.
+const void* advance_1d_kernel(bool fp64, int solver, int tx, size_t* smem);
 int tile_count_2d();
 int tile_count_3d_f32();
 int tile_count_3d_f64();

@@ -59,8 +59,15 @@ struct StageArgs {
 
 // PRE pays in 3D, where both in-plane axes would form every slope twice; in
 // 1D/2D one axis gains less than the extra barrier costs.
-template <int NDIM, class T, int SOLVER, int STAGE, int TX, int TY, bool PRE = (NDIM == 3)>
+// COH: the state arrays may have been written earlier in the same launch (the
+// one-launch advance of small 1D meshes), so they are read through L2 (__ldcg), which
+// is coherent, instead of the read-only cache (__ldg).  Same values either way.
+template <int NDIM, class T, int SOLVER, int STAGE, int TX, int TY, bool PRE = (NDIM == 3), bool COH = false>
 struct StageKernel {
+  static __device__ __forceinline__ T ld(const T* p) {
+    if constexpr (COH) return __ldcg(p);
+    else return __ldg(p);
+  }
   static constexpr int NV = NDIM + 2;
   static constexpr bool SW = SOLVER == SOLVER_HLLC_SW;  // per-face HLLC/HLL choice from shock bits
   static constexpr bool MARCH = NDIM >= 2;
@@ -149,8 +156,8 @@ struct StageKernel {
     T u[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      T x = __ldg(A.un + v * vs + c);
-      if (STAGE == 2) x = fma(dt, __ldg(A.k1 + v * vs + c), x);
+      T x = ld(A.un + v * vs + c);
+      if (STAGE == 2) x = fma(dt, ld(A.k1 + v * vs + c), x);
       u[v] = x;
     }
     if (r.fa) u[1] = -u[1];
@@ -561,13 +568,13 @@ struct StageKernel {
           if (A.want_totals) {
             const T dm_hi = MARCH ? A.wdh[AM][m] : T(1), dm_lo = MARCH ? A.wdl[AM][m] : T(0);
 #pragma unroll
-            for (int v = 0; v < NV; ++v) tcol[v].add_product(__ldg(A.un + v * vs + c), dm_hi, dm_lo);
+            for (int v = 0; v < NV; ++v) tcol[v].add_product(ld(A.un + v * vs + c), dm_hi, dm_lo);
           }
         } else {
           const T hdt = T(0.5) * dt;
 #pragma unroll
           for (int v = 0; v < NV; ++v) {
-            const T u0 = __ldg(A.un + v * vs + c), k = __ldg(A.k1 + v * vs + c);
+            const T u0 = ld(A.un + v * vs + c), k = ld(A.k1 + v * vs + c);
             A.out[v * vs + c] = fma(hdt, add_rn(k, L[v]), u0);
           }
         }

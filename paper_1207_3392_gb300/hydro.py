@@ -21,6 +21,7 @@ HLL, HLLC, HLLC_SWITCH = 0, 1, 2  # HLLC_SWITCH: HLLC with HLL transverse to sho
 BC_PERIODIC, BC_REFLECT, BC_OUTFLOW = 0, 1, 2
 FP64, FP32_MIXED, FP64_DW = 0, 1, 2  # FP64_DW: double-word FP32 pairs on the device, FP64 on the host
 OPT_STEP_TOTALS = 1
+OPT_ONE_LAUNCH = 2
 
 
 class HydroError(RuntimeError):
@@ -331,6 +332,10 @@ class Hydro:
 
     def set_step_totals(self, enabled):
         check(load().genasis_hydro_set_option(self._h, OPT_STEP_TOTALS, int(bool(enabled))))
+
+    def set_one_launch(self, enabled):
+        """Small 1D meshes: all steps of a call in one cooperative launch (default on)."""
+        check(load().genasis_hydro_set_option(self._h, OPT_ONE_LAUNCH, int(bool(enabled))))
 
     def status(self):
         return check(load().genasis_hydro_status(self._h))

@@ -42,6 +42,30 @@ def test_sod_1d_full_run(solver):
         _check(Ug, Uo, 1, tol, f"sod prec={precision}")
 
 
+@pytest.mark.parametrize("n", [256, 1500])
+@pytest.mark.parametrize("precision", [H.FP64, H.FP32_MIXED])
+def test_one_launch_1d_advance_is_the_multi_launch_advance(n, precision):
+    """Small 1D meshes run every step of an advance (and a fixed-dt step) in
+    one cooperative launch: bitwise the states and time of the three launches
+    per step, on one tile (256 cells) and on three (1500), in a run clamped
+    to its end time.  The step totals sum the same cells in tiles of another
+    width, so they agree to rounding."""
+    pr = P.sod(n, t_end=0.1)
+    out = []
+    for one in (True, False):
+        h = H.Hydro.from_problem(pr, precision=precision)
+        h.set_one_launch(one)
+        assert h.launches_per_step() == (1 if one else 3)
+        t = h.evolve(pr.cfl, pr.t_end, chunk=17)
+        h.step(1e-4)
+        out.append((h.get_conserved(), t, h.time, h.step_totals()))
+        h.close()
+    (ua, ta, t2a, sa), (ub, tb, t2b, sb) = out
+    np.testing.assert_array_equal(ua, ub)
+    assert ta == tb == pytest.approx(0.1, rel=1e-14) and t2a == t2b
+    np.testing.assert_allclose(sa, sb, rtol=1e-12)
+
+
 @pytest.mark.parametrize("solver", [H.HLL, H.HLLC])
 @pytest.mark.parametrize("bc", [P.PERIODIC, P.REFLECT, P.OUTFLOW])
 def test_random_blocks_2d(solver, bc):
