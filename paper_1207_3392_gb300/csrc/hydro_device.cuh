@@ -107,11 +107,31 @@ __device__ __forceinline__ T limited_slope(T wm, T wc, T wp, const Geo<T>& g) {
 }
 
 // Division, reciprocal and square root used by the flux arithmetic.  FP64
-// keeps IEEE operations (its parity bar is 1e-10); FP32 uses the hardware
-// approximations (a few ulp, far inside its 1e-5 bar).
-__device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
+// takes Newton reciprocals from an FP32 seed (a few ulp, far inside its 1e-10
+// parity bar); FP32 uses the hardware approximations (a few ulp, far inside
+// its 1e-5 bar).
+// FP64 reciprocal by Newton's method for 1/x: the FP32 hardware approximation
+// as the seed (relative error ~2^-22), then two steps r <- r + r (1 - x r),
+// each of which squares the relative error (~2^-44, then the FP64 rounding
+// level): four FP64 FMAs in place of an IEEE division on GB300's slow FP64
+// pipe, within a few ulp.  Arguments whose exponent lies outside the normal
+// FP32 range (and 0, infinities, NaN) take the IEEE division; the test is on
+// the exponent bits, on the integer pipe.
+__device__ __forceinline__ double frcp(double x) {
+  const unsigned ex = (unsigned)((unsigned long long)__double_as_longlong(x) >> 52) & 0x7ffu;
+  if (ex - 900u > 246u) return 1.0 / x;  // biased exponent outside [900, 1146] (|x| ~ 1e-37 .. 1e37)
+  double r = (double)__fdividef(1.0f, (float)x);
+  r = fma(r, fma(-x, r, 1.0), r);
+  r = fma(r, fma(-x, r, 1.0), r);
+  return r;
+}
+// a / b from the reciprocal and one residual correction q + r (a - b q).
+__device__ __forceinline__ double fdiv(double a, double b) {
+  const double r = frcp(b);
+  const double q = a * r;
+  return fma(r, fma(-b, q, a), q);
+}
 __device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
-__device__ __forceinline__ double frcp(double x) { return 1.0 / x; }
 __device__ __forceinline__ float frcp(float x) { return __fdividef(1.0f, x); }
 // Correctly rounded sum that the compiler may not fuse with a product feeding
 // it: keeps the stage combine bitwise the same in every kernel that inlines it,
@@ -158,7 +178,7 @@ __device__ __forceinline__ double sound_speed(double gamma, double p, double n) 
 template <int NDIM>
 __device__ __forceinline__ void recover(const double (&u)[NDIM + 2], double (&w)[NDIM + 2]) {
   constexpr int NV = NDIM + 2;
-  const double rn = 1.0 / u[0];
+  const double rn = frcp(u[0]);
   double v2 = 0.0;
   w[0] = u[0];
 #pragma unroll
