@@ -673,9 +673,11 @@ def measure_learned(steps, warmup, stream, sampler=None):
     """Learned flux correction on the 2D periodic shear layer, 256^2 FP32: one
     RK2 step = CFL reduction, and per stage the plain face fluxes and
     features, the BF16 MLP, the FCT ratios, the corrected update (plus the
-    fallback passes, which return at once when no cell failed).  The network
-    is a seeded random one of the trained shape; the cost does not depend on
-    the weights while no cell falls back."""
+    fallback passes, which run only when a cell failed).  By default a step
+    (one advance call) is one cooperative launch; the per-phase launches
+    (a CUDA graph of 18 kernels) are timed beside it.  The network is a seeded
+    random one of the trained shape; the cost does not depend on the weights
+    while no cell falls back."""
     import torch
     from paper_1207_3392_gb300 import hydro as H
     from paper_1207_3392_gb300 import learned_flux as LF
@@ -684,30 +686,39 @@ def measure_learned(steps, warmup, stream, sampler=None):
     params = LF._init_params(0)
     nlast = 4 * 64 + 4                      # output layer W3, b3 (zero at initialisation)
     params[-nlast:] = np.random.default_rng(0).normal(0.0, 0.02, nlast).astype(np.float32)
-    L = H.Learned(pr, params=params, stream=stream.cuda_stream)
-    L.set_primitive(pr.rho, pr.vel, pr.p)
-    for _ in range(max(warmup, 3)):
-        L.advance(1, 0.5, sync=False)
-    torch.cuda.synchronize()
-    if sampler is not None:
-        sampler.start()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(steps):
-        L.advance(1, 0.5, sync=False)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    clocks = sampler.stop() if sampler is not None else None
-    ms = e0.elapsed_time(e1) / steps
-    fb = L.fallbacks()
-    L.close()
+
+    def timed(one_launch, smp):
+        L = H.Learned(pr, params=params, stream=stream.cuda_stream)
+        L.set_one_launch(one_launch)
+        L.set_primitive(pr.rho, pr.vel, pr.p)
+        for _ in range(max(warmup, 3)):
+            L.advance(1, 0.5, sync=False)
+        torch.cuda.synchronize()
+        if smp is not None:
+            smp.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            L.advance(1, 0.5, sync=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        clk = smp.stop() if smp is not None else None
+        ms = e0.elapsed_time(e1) / steps
+        res = (ms, L.fallbacks(), L.launches_per_step(), clk)
+        L.close()
+        return res
+
+    ms_pp, _, lps_pp, _ = timed(False, None)
+    ms, fb, lps, clocks = timed(True, sampler)
     cells = 256 * 256
     return {"value": cells * 2 / (ms * 1e-3), "ms_per_step": ms, "steps": steps, "cells": cells,
             "network": "24-64-64-4 SiLU, BF16 mma.sync, FP32 accumulate", "fallback_cells": fb,
             "l2": "inputs smaller than L2 (state 1 MB): the step is launch- and latency-bound",
-            # per step: CFL speed + finalize, and per stage faces, MLP, FCT,
-            # the update, 3 widening passes and the all-plain pass
-            "gpu_launches": steps * (2 + 2 * 8), "clocks": clocks}
+            "launch": ("one cooperative launch per advance call (persistent grid, 7 grid barriers a step)"
+                       if lps == 1 else f"{lps} launches per step"),
+            "per_phase_ms_per_step": ms_pp, "per_phase_launches_per_step": lps_pp,
+            # one advance call per step
+            "gpu_launches": steps * lps, "clocks": clocks}
 
 
 def run_learned(args):
@@ -723,7 +734,8 @@ def run_learned(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": rec["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16", "data": "synthetic",
             "config": {"workload": "learned_kh2d_256^2_hllc_fct", "cells": rec["cells"], "faces": 2 * rec["cells"],
-                       "network": rec["network"], "l2": rec["l2"], "fallback_cells": rec["fallback_cells"]},
+                       "network": rec["network"], "l2": rec["l2"], "fallback_cells": rec["fallback_cells"],
+                       "launch": rec["launch"], "per_phase_ms_per_step": rec["per_phase_ms_per_step"]},
             "roofline": None, "clocks": rec["clocks"], "gpu_launches": rec["gpu_launches"]}
     if rank == 0:
         print(json.dumps(line), flush=True)

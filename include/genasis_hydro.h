@@ -197,7 +197,8 @@ int genasis_hydro_autotune(genasis_hydro_t h, int trial_steps, const char *cache
  * (the same tile arithmetic and dt fold as the three launches per step, so
  * bitwise the same states, dt and time; the step totals sum the cells in
  * tiles of another width and agree to rounding); 0 keeps three launches per
- * step. */
+ * step.  With a network attached (genasis_hydro_set_flux_mlp) the option is
+ * passed on to its corrected scheme (genasis_learned_set_option). */
 #define GENASIS_OPT_ONE_LAUNCH 2
 int genasis_hydro_set_option(genasis_hydro_t h, int option, int value);
 /* External force of a linear potential Phi = grad_phi . x (the uniform force
@@ -341,6 +342,18 @@ int genasis_learned_advance(genasis_learned_t l, int nsteps, double cfl, double 
 int genasis_learned_step(genasis_learned_t l, double dt);
 /* Cells whose corrected update fell back to the plain flux, cumulative. */
 int genasis_learned_fallbacks(genasis_learned_t l, long long *cells);
+/* GENASIS_OPT_ONE_LAUNCH: 1 (default) runs genasis_learned_advance and
+ * genasis_learned_step as one cooperative kernel launch for all the steps of
+ * the call (a persistent grid of CTAs that meet at bounded grid barriers
+ * between the phases; a barrier that waits about a second sets the timeout
+ * status and ends the launch).  The face, network and cell arithmetic is that
+ * of the per-phase launches, so states, dt, time and fallback counts are
+ * bitwise the same.  0 keeps the per-phase launches (a CUDA graph per call
+ * shape).  Returns EINVAL for another option or value. */
+int genasis_learned_set_option(genasis_learned_t l, int option, int value);
+/* Kernel launches one step takes: 1 when one launch covers all the steps of a
+ * call, else the per-phase count (2 + 2 x 8 with a network and FCT). */
+int genasis_learned_launches_per_step(genasis_learned_t l);
 /* Training support on a periodic mesh, device pointers, compact face order
  * f = (axis * ny + j) * nx + i (face (i, j) of axis 0 lies between cells
  * (i-1, j) and (i, j)):

@@ -823,6 +823,7 @@ int genasis_hydro_set_option(genasis_hydro_t h, int option, int value) {
   if (option == GENASIS_OPT_ONE_LAUNCH) {
     if (value != 0 && value != 1) return fail(GENASIS_EINVAL, "GENASIS_OPT_ONE_LAUNCH takes 0 or 1");
     h->one_launch = value;
+    if (h->lf) return genasis_learned_set_option(h->lf, option, value);
     return GENASIS_OK;
   }
   return fail(GENASIS_EINVAL, "unknown option %d", option);
@@ -901,6 +902,10 @@ int genasis_hydro_launches_per_step(genasis_hydro_t h) {
   GH_SINGLE_MESH(h);
   if (!h) return fail(GENASIS_EINVAL, "NULL handle");
   if (use_1d_advance(h)) return 1;  // one launch covers all the steps of a call
+  if (h->lf) {  // the corrected scheme, and the kernel that passes its status back
+    const int n = genasis_learned_launches_per_step(h->lf);
+    return n < 0 ? n : n + 1;
+  }
   return h->solver == GENASIS_HLLC_SWITCH ? 5 : 3;
 }
 

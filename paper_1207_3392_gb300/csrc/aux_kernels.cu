@@ -37,29 +37,11 @@ __global__ void convert_kernel(size_t count, const Tin* __restrict__ in, Tout* _
 // cell's CFL time (Eq. courantTimeStep).
 template <class T, int NDIM>
 __global__ void speed_kernel(ReduceArgs<T> A) {
-  constexpr int NV = NDIM + 2;
   __shared__ double red[32];
   double best = 0.0;
   bool bad = false;
-  const T gm1 = (T)(A.gamma - 1.0), gamma = (T)A.gamma;
-  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < A.ncell; c += (size_t)gridDim.x * blockDim.x) {
-    T u[NV], w[NV];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) u[v] = A.U[v * A.ncell + c];
-    recover<NDIM>(u, w);
-    const T p = gm1 * w[NV - 1];
-    bad |= !(w[0] > T(0)) || !(p > T(0));
-    const T cs = sqrt(gamma * p / w[0]);
-    size_t r = c;
-    T s = T(0);
-#pragma unroll
-    for (int q = 0; q < NDIM; ++q) {
-      const size_t i = r % A.n[q];
-      r /= A.n[q];
-      s = fmax(s, (fabs(w[1 + q]) + cs) * A.iw[q][i + 2]);
-    }
-    best = fmax(best, (double)s);
-  }
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < A.ncell; c += (size_t)gridDim.x * blockDim.x)
+    best = fmax(best, (double)fin::cell_speed<T, NDIM, false>(A, c, bad));
   if (bad) atomicOr(A.status, STATUS_NONPHYS);
   best = warp_max(best);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = best;

@@ -1,7 +1,7 @@
-// finalize.cuh -- the fixed-order fold of the per-CTA reduction partials and
-// the time-step update (Eq. courantTimeStep x C_CFL), shared by the finalize
-// kernel and the persistent single-CTA advance of small 1D meshes, so that
-// both give bitwise the same dt, time and totals.
+// finalize.cuh -- the per-cell CFL speed, the fixed-order fold of the per-CTA
+// reduction partials and the time-step update (Eq. courantTimeStep x C_CFL),
+// shared by the speed and finalize kernels and the one-launch advances, so
+// that all give bitwise the same dt, time and totals.
 #pragma once
 
 #include "aux_kernels.h"
@@ -9,6 +9,35 @@
 
 namespace gh {
 namespace fin {
+
+// Inverse CFL time of cell c, max_q (|v_q| + c_s) / dq (Eq. courantTimeStep),
+// from the state A.U (read through L2 when COH: the one-launch advances read
+// states written earlier in the same launch); bad is set for rho <= 0 or
+// p <= 0.
+template <class T, int NDIM, bool COH>
+__device__ __forceinline__ T cell_speed(const ReduceArgs<T>& A, size_t c, bool& bad) {
+  constexpr int NV = NDIM + 2;
+  const T gm1 = (T)(A.gamma - 1.0), gamma = (T)A.gamma;
+  T u[NV], w[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    if constexpr (COH) u[v] = __ldcg(A.U + v * A.ncell + c);
+    else u[v] = A.U[v * A.ncell + c];
+  }
+  recover<NDIM>(u, w);
+  const T p = gm1 * w[NV - 1];
+  bad |= !(w[0] > T(0)) || !(p > T(0));
+  const T cs = sqrt(gamma * p / w[0]);
+  size_t r = c;
+  T s = T(0);
+#pragma unroll
+  for (int q = 0; q < NDIM; ++q) {
+    const size_t i = r % A.n[q];
+    r /= A.n[q];
+    s = fmax(s, (fabs(w[1 + q]) + cs) * A.iw[q][i + 2]);
+  }
+  return s;
+}
 
 // Fixed butterfly over the warp: every lane ends with the same sum / max.
 __device__ __forceinline__ void fold_warp(double (&s)[5], unsigned long long& m) {

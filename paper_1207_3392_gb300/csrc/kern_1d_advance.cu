@@ -19,54 +19,15 @@
 // this GPU even for 256 cells: an SM retires about two FP64 operations per
 // clock.
 //
-// The grid barrier is a counter and a generation word in device memory; the
-// CTAs are co-resident (cooperative launch).  Its wait is bounded (about one
-// second of %globaltimer, with __nanosleep between polls): a CTA that gives
-// up sets STATUS_TIMEOUT, and every CTA leaves at its next barrier.
+// The CTAs are co-resident (cooperative launch) and meet at the bounded grid
+// barrier of grid_sync.cuh: a CTA that gives up waiting sets STATUS_TIMEOUT,
+// and every CTA leaves at its next barrier.
 #include "finalize.cuh"
+#include "grid_sync.cuh"
 #include "registry.h"
 #include "stage_kernel.cuh"
 
 namespace gh {
-
-namespace {
-
-__device__ __forceinline__ unsigned long long gtimer() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Barrier of all CTAs of the launch; false (on every thread of the CTA) if
-// this CTA gave up waiting, or an earlier barrier of the launch did.
-__device__ bool grid_barrier(unsigned* count, unsigned* gen, unsigned nblocks, unsigned& my_gen, unsigned* status,
-                             bool& failed) {
-  __syncthreads();
-  if (threadIdx.x == 0 && !failed) {
-    __threadfence();  // this CTA's writes before the arrival
-    const unsigned g = my_gen;
-    if (atomicAdd(count, 1u) == nblocks - 1) {
-      atomicExch(count, 0u);
-      __threadfence();
-      atomicExch(gen, g + 1u);
-    } else {
-      const unsigned long long t0 = gtimer();
-      while (atomicAdd(gen, 0u) == g) {
-        if (gtimer() - t0 > 1000000000ull) {
-          failed = true;
-          atomicOr(status, STATUS_TIMEOUT);
-          break;
-        }
-        __nanosleep(64);
-      }
-    }
-    __threadfence();  // the others' writes after the release
-    my_gen = g + 1u;
-  }
-  return __syncthreads_or(failed ? 1 : 0) == 0;
-}
-
-}  // namespace
 
 template <class T, int SOLVER, int TX>
 __global__ void __launch_bounds__(TX)

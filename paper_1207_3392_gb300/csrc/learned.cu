@@ -14,8 +14,9 @@
 #include "common.h"
 #include "genasis_hydro.h"
 #include "geometry.h"
-#include "learned_kernels.cuh"
 #include "learned_internal.h"
+#include "learned_kernels.cuh"
+#include "learned_step.cuh"
 
 namespace gh {
 
@@ -288,245 +289,27 @@ __global__ void lf_faces_kernel(Mesh2 M, const float* __restrict__ un, const flo
                                 float* __restrict__ scale) {
   const long long nxf = (long long)(M.nx + 1) * M.ny, nf = nxf + (long long)M.nx * (M.ny + 1);
   const float dt = k ? (float)*dtp : 0.f;
-  for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < nf; f += (long long)gridDim.x * blockDim.x) {
-    float s[6][4], Fl[4];
-    if (f < nxf) {
-      const int i = (int)(f % (M.nx + 1)), j = (int)(f / (M.nx + 1));
-#pragma unroll
-      for (int c = 0; c < 6; ++c) cell_prim(M, un, k, dt, i - 3 + c, j, s[c]);
-      const float(&w)[4][4] = *reinterpret_cast<const float(*)[4][4]>(&s[1][0]);
-      plain_face_flux<0, SOLVER>(M, w, i - 1, Fl);
-      if (X) face_features<0>(M, s, X + f * mlp::KIN, scale + f * 4);
-    } else {
-      const long long gidx = f - nxf;
-      const int i = (int)(gidx % M.nx), j = (int)(gidx / M.nx);
-#pragma unroll
-      for (int c = 0; c < 6; ++c) cell_prim(M, un, k, dt, i, j - 3 + c, s[c]);
-      const float(&w)[4][4] = *reinterpret_cast<const float(*)[4][4]>(&s[1][0]);
-      plain_face_flux<1, SOLVER>(M, w, j - 1, Fl);
-      if (X) face_features<1>(M, s, X + f * mlp::KIN, scale + f * 4);
-    }
-#pragma unroll
-    for (int v = 0; v < 4; ++v) F[v * nf + f] = Fl[v];
-  }
+  for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < nf; f += (long long)gridDim.x * blockDim.x)
+    lf_face<SOLVER, false>(M, un, k, dt, f, nxf, nf, F, X ? X + f * mlp::KIN : nullptr, scale);
 }
 
-struct UpdateArgs {
-  Mesh2 M;
-  const float* un;
-  const float* k1;      // stage 2: K of stage 1
-  const double* dtp;
-  const float* F;       // plain face fluxes [4][nf]
-  const float* dY;      // network outputs [nf][4], or null (no correction)
-  const float* scale;   // [nf][4]
-  float* out;                   // stage 1: K; stage 2: U^{n+1}
-  const unsigned char* flag;    // per cell: keeps the plain flux on all its faces (read)
-  unsigned char* flag_out;      // flags for the next pass (written)
-  unsigned long long* nfallback;
-  unsigned* status;
-  int stage;
-  int fixup;                    // 0: corrected pass; k > 0: k-th widening pass; -1: all-plain pass
-  int last;                     // last widening pass: remaining failures request the all-plain pass
-  unsigned* all_plain;          // device flags: [0] redo the whole stage with plain fluxes,
-                                // [1] some cell failed in the corrected pass of this stage
-  float ylim;                   // network outputs are clamped to [-ylim, ylim]
-  const float* R;               // FCT ratios [8][ncell] (R+ then R- per variable), or null
-};
-
-__device__ __forceinline__ bool cell_flagged(const UpdateArgs& A, int i, int j) {
-  const Mesh2& M = A.M;
-  if (i < 0 || i >= M.nx) {
-    if (M.bc_lo[0] != BC_PERIODIC) return false;
-    i = ((i % M.nx) + M.nx) % M.nx;
-  }
-  if (j < 0 || j >= M.ny) {
-    if (M.bc_lo[1] != BC_PERIODIC) return false;
-    j = ((j % M.ny) + M.ny) % M.ny;
-  }
-  return A.flag[(size_t)j * M.nx + i] != 0;
-}
-
-
-// Learned correction of face f in conserved order (network output clamped to
-// [-ylim, ylim], times the face's flux scale, rotated from the face frame).
-__device__ __forceinline__ void face_correction(const float* dY, const float* scale, float ylim, long long f, int axis,
-                                                float (&d)[4]) {
-  const float* yr = dY + f * 4;
-  const float* s = scale + f * 4;
-  float y[4];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) y[k] = fminf(fmaxf(yr[k], -ylim), ylim);
-  d[0] = s[0] * y[0];
-  d[1 + axis] = s[1] * y[1];
-  d[2 - axis] = s[2] * y[2];
-  d[3] = s[3] * y[3];
-}
-
-// Flux-corrected-transport factor of a face with correction d between cells
-// l and r (linear indices, -1 outside the mesh): the correction may raise a
-// cell by at most its R+ and lower it by at most its R-, for every variable.
-__device__ __forceinline__ float fct_factor(const float* R, size_t ncell, long long l, long long r, const float (&d)[4]) {
-  float C = 1.0f;
-#pragma unroll
-  for (int v = 0; v < 4; ++v) {
-    const float rpr = r >= 0 ? R[v * ncell + r] : 1.f, rmr = r >= 0 ? R[(4 + v) * ncell + r] : 1.f;
-    const float rpl = l >= 0 ? R[v * ncell + l] : 1.f, rml = l >= 0 ? R[(4 + v) * ncell + l] : 1.f;
-    if (d[v] > 0.f) C = fminf(C, fminf(rpr, rml));
-    else if (d[v] < 0.f) C = fminf(C, fminf(rmr, rpl));
-  }
-  return C;
-}
-
-// Face flux: plain flux plus the (FCT-limited) learned correction, unless the
-// correction is off or, in a widening pass, either neighbour is flagged.
-__device__ __forceinline__ void face_total(const UpdateArgs& A, long long f, int axis, bool corr, long long nf,
-                                           long long lcell, long long rcell, float (&Fo)[4]) {
-#pragma unroll
-  for (int v = 0; v < 4; ++v) Fo[v] = A.F[v * nf + f];
-  if (!corr || !A.dY) return;
-  float d[4];
-  face_correction(A.dY, A.scale, A.ylim, f, axis, d);
-  const float C = A.R ? fct_factor(A.R, (size_t)A.M.nx * A.M.ny, lcell, rcell, d) : 1.0f;
-#pragma unroll
-  for (int v = 0; v < 4; ++v) Fo[v] = fmaf(C, d[v], Fo[v]);
-}
-
-// Neighbour cell index with periodic wrap, or -1 across a non-periodic wall.
-__device__ __forceinline__ long long neighbour(const Mesh2& M, int i, int j) {
-  if (i < 0 || i >= M.nx) {
-    if (M.bc_lo[0] != BC_PERIODIC) return -1;
-    i = ((i % M.nx) + M.nx) % M.nx;
-  }
-  if (j < 0 || j >= M.ny) {
-    if (M.bc_lo[1] != BC_PERIODIC) return -1;
-    j = ((j % M.ny) + M.ny) % M.ny;
-  }
-  return (long long)j * M.nx + i;
-}
-
-// Zalesak's ratios for the stage U_new = U_b - c dt div(F): with the low-order
-// update U_L = U_b - c dt div(F_plain), bounds over the cell and its face
-// neighbours of U_L and of the stage input, and P+/P- the sums of the
-// positive/negative correction contributions of the cell's faces,
-// R+ = min(1, (U_max - U_L)/P+), R- = min(1, (U_L - U_min)/P-).
+// FCT ratios of every cell (lf_fct_cell).
 __global__ void lf_fct_kernel(UpdateArgs A, float* __restrict__ R) {
-  const Mesh2& M = A.M;
-  const long long ncell = (long long)M.nx * M.ny;
-  const long long nxf = (long long)(M.nx + 1) * M.ny, nf = nxf + (long long)M.nx * (M.ny + 1);
+  const long long ncell = (long long)A.M.nx * A.M.ny;
   const float dt = (float)*A.dtp;
-  const float cdt = A.stage == 1 ? dt : 0.5f * dt;
-  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell; c += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(c % M.nx), j = (int)(c / M.nx);
-    float umax[4], umin[4], UL[4];
-    const int di[5] = {0, -1, 1, 0, 0}, dj[5] = {0, 0, 0, -1, 1};
-    for (int k = 0; k < 5; ++k) {
-      const long long n = k == 0 ? c : neighbour(M, i + di[k], j + dj[k]);
-      if (n < 0) continue;
-      const int ni = (int)(n % M.nx), nj = (int)(n / M.nx);
-      const long long xl = (long long)nj * (M.nx + 1) + ni, yb = nxf + (long long)nj * M.nx + ni;
-      const float iwx = M.iw[0][ni + 2], iwy = M.iw[1][nj + 2];
-#pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        const float u0 = A.un[v * ncell + n];
-        const float kk = A.stage == 2 ? A.k1[v * ncell + n] : 0.f;
-        const float ub = fmaf(A.stage == 2 ? 0.5f * dt : 0.f, kk, u0);
-        const float uin = fmaf(A.stage == 2 ? dt : 0.f, kk, u0);
-        const float div = (A.F[v * nf + xl + 1] - A.F[v * nf + xl]) * iwx + (A.F[v * nf + yb + M.nx] - A.F[v * nf + yb]) * iwy;
-        const float ul = fmaf(-cdt, div, ub);
-        if (k == 0) {
-          UL[v] = ul;
-          umax[v] = fmaxf(ul, uin);
-          umin[v] = fminf(ul, uin);
-        } else {
-          umax[v] = fmaxf(umax[v], fmaxf(ul, uin));
-          umin[v] = fminf(umin[v], fminf(ul, uin));
-        }
-      }
-    }
-    const long long xl = (long long)j * (M.nx + 1) + i, yb = nxf + (long long)j * M.nx + i;
-    const float iwx = M.iw[0][i + 2], iwy = M.iw[1][j + 2];
-    float dl[4], dr[4], db[4], dt4[4];
-    face_correction(A.dY, A.scale, A.ylim, xl, 0, dl);
-    face_correction(A.dY, A.scale, A.ylim, xl + 1, 0, dr);
-    face_correction(A.dY, A.scale, A.ylim, yb, 1, db);
-    face_correction(A.dY, A.scale, A.ylim, yb + M.nx, 1, dt4);
-#pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      const float q[4] = {cdt * dl[v] * iwx, -cdt * dr[v] * iwx, cdt * db[v] * iwy, -cdt * dt4[v] * iwy};
-      float pp = 0.f, pm = 0.f;
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        pp += fmaxf(q[k], 0.f);
-        pm += fmaxf(-q[k], 0.f);
-      }
-      R[v * ncell + c] = pp > 0.f ? fminf(1.f, (umax[v] - UL[v]) / pp) : 1.f;
-      R[(4 + v) * ncell + c] = pm > 0.f ? fminf(1.f, (UL[v] - umin[v]) / pm) : 1.f;
-    }
-  }
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell; c += (long long)gridDim.x * blockDim.x)
+    lf_fct_cell<false>(A, c, dt, R);
 }
 
+// One pass of the corrected update over every cell (lf_update_cell); the
+// widening and all-plain passes return at once unless requested.
 __global__ void lf_update_kernel(UpdateArgs A) {
-  const Mesh2& M = A.M;
-  const long long ncell = (long long)M.nx * M.ny;
-  const long long nxf = (long long)(M.nx + 1) * M.ny, nf = nxf + (long long)M.nx * (M.ny + 1);
+  const long long ncell = (long long)A.M.nx * A.M.ny;
   const float dt = (float)*A.dtp;
   if (A.fixup < 0 && A.all_plain[0] == 0u) return;
   if (A.fixup > 0 && A.all_plain[1] == 0u) return;  // nothing to widen
-  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell; c += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(c % M.nx), j = (int)(c / M.nx);
-    bool cl = true, cr = true, cb = true, ct = true, me = false;
-    if (A.fixup < 0) {
-      cl = cr = cb = ct = false;
-    } else if (A.fixup) {
-      me = A.flag[c] != 0;
-      const bool fl = cell_flagged(A, i - 1, j), fr = cell_flagged(A, i + 1, j);
-      const bool fb = cell_flagged(A, i, j - 1), ft = cell_flagged(A, i, j + 1);
-      if (!(me || fl || fr || fb || ft)) {
-        A.flag_out[c] = 0;
-        continue;
-      }
-      cl = !(me || fl);
-      cr = !(me || fr);
-      cb = !(me || fb);
-      ct = !(me || ft);
-    }
-    const long long xl = (long long)j * (M.nx + 1) + i, yb = nxf + (long long)j * M.nx + i;
-    float FL[4], FR[4], FB[4], FT[4];
-    face_total(A, xl, 0, cl, nf, neighbour(M, i - 1, j), c, FL);
-    face_total(A, xl + 1, 0, cr, nf, c, neighbour(M, i + 1, j), FR);
-    face_total(A, yb, 1, cb, nf, neighbour(M, i, j - 1), c, FB);
-    face_total(A, yb + M.nx, 1, ct, nf, c, neighbour(M, i, j + 1), FT);
-    const float iwx = M.iw[0][i + 2], iwy = M.iw[1][j + 2];
-    float u[4], w[4];
-#pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      const float L = -((FR[v] - FL[v]) * iwx + (FT[v] - FB[v]) * iwy);
-      const float u0 = A.un[v * ncell + c];
-      if (A.stage == 1) {
-        A.out[v * ncell + c] = L;
-        u[v] = fmaf(dt, L, u0);
-      } else {
-        u[v] = fmaf(0.5f * dt, A.k1[v * ncell + c] + L, u0);
-        A.out[v * ncell + c] = u[v];
-      }
-    }
-    recover<2>(u, w);
-    const bool ok = w[0] > 0.f && M.gm1 * w[3] > 0.f && fabsf(w[1]) < INFINITY && fabsf(w[2]) < INFINITY;
-    if (A.fixup == 0) {
-      A.flag_out[c] = ok ? 0 : 1;
-      if (!ok) {
-        atomicAdd(A.nfallback, 1ull);
-        atomicOr(A.all_plain + 1, 1u);
-      }
-    } else if (A.fixup > 0) {
-      // flags only grow: a flagged cell stays plain, a newly failing one joins
-      A.flag_out[c] = (me || !ok) ? 1 : 0;
-      if (!ok && me) atomicOr(A.status, STATUS_NONPHYS);  // all its faces are plain already
-      if (!ok && A.last) atomicOr(A.all_plain, 1u);  // flag [0]
-    } else if (!ok) {
-      atomicOr(A.status, STATUS_NONPHYS);  // the plain scheme itself fails
-    }
-  }
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell; c += (long long)gridDim.x * blockDim.x)
+    lf_update_cell<false>(A, c, dt);
 }
 
 // Training targets: add weight * (F(U) + F(U + dt K)) / 2, averaged over the
@@ -824,6 +607,9 @@ struct genasis_learned {
   unsigned* status = nullptr;
   unsigned long long* nfallback = nullptr;
   unsigned* all_plain = nullptr;
+  int one_launch = 1;           // GENASIS_OPT_ONE_LAUNCH
+  int adv_grid = -1;            // CTAs of the one-launch advance (0: not available; -1: not yet asked)
+  unsigned* adv = nullptr;      // its barrier and all-plain words, then (at 256 B) one double per CTA
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   int g_nsteps = -1;
   double g_cfl = 0, g_tend = 0;
@@ -845,7 +631,7 @@ int learned_free(genasis_learned* l) {
   }
   for (void* p : {(void*)l->K, (void*)l->F, (void*)l->X, (void*)l->scale, (void*)l->dY, (void*)l->flag[0],
                   (void*)l->flag[1], (void*)l->params, (void*)l->scal, (void*)l->part_speed, (void*)l->status,
-                  (void*)l->nfallback, (void*)l->all_plain, (void*)l->R, (void*)l->wimg})
+                  (void*)l->nfallback, (void*)l->all_plain, (void*)l->R, (void*)l->wimg, (void*)l->adv})
     cudaFree(p);
   if (l->own_stream && l->stream) cudaStreamDestroy(l->stream);
   delete l;
@@ -858,6 +644,71 @@ void drop_graphs(genasis_learned* l) {
       cudaGraphExecDestroy(l->graph[b]);
       l->graph[b] = nullptr;
     }
+}
+
+constexpr int kAdvanceMaxGrid = 1024;  // part_speed holds 1024 partials
+constexpr size_t kAdvanceBytes = 256 + kAdvanceMaxGrid * sizeof(double);
+
+bool one_launch_usable(genasis_learned* l) {
+  if (!l->one_launch) return false;
+  if (l->adv_grid < 0) l->adv_grid = learned_advance_max_grid(l->solver);
+  return l->adv_grid > 0;
+}
+
+// nsteps corrected RK2 steps in one cooperative launch (learned_advance.cu),
+// dt by the finalize rule `mode` (FIN_CFL: cfl * dt_CFL clamped at t_end > 0;
+// FIN_FIXED: fixed_dt).  Needs one_launch_usable(l).
+int enqueue_one_launch(genasis_learned* l, int nsteps, int mode, double cfl, double fixed_dt, double t_end) {
+  const long long tiles = (l->nf + LF_ADVANCE_THREADS - 1) / LF_ADVANCE_THREADS;
+  long long grid = l->adv_grid < tiles ? l->adv_grid : tiles;
+  if (grid > kAdvanceMaxGrid) grid = kAdvanceMaxGrid;
+  if (!l->adv) GH_CK(cudaMalloc((void**)&l->adv, kAdvanceBytes));
+  // barrier, all-plain and speed words start at zero in every launch (even after one that gave up)
+  GH_CK(cudaMemsetAsync(l->adv, 0, 12 * sizeof(unsigned), l->stream));
+  LfAdvanceArgs P;
+  memset(&P, 0, sizeof(P));
+  P.M = l->M;
+  P.R.ncell = l->ncell;
+  P.R.n[0] = l->M.nx;
+  P.R.n[1] = l->M.ny;
+  P.R.n[2] = 1;
+  P.R.gamma = l->M.gamma;
+  P.R.iw[0] = l->iw[0];
+  P.R.iw[1] = l->iw[1];
+  P.R.wd[0] = l->wd[0];
+  P.R.wd[1] = l->wd[1];
+  P.R.part_speed = l->part_speed;
+  P.R.status = l->status;
+  P.R.nblk = (int)grid;
+  P.Fa.part_speed = l->part_speed;
+  P.Fa.nblk = (int)grid;
+  P.Fa.nv = 4;
+  P.Fa.mode = mode;
+  P.Fa.cfl = cfl;
+  P.Fa.fixed_dt = fixed_dt;
+  P.Fa.t_end = t_end;
+  P.Fa.scal = l->scal;
+  P.Fa.status = l->status;
+  P.U[0] = (float*)l->U[l->cur];
+  P.U[1] = (float*)l->U[1 - l->cur];
+  P.K = l->K;
+  P.F = l->F;
+  P.dY = l->dY;
+  P.scale = l->scale;
+  P.Rfct = l->R;
+  P.flag[0] = l->flag[0];
+  P.flag[1] = l->flag[1];
+  P.W = l->corrected ? l->wimg : nullptr;
+  P.fct = l->fct ? 1 : 0;
+  P.ylim = l->ylim;
+  P.nfallback = l->nfallback;
+  P.status = l->status;
+  P.sync = l->adv;
+  P.dts = (double*)((char*)l->adv + 256);
+  P.nsteps = nsteps;
+  GH_CK(launch_learned_advance(P, l->solver, (int)grid, l->stream));
+  l->cur ^= nsteps & 1;
+  return GENASIS_OK;
 }
 
 // One corrected RK2 step: dt = cfl * dt_CFL (clamped at t_end > 0), or the
@@ -1147,6 +998,7 @@ int genasis_learned_get_conserved(genasis_learned_t l, float* U) {
   unsigned st = 0;
   GH_CK(cudaMemcpyAsync(&st, l->status, sizeof(unsigned), cudaMemcpyDeviceToHost, l->stream));
   GH_CK(cudaStreamSynchronize(l->stream));
+  if (st & STATUS_TIMEOUT) return fail(GENASIS_ETIMEOUT, "a bounded device wait gave up");
   if (st & STATUS_NONPHYS) return fail(GENASIS_ENONPHYS, "non-physical state (rho <= 0, p <= 0 or NaN) on the device");
   return GENASIS_OK;
 }
@@ -1154,7 +1006,10 @@ int genasis_learned_get_conserved(genasis_learned_t l, float* U) {
 int genasis_learned_advance(genasis_learned_t l, int nsteps, double cfl, double t_end, double* t_out) {
   if (!l) return fail(GENASIS_EINVAL, "NULL handle");
   if (nsteps < 0 || !(cfl > 0.0)) return fail(GENASIS_EINVAL, "learned_advance: bad nsteps or cfl");
-  if (nsteps > 0) {
+  if (nsteps > 0 && one_launch_usable(l)) {
+    const int rc = enqueue_one_launch(l, nsteps, FIN_CFL, cfl, 0.0, t_end);
+    if (rc) return rc;
+  } else if (nsteps > 0) {
     if (l->g_nsteps != nsteps || l->g_cfl != cfl || l->g_tend != t_end || l->g_corr != l->corrected) {
       drop_graphs(l);
       l->g_nsteps = nsteps;
@@ -1187,6 +1042,7 @@ int genasis_learned_advance(genasis_learned_t l, int nsteps, double cfl, double 
     unsigned st = 0;
     GH_CK(cudaMemcpyAsync(&st, l->status, sizeof(unsigned), cudaMemcpyDeviceToHost, l->stream));
     GH_CK(cudaStreamSynchronize(l->stream));
+    if (st & STATUS_TIMEOUT) return fail(GENASIS_ETIMEOUT, "a bounded device wait gave up");
     if (st & STATUS_NONPHYS) return fail(GENASIS_ENONPHYS, "non-physical state even with the plain flux");
   }
   return GENASIS_OK;
@@ -1195,7 +1051,26 @@ int genasis_learned_advance(genasis_learned_t l, int nsteps, double cfl, double 
 int genasis_learned_step(genasis_learned_t l, double dt) {
   if (!l) return fail(GENASIS_EINVAL, "NULL handle");
   if (!(dt > 0.0) || !(dt < INFINITY)) return fail(GENASIS_EINVAL, "learned_step: dt must be finite and > 0");
+  if (one_launch_usable(l)) return enqueue_one_launch(l, 1, FIN_FIXED, 1.0, dt, 0.0);
   return learned_enqueue_step(l, 1.0, 0.0, dt);
+}
+
+int genasis_learned_set_option(genasis_learned_t l, int option, int value) {
+  if (!l) return fail(GENASIS_EINVAL, "NULL handle");
+  if (option != GENASIS_OPT_ONE_LAUNCH) return fail(GENASIS_EINVAL, "learned_set_option: unknown option %d", option);
+  if (value != 0 && value != 1) return fail(GENASIS_EINVAL, "GENASIS_OPT_ONE_LAUNCH takes 0 or 1");
+  l->one_launch = value;
+  return GENASIS_OK;
+}
+
+int genasis_learned_launches_per_step(genasis_learned_t l) {
+  if (!l) return fail(GENASIS_EINVAL, "NULL handle");
+  if (one_launch_usable(l)) return 1;  // one launch covers all the steps of a call
+  // CFL speed and finalize; per stage the faces and the update, with a
+  // network also the inference, the 3 widening passes, the all-plain pass
+  // and (limiting) the FCT ratios
+  const int per_stage = l->corrected ? (l->fct ? 8 : 7) : 2;
+  return 2 + 2 * per_stage;
 }
 
 int genasis_learned_fallbacks(genasis_learned_t l, long long* cells) {

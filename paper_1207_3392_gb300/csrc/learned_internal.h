@@ -4,10 +4,42 @@
 
 #include <cuda_runtime.h>
 
+#include "aux_kernels.h"
 #include "genasis_hydro.h"
 #include "learned_kernels.cuh"
 
 namespace gh {
+
+// Arguments of the one-launch corrected advance (learned_advance.cu): every
+// step of a call in one cooperative launch.
+struct LfAdvanceArgs {
+  Mesh2 M;
+  ReduceArgs<float> R;         // CFL speed: U set per step; part_speed holds one partial per CTA
+  FinalizeArgs Fa;             // dt rule (mode, cfl, fixed_dt, t_end), scal, status; nblk = the grid
+  float* U[2];                 // U[0]: the state at launch; step s writes U[(s + 1) & 1]
+  float* K;                    // stage-1 update
+  float* F;                    // plain face fluxes [nf][4]
+  float* dY;                   // network outputs [nf][4]
+  float* scale;                // face flux scales [nf][4]
+  float* Rfct;                 // FCT ratios [ncell][8]
+  unsigned char* flag[2];      // fallback flags per cell
+  const mlp::InferWeights* W;  // BF16 network image, or null: the plain scheme
+  int fct;                     // FCT limiting of the correction
+  float ylim;                  // bound on the network outputs
+  unsigned long long* nfallback;
+  unsigned* status;
+  unsigned* sync;              // [0..1] grid barrier, [2..3] / [4..5] all-plain flags of stage 1 / 2,
+                               // [8..11] two 64-bit speed maxima; the first 48 bytes zero at launch
+  double* dts;                 // one per CTA
+  int nsteps;
+};
+
+// Largest cooperative grid of the one-launch advance (CTAs of
+// LF_ADVANCE_THREADS threads that fit on the device at once), 0 if none.
+constexpr int LF_ADVANCE_THREADS = 256;
+int learned_advance_max_grid(int solver);
+// Launch it with grid CTAs (1 <= grid <= learned_advance_max_grid).
+cudaError_t launch_learned_advance(const LfAdvanceArgs& P, int solver, int grid, cudaStream_t st);
 
 cudaError_t launch_face_flux_accumulate(const Mesh2& M, int solver, const float* un, const float* k, const double* dtp,
                                         int s, double weight, double* acc, cudaStream_t st);

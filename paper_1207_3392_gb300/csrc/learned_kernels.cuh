@@ -36,8 +36,17 @@ struct Mesh2 {
   const float* iw[2];
 };
 
+// Load through L2 only (ld.global.cg) when COH, for arrays written earlier in
+// the same launch; a plain load otherwise.
+template <bool COH, class V>
+__device__ __forceinline__ V lf_ld(const V* p) {
+  if constexpr (COH) return __ldcg(p);
+  else return *p;
+}
+
 // Conserved state of cell (i, j) (any integer indices), as U = un + dt * k when
 // k is non-null, with boundary mapping; returns primitives (n, vx, vy, e).
+template <bool COH = false>
 __device__ __forceinline__ void cell_prim(const Mesh2& M, const float* __restrict__ un, const float* __restrict__ k,
                                           float dt, int i, int j, float (&w)[4]) {
   bool fx, fy;
@@ -47,8 +56,8 @@ __device__ __forceinline__ void cell_prim(const Mesh2& M, const float* __restric
   float u[4];
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
-    float x = un[v * vs + c];
-    if (k) x = fmaf(dt, k[v * vs + c], x);
+    float x = lf_ld<COH>(un + v * vs + c);
+    if (k) x = fmaf(dt, lf_ld<COH>(k + v * vs + c), x);
     u[v] = x;
   }
   if (fx) u[1] = -u[1];
@@ -85,11 +94,15 @@ __device__ __forceinline__ void plain_face_flux(const Mesh2& M, const float (&w)
 template <int Q>
 __device__ __forceinline__ void face_features(const Mesh2& M, const float (&s)[6][4], __nv_bfloat16* __restrict__ x,
                                               float* __restrict__ scale) {
-  float rs = 0.f, ps = 0.f;
+  // Every rounding is spelt out (the pressures as separate products, the
+  // ratios minus one as fused multiply-adds), so that each kernel that inlines
+  // this computes bitwise the same features.
+  float pk[6], rs = 0.f, ps = 0.f;
 #pragma unroll
   for (int k = 0; k < 6; ++k) {
+    pk[k] = __fmul_rn(M.gm1, s[k][3]);
     rs += s[k][0];
-    ps += M.gm1 * s[k][3];
+    ps += pk[k];
   }
   const float rbar = rs * (1.0f / 6.0f), pbar = ps * (1.0f / 6.0f);
   const float cbar = sqrtf(M.gamma * pbar / rbar);
@@ -98,8 +111,8 @@ __device__ __forceinline__ void face_features(const Mesh2& M, const float (&s)[6
 #pragma unroll
   for (int k = 0; k < 6; ++k) {
     const float vn = s[k][1 + Q], vt = s[k][2 - Q];
-    packed[2 * k] = mlp::pack2(s[k][0] * ir - 1.0f, vn * ic);
-    packed[2 * k + 1] = mlp::pack2(vt * ic, M.gm1 * s[k][3] * ip - 1.0f);
+    packed[2 * k] = mlp::pack2(fmaf(s[k][0], ir, -1.0f), vn * ic);
+    packed[2 * k + 1] = mlp::pack2(vt * ic, fmaf(pk[k], ip, -1.0f));
   }
 #pragma unroll
   for (int k = 12; k < 16; ++k) packed[k] = 0u;

@@ -92,6 +92,8 @@ SIGNATURES = {
     "genasis_learned_get_conserved": [_P, _P],
     "genasis_learned_advance": [_P, _I, _D, _D, _P],
     "genasis_learned_fallbacks": [_P, _P],
+    "genasis_learned_set_option": [_P, ctypes.c_int, ctypes.c_int],
+    "genasis_learned_launches_per_step": [_P],
     "genasis_learned_features": [_P, _P, _P],
     "genasis_learned_targets": [_P, _P, _P, _P, _P],
     "genasis_mlp_param_count": [],
@@ -781,6 +783,14 @@ class Learned:
                 break
             t = self.advance(chunk, cfl, t_end)
         return t
+
+    def set_one_launch(self, enabled):
+        """All steps of a call in one cooperative launch (default on) or the
+        per-phase launches; the results are bitwise the same."""
+        check(load().genasis_learned_set_option(self._h, OPT_ONE_LAUNCH, int(bool(enabled))))
+
+    def launches_per_step(self):
+        return check(load().genasis_learned_launches_per_step(self._h))
 
     def fallbacks(self):
         v = ctypes.c_longlong()

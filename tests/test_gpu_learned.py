@@ -395,3 +395,94 @@ def test_trained_network_gains_over_the_plain_scheme():
               f"({', '.join(f'{r['ratio_learned_fct']:.3f}' for r in rows)})")
         assert ratio <= 0.85, (m, rows)
         assert all(r["ratio_learned_fct"] <= 0.9 for r in rows), (m, rows)
+
+
+def _fallback_net():
+    th = _random_net(9, last=0.0)
+    th[M.NPARAM - 4] = 40.0   # b3[0]: a huge mass-flux correction on every face
+    return th
+
+
+# (problem, network, FCT, output bound, solver): a periodic shear layer with a
+# random network, with and without the limiter; ragged meshes with walls
+# (reflecting, outflow) on non-uniform widths, with and without a network;
+# and a network whose unlimited correction makes cells fall back.
+ONE_LAUNCH_CASES = {
+    "kh64_net_fct": (lambda: P.kelvin_helmholtz(64, seed=5), lambda: _random_net(21, last=0.3), True, None, None),
+    "kh48_net_limit": (lambda: P.kelvin_helmholtz(48, seed=6), lambda: _random_net(22, last=0.3), False, 2.0, None),
+    "blocks45x37_reflect_plain_hll": (lambda: P.random_blocks(2, (45, 37), seed=7), lambda: None, True, None, H.HLL),
+    "blocks61x29_outflow_net_fct": (lambda: P.random_blocks(2, (61, 29), seed=8, bc=P.OUTFLOW),
+                                    lambda: _random_net(23, last=0.3), True, None, H.HLLC),
+    "kh64_fallbacks": (lambda: P.kelvin_helmholtz(64, seed=3), _fallback_net, False, None, None),
+}
+
+
+def _learned_pair(case):
+    mk_pr, mk_net, fct, ylim, solver = ONE_LAUNCH_CASES[case]
+    pr = mk_pr()
+    th = mk_net()
+    out = []
+    for one in (False, True):
+        L = H.Learned(pr, params=None if th is None else th.astype(np.float32), solver=solver)
+        L.set_one_launch(one)
+        L.set_fct(fct)
+        if ylim is not None:
+            L.set_limit(ylim)
+        L.set_primitive(pr.rho, pr.vel, pr.p)
+        out.append(L)
+    return pr, th, out
+
+
+@pytest.mark.parametrize("case", sorted(ONE_LAUNCH_CASES))
+def test_one_launch_advance_is_the_per_phase_advance(case):
+    """All steps of a call in one cooperative launch give bitwise the states,
+    times and fallback counts of the per-phase launches: CFL steps (the last
+    one clamped at t_end), then fixed-dt steps."""
+    pr, th, (Lp, L1) = _learned_pair(case)
+    assert L1.launches_per_step() == 1
+    assert Lp.launches_per_step() == (2 + 2 * (2 if th is None else (8 if ONE_LAUNCH_CASES[case][2] else 7)))
+    tp = Lp.advance(3, 0.45)
+    t1 = L1.advance(3, 0.45)
+    assert tp == t1
+    np.testing.assert_array_equal(L1.get_conserved(), Lp.get_conserved())
+    # two more steps in one call: the first clamped at t_end, the second of dt 0
+    t_end = tp + 0.1 * (tp / 3)
+    assert Lp.advance(2, 0.45, t_end) == t_end
+    assert L1.advance(2, 0.45, t_end) == t_end
+    Up, U1 = Lp.get_conserved(), L1.get_conserved()
+    np.testing.assert_array_equal(U1, Up)
+    dt = 0.25 * tp / 3
+    for L in (Lp, L1):
+        L.step(dt)
+        L.step(dt)
+    np.testing.assert_array_equal(L1.get_conserved(), Lp.get_conserved())
+    assert L1.advance(0, 0.45) == Lp.advance(0, 0.45)
+    assert L1.fallbacks() == Lp.fallbacks()
+    if case == "kh64_fallbacks":
+        assert L1.fallbacks() > 0
+    # the state moved
+    assert np.max(np.abs(U1 - L1.get_conserved())) > 0
+    for L in (Lp, L1):
+        L.close()
+
+
+def test_one_launch_handle_with_network_is_the_per_phase_handle():
+    """The option reaches the network attached to a single-mesh handle, set
+    before or after attaching it."""
+    pr = P.kelvin_helmholtz(48, seed=11)
+    bits, _ = _bf16_bits(_random_net(24, last=0.3))
+    res = []
+    for one, before in ((False, True), (False, False), (True, False)):
+        h = H.Hydro.from_problem(pr, precision=H.FP32_MIXED)
+        if before:
+            h.set_one_launch(one)
+        h.set_flux_mlp(bits)
+        if not before:
+            h.set_one_launch(one)
+        assert h.launches_per_step() == (2 if one else 19)
+        t = h.advance(4, 0.45)
+        res.append((h.get_conserved(), t))
+        h.close()
+    for U, t in res[1:]:
+        np.testing.assert_array_equal(U, res[0][0])
+        assert t == res[0][1]
