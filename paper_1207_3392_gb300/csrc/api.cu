@@ -191,6 +191,7 @@ int configure(genasis_hydro* h, int tile, int kchunk_req) {
       kchunk = (int)((nm + chunks - 1) / chunks);
     }
     if (kchunk > nm) kchunk = nm;
+    if ((v1.pair || v2.pair) && (kchunk & 1)) ++kchunk;  // whole plane pairs per chunk
     gz = (nm + kchunk - 1) / kchunk;
   }
   const size_t nblk = (size_t)gx * gy * gz;

@@ -14,6 +14,7 @@ struct StageVariant {
   int threads;         // threads per CTA
   int tma = 0;         // 1: takes TmaStageArgs (state planes staged by TMA), see stage_tma.cuh
   int box_x = 0, box_y = 0;  // TMA box of one plane (cells along x and y)
+  int pair = 0;        // 1: two march planes per thread (stage_pair.cuh); chunks of an even plane count
 };
 
 // Tile shapes compiled per dimensionality and precision (GENASIS_FP64,
@@ -30,6 +31,7 @@ bool stage_variant_2d(bool fp64, int solver, int stage, int tile, StageVariant* 
 bool stage_variant_3d_f32(int solver, int stage, int tile, StageVariant* out);
 bool stage_variant_3d_f32_wide(int solver, int stage, int tile, StageVariant* out);
 bool stage_variant_3d_f32_tma(int solver, int stage, int tile, StageVariant* out);
+bool stage_variant_3d_f32_pair(int solver, int stage, int tile, StageVariant* out);
 bool stage_variant_3d_f64(int solver, int stage, int tile, StageVariant* out);
 int tile_count_1d();
 // One-launch advance of small 1D meshes (kern_1d_advance.cu): the

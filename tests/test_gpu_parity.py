@@ -196,16 +196,81 @@ def test_every_tile_shape_identical(ndim, precision, shape):
     count = h.tile_info()["tile_count"]
     h.close()
     ran = 0
+    pair_ref = None
     for tile in range(count):
+        paired = ndim == 3 and precision == H.FP32_MIXED and tile in PAIR_TILES
         for kc in ((0, 7, shape[-1]) if ndim > 1 else (0,)):
             try:
                 U, _ = gpu_run(pr, precision, steps=4, tile=tile, kchunk=kc)
             except H.HydroError as e:
                 assert e.code == H.EINVAL and "TMA" in str(e) and shape[0] % 4 != 0, (tile, str(e))
                 continue
-            np.testing.assert_array_equal(U, ref, err_msg=f"tile {tile} kchunk {kc}")
+            if paired:
+                # the paired family: bitwise among themselves, within the
+                # FP32 bar of the scalar tiles
+                if pair_ref is None:
+                    pair_ref = U
+                    _check(U, ref, 3, TOL_FP32, f"paired tile {tile} against tile 0")
+                np.testing.assert_array_equal(U, pair_ref, err_msg=f"tile {tile} kchunk {kc}")
+            else:
+                np.testing.assert_array_equal(U, ref, err_msg=f"tile {tile} kchunk {kc}")
             ran += 1
     assert ran >= 1
+    if ndim == 3 and precision == H.FP32_MIXED:
+        assert pair_ref is not None
+
+
+PAIR_TILES = (11, 12, 13)  # 3D FP32 tiles taking two march planes per thread (packed FP32)
+
+
+@pytest.mark.parametrize("bc", ["periodic", "reflect", "outflow", "mixed"])
+def test_pair_tiles_match_the_oracle_and_each_other(bc):
+    """The z-paired tiles under every boundary rule, HLL and HLLC, on a mesh
+    ragged in x, y and z (72 x 29 x 23: an odd plane count, so a last chunk
+    computes one plane past its end): within the FP32 bar of the oracle and of
+    the scalar tiles, and bitwise the same state for every paired tile and
+    chunk length (2 planes per chunk: a warm-up pair per pair; odd requests
+    round up to whole plane pairs)."""
+    codes = {"periodic": P.PERIODIC, "reflect": P.REFLECT, "outflow": P.OUTFLOW, "mixed": P.REFLECT}
+    pr = P.random_blocks(3, (72, 29, 23), seed=19, bc=codes[bc])
+    if bc == "mixed":
+        pr = pr.with_(bc_lo=(P.REFLECT, P.OUTFLOW, P.PERIODIC), bc_hi=(P.OUTFLOW, P.REFLECT, P.PERIODIC))
+    for solver in (H.HLL, H.HLLC):
+        Uo, to = oracle_run(pr, solver=solver, steps=3)
+        ref, t = gpu_run(pr, H.FP32_MIXED, solver=solver, steps=3, tile=PAIR_TILES[0], kchunk=0)
+        assert t == pytest.approx(to, rel=1e-5)
+        _check(ref, Uo, 3, TOL_FP32, f"paired tiles bc={bc} solver={solver}")
+        scalar, _ = gpu_run(pr, H.FP32_MIXED, solver=solver, steps=3, tile=0, kchunk=0)
+        _check(ref, scalar, 3, TOL_FP32, f"paired against scalar bc={bc} solver={solver}")
+        for tile in PAIR_TILES:
+            for kc in (0, 2, 5, 23):
+                U, _ = gpu_run(pr, H.FP32_MIXED, solver=solver, steps=3, tile=tile, kchunk=kc)
+                np.testing.assert_array_equal(U, ref, err_msg=f"solver {solver} tile {tile} kchunk {kc}")
+
+
+def test_pair_tiles_sedov_source_and_totals():
+    """The paired tiles on the point blast (50 steps at 64^3) and with an
+    external force on all three axes: within the FP32 bar of the oracle; the
+    step totals (each column's two lanes summed apart) within rounding of the
+    scalar tiles' totals."""
+    pr = P.sedov_3d(64)
+    Uo, to = oracle_run(pr, steps=50)
+    for tile in PAIR_TILES:
+        Ug, tg = gpu_run(pr, H.FP32_MIXED, steps=50, tile=tile, kchunk=0)
+        assert tg == pytest.approx(to, rel=1e-5)
+        _check(Ug, Uo, 3, TOL_FP32, f"sedov 64^3 paired tile {tile}")
+    pf = P.random_blocks(3, (30, 26, 22), seed=21, bc=P.REFLECT).with_(grad_phi=(0.3, -0.2, 0.5))
+    Uo, _ = oracle_run(pf, steps=8)
+    Ug, _ = gpu_run(pf, H.FP32_MIXED, steps=8, tile=PAIR_TILES[1], kchunk=0)
+    _check(Ug, Uo, 3, TOL_FP32, "3d source, paired tile")
+    tots = []
+    for tile in (0, PAIR_TILES[2]):
+        h = H.Hydro.from_problem(pf, precision=H.FP32_MIXED)
+        h.set_tile(tile, 0)
+        h.advance(2, pf.cfl)
+        tots.append(np.asarray(h.step_totals()))
+        h.close()
+    np.testing.assert_allclose(tots[1], tots[0], rtol=1e-6, atol=1e-9 * np.max(np.abs(tots[0])))
 
 
 TMA_TILES = (9, 10)  # 3D FP32 tiles whose stage 1 stages the state planes with TMA
@@ -475,7 +540,7 @@ def test_nonphysical_state_sets_status():
 
 # ----------------------------------------------------------- full-size workloads
 
-def _one_step_full(prob, precisions):
+def _one_step_full(prob, precisions, pair_tile=None):
     """One device-CFL step at full size, in the benchmark's launch
     configuration, against one oracle step with the oracle's dt."""
     g = O.Grid(prob)
@@ -483,18 +548,24 @@ def _one_step_full(prob, precisions):
     dt = prob.cfl * O.cfl_dt(g, U0)
     Uo = O.step(g, U0, dt)
     del U0
-    for precision, tol in precisions:
+    runs = [(precision, tol, None) for precision, tol in precisions]
+    if pair_tile is not None:
+        runs.append((H.FP32_MIXED, TOL_FP32, pair_tile))
+    for precision, tol, tile in runs:
         h = H.Hydro.from_problem(prob, precision=precision)
+        if tile is not None:
+            h.set_tile(tile, 40)
         t = h.advance(1, prob.cfl)
         assert t == pytest.approx(dt, rel=1e-12 if precision == H.FP64 else 1e-6)
         Ug = h.get_conserved(precision=H.FP64)
         h.close()
-        _check(Ug, Uo, prob.ndim, tol, f"{prob.name} prec={precision}")
+        _check(Ug, Uo, prob.ndim, tol, f"{prob.name} prec={precision} tile={tile}")
 
 
 def test_sedov_full_size_one_step():
-    """256^3 point blast, one step, both precisions."""
-    _one_step_full(P.sedov_3d(256), PRECISIONS)
+    """256^3 point blast, one step, both precisions; FP32 also on the paired
+    tile that the bench offers, at 40 planes per CTA."""
+    _one_step_full(P.sedov_3d(256), PRECISIONS, pair_tile=PAIR_TILES[2])
 
 
 def test_stretched_pulse_full_size_one_step():
