@@ -687,9 +687,10 @@ def measure_learned(steps, warmup, stream, sampler=None):
     nlast = 4 * 64 + 4                      # output layer W3, b3 (zero at initialisation)
     params[-nlast:] = np.random.default_rng(0).normal(0.0, 0.02, nlast).astype(np.float32)
 
-    def timed(one_launch, smp):
+    def timed(one_launch, smp, tc=False):
         L = H.Learned(pr, params=params, stream=stream.cuda_stream)
         L.set_one_launch(one_launch)
+        L.set_mlp_tcgen05(tc)
         L.set_primitive(pr.rho, pr.vel, pr.p)
         for _ in range(max(warmup, 3)):
             L.advance(1, 0.5, sync=False)
@@ -709,6 +710,7 @@ def measure_learned(steps, warmup, stream, sampler=None):
         return res
 
     ms_pp, _, lps_pp, _ = timed(False, None)
+    ms_tc, _, _, _ = timed(True, None, tc=True)
     ms, fb, lps, clocks = timed(True, sampler)
     cells = 256 * 256
     return {"value": cells * 2 / (ms * 1e-3), "ms_per_step": ms, "steps": steps, "cells": cells,
@@ -717,6 +719,9 @@ def measure_learned(steps, warmup, stream, sampler=None):
             "launch": ("one cooperative launch per advance call (persistent grid, 7 grid barriers a step)"
                        if lps == 1 else f"{lps} launches per step"),
             "per_phase_ms_per_step": ms_pp, "per_phase_launches_per_step": lps_pp,
+            # the same one-launch step with the network on tcgen05 (accumulators
+            # in tensor memory) instead of mma.sync fragments in registers
+            "tcgen05_ms_per_step": ms_tc,
             # one advance call per step
             "gpu_launches": steps * lps, "clocks": clocks}
 
@@ -735,7 +740,8 @@ def run_learned(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16", "data": "synthetic",
             "config": {"workload": "learned_kh2d_256^2_hllc_fct", "cells": rec["cells"], "faces": 2 * rec["cells"],
                        "network": rec["network"], "l2": rec["l2"], "fallback_cells": rec["fallback_cells"],
-                       "launch": rec["launch"], "per_phase_ms_per_step": rec["per_phase_ms_per_step"]},
+                       "launch": rec["launch"], "per_phase_ms_per_step": rec["per_phase_ms_per_step"],
+                       "tcgen05_ms_per_step": rec["tcgen05_ms_per_step"]},
             "roofline": None, "clocks": rec["clocks"], "gpu_launches": rec["gpu_launches"]}
     if rank == 0:
         print(json.dumps(line), flush=True)

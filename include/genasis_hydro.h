@@ -198,7 +198,9 @@ int genasis_hydro_autotune(genasis_hydro_t h, int trial_steps, const char *cache
  * bitwise the same states, dt and time; the step totals sum the cells in
  * tiles of another width and agree to rounding); 0 keeps three launches per
  * step.  With a network attached (genasis_hydro_set_flux_mlp) the option is
- * passed on to its corrected scheme (genasis_learned_set_option). */
+ * passed on to its corrected scheme (genasis_learned_set_option), as is
+ * GENASIS_OPT_MLP_TCGEN05 (defined with genasis_learned_set_option), which
+ * this call also accepts. */
 #define GENASIS_OPT_ONE_LAUNCH 2
 int genasis_hydro_set_option(genasis_hydro_t h, int option, int value);
 /* External force of a linear potential Phi = grad_phi . x (the uniform force
@@ -349,7 +351,15 @@ int genasis_learned_fallbacks(genasis_learned_t l, long long *cells);
  * status and ends the launch).  The face, network and cell arithmetic is that
  * of the per-phase launches, so states, dt, time and fallback counts are
  * bitwise the same.  0 keeps the per-phase launches (a CUDA graph per call
- * shape).  Returns EINVAL for another option or value. */
+ * shape).
+ * GENASIS_OPT_MLP_TCGEN05: 0 (default) runs the network on mma.sync
+ * fragments held in registers; 1 on the 5th-generation tensor cores
+ * (tcgen05.mma, operands in shared memory, FP32 accumulators in tensor
+ * memory, 128 faces per MMA tile).  Both accumulate the same BF16 products in
+ * FP32 in different orders, so their states agree to rounding; for this
+ * 24-64-64-4 network the register-resident form is the faster one.
+ * Returns EINVAL for another option or value. */
+#define GENASIS_OPT_MLP_TCGEN05 3
 int genasis_learned_set_option(genasis_learned_t l, int option, int value);
 /* Kernel launches one step takes: 1 when one launch covers all the steps of a
  * call, else the per-phase count (2 + 2 x 8 with a network and FCT). */
@@ -374,7 +384,10 @@ int genasis_hydro_accumulate_face_flux(genasis_hydro_t h, int stride, double wei
 int genasis_hydro_restrict(genasis_hydro_t h, int factor, float *U_coarse);
 
 /* Network on tensor cores (device pointers; stream may be NULL):
- *   forward:  Y [n][4] from X [n][32] BF16;
+ *   forward:  Y [n][4] from X [n][32] BF16 (X and Y 16-byte aligned, else
+ *             EINVAL), asynchronous: tcgen05 MMAs with FP32 accumulators in
+ *             tensor memory, 128 samples per tile; a tile whose wait for the
+ *             tensor cores runs out (about a second) leaves NaN in its rows;
  *   gradient: grad [param_count] of mean((y - T)^2) over n samples x 4
  *             outputs, and optionally the sum of squared errors (*loss). */
 int genasis_mlp_forward(const float *params, const void *X, long long n, float *Y, void *stream);

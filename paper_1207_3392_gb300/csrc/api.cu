@@ -827,6 +827,12 @@ int genasis_hydro_set_option(genasis_hydro_t h, int option, int value) {
     if (h->lf) return genasis_learned_set_option(h->lf, option, value);
     return GENASIS_OK;
   }
+  if (option == GENASIS_OPT_MLP_TCGEN05) {
+    if (value != 0 && value != 1) return fail(GENASIS_EINVAL, "GENASIS_OPT_MLP_TCGEN05 takes 0 or 1");
+    h->mlp_tc = value;
+    if (h->lf) return genasis_learned_set_option(h->lf, option, value);
+    return GENASIS_OK;
+  }
   return fail(GENASIS_EINVAL, "unknown option %d", option);
 }
 

@@ -153,6 +153,7 @@ int genasis_hydro_set_flux_mlp(genasis_hydro_t h, const void* bf16_weights, size
     const int rc = genasis_learned_create(&d, &l);
     if (rc) return rc;
     genasis_learned_set_option(l, GENASIS_OPT_ONE_LAUNCH, h->one_launch);
+    genasis_learned_set_option(l, GENASIS_OPT_MLP_TCGEN05, h->mlp_tc);
     h->lf = l;
   }
   return genasis_learned_set_params(h->lf, params.data());

@@ -44,6 +44,7 @@ struct genasis_hydro {
   CUtensorMap tmap[3];
   int want_totals = 1;
   int one_launch = 1;  // small 1D meshes: a whole advance in one cooperative launch
+  int mlp_tc = 0;      // attached network: on tcgen05 (1) or mma.sync (0)
   unsigned* adv = nullptr;  // its grid-barrier words [2] (zero between launches), then one dt per CTA
   // cached graphs of `advance`, one per starting state buffer
   cudaGraphExec_t graph[2] = {nullptr, nullptr};

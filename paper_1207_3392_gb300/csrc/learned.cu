@@ -17,6 +17,7 @@
 #include "learned_internal.h"
 #include "learned_kernels.cuh"
 #include "learned_step.cuh"
+#include "mlp_tc.cuh"
 
 namespace gh {
 
@@ -56,15 +57,84 @@ __global__ void __launch_bounds__(256) mlp_infer_kernel(const mlp::InferWeights*
   }
 }
 
-// Inference over n samples with a persistent grid of up to 4 CTAs per SM.
+// Y[n][4] = net(X[n][32]) on the tensor cores (mlp_tc.cuh): a persistent
+// grid over tiles of 128 samples, one sample per thread, weights in shared
+// memory once per CTA, 128 TMEM columns per CTA.  If a wait for the tensor
+// cores runs out, *status (if non-null) gets STATUS_TIMEOUT and the rows of
+// the CTA's remaining tiles are NaN.
+constexpr size_t MLP_TC_SMEM = 50 * 1024;  // at most 4 CTAs per SM: 4 x 128 TMEM columns fit the SM's 512
+static_assert(sizeof(mlptc::Weights) + sizeof(mlptc::Tile) <= MLP_TC_SMEM, "operand images fit");
+
+__global__ void __launch_bounds__(mlptc::M, 4) mlp_infer_tc_kernel(const mlp::InferWeights* __restrict__ Wg,
+                                                                 const __nv_bfloat16* __restrict__ X, long long n,
+                                                                 float* __restrict__ Y, unsigned* status) {
+  extern __shared__ __align__(128) unsigned char smem_mlptc[];
+  auto& W = *reinterpret_cast<mlptc::Weights*>(smem_mlptc);
+  auto& T = *reinterpret_cast<mlptc::Tile*>(smem_mlptc + sizeof(mlptc::Weights));
+  __shared__ unsigned long long mbar;
+  __shared__ uint32_t tmem_slot;
+  const int t = threadIdx.x;
+  mlptc::load_weights(W, Wg);
+  if (t == 0) {
+    tma::mbar_init(&mbar, 1);
+    tma::fence_mbar_init();
+  }
+  if (t < 32) mlptc::tmem_alloc(&tmem_slot, mlptc::TMEM_COLS);
+  mlptc::fence_before();
+  __syncthreads();
+  mlptc::fence_after();
+  const uint32_t tmem = tmem_slot;
+  unsigned phase = 0;
+  const long long ntile = (n + mlptc::M - 1) / mlptc::M;
+  long long tile = blockIdx.x;
+  bool ok = true;
+  for (; tile < ntile; tile += gridDim.x) {
+    const long long r = tile * mlptc::M + t;
+    const uint4* src = reinterpret_cast<const uint4*>(X + r * mlp::KIN);
+#pragma unroll
+    for (int c = 0; c < mlp::KIN / 8; ++c)
+      *reinterpret_cast<uint4*>(T.x + mlptc::core_idx(t, 8 * c, mlp::KIN)) = r < n ? __ldg(src + c) : make_uint4(0, 0, 0, 0);
+    float y[4];
+    ok = mlptc::forward_tile(W, T, &mbar, phase, tmem, 1, t, y);
+    if (!ok) break;
+    if (r < n) *reinterpret_cast<float4*>(Y + r * 4) = make_float4(y[0], y[1], y[2], y[3]);
+  }
+  if (!ok) {  // poison what this CTA did not compute
+    if (t == 0 && status) atomicOr(status, STATUS_TIMEOUT);
+    for (; tile < ntile; tile += gridDim.x) {
+      const long long r = tile * mlptc::M + t;
+      if (r < n) *reinterpret_cast<float4*>(Y + r * 4) = make_float4(NAN, NAN, NAN, NAN);
+    }
+  }
+  mlptc::fence_before();
+  __syncthreads();
+  mlptc::fence_after();
+  if (t < 32) mlptc::tmem_dealloc(tmem, mlptc::TMEM_COLS);
+}
+
+// Inference over n samples with a persistent grid of up to 4 CTAs per SM:
+// on mma.sync fragments in registers (tc = false, the default engine: for a
+// network this small it is twice as fast), or on tcgen05 (tc = true).
 cudaError_t launch_mlp_infer(const mlp::InferWeights* W, const __nv_bfloat16* X, long long n, float* Y,
-                             cudaStream_t st) {
+                             unsigned* status, bool tc, cudaStream_t st) {
+  static bool attr_set = false;
   int dev = 0, sms = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
-  const long long tiles = (n + 15) / 16, want = (tiles + 7) / 8, cap = 4LL * sms;
-  mlp_infer_kernel<<<(int)(want < cap ? want : cap), 256, 0, st>>>(W, X, n, Y);
+  const long long cap = 4LL * sms;
+  if (!tc) {
+    const long long tiles = (n + 15) / 16, want = (tiles + 7) / 8;
+    mlp_infer_kernel<<<(int)(want < cap ? want : cap), 256, 0, st>>>(W, X, n, Y);
+    return cudaGetLastError();
+  }
+  if (!attr_set) {
+    e = cudaFuncSetAttribute(mlp_infer_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MLP_TC_SMEM);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const long long tiles = (n + mlptc::M - 1) / mlptc::M;
+  mlp_infer_tc_kernel<<<(int)(tiles < cap ? tiles : cap), mlptc::M, MLP_TC_SMEM, st>>>(W, X, n, Y, status);
   return cudaGetLastError();
 }
 
@@ -490,13 +560,15 @@ int genasis_mlp_forward(const float* params, const void* X, long long n, float* 
   if (!params || !X || !Y || n < 0) return fail(GENASIS_EINVAL, "mlp_forward: bad argument");
   if (!is_device_ptr(params) || !is_device_ptr(X) || !is_device_ptr(Y))
     return fail(GENASIS_EINVAL, "mlp_forward: params, X and Y must be device pointers");
+  if (((uintptr_t)X & 15u) || ((uintptr_t)Y & 15u))
+    return fail(GENASIS_EINVAL, "mlp_forward: X and Y must be 16-byte aligned (rows are moved as 16-byte vectors)");
   if (n == 0) return GENASIS_OK;
   cudaStream_t st = (cudaStream_t)stream;
   mlp::InferWeights* W = nullptr;
   GH_CK(cudaMallocAsync((void**)&W, sizeof(mlp::InferWeights), st));
   mlp_pack_kernel<<<1, 256, 0, st>>>(params, W);
   cudaError_t e = cudaGetLastError();
-  if (e == cudaSuccess) e = launch_mlp_infer(W, (const __nv_bfloat16*)X, n, Y, st);
+  if (e == cudaSuccess) e = launch_mlp_infer(W, (const __nv_bfloat16*)X, n, Y, nullptr, false, st);
   cudaFreeAsync(W, st);
   GH_CK(e);
   return GENASIS_OK;
@@ -608,7 +680,8 @@ struct genasis_learned {
   unsigned long long* nfallback = nullptr;
   unsigned* all_plain = nullptr;
   int one_launch = 1;           // GENASIS_OPT_ONE_LAUNCH
-  int adv_grid = -1;            // CTAs of the one-launch advance (0: not available; -1: not yet asked)
+  int mlp_tc = 0;               // GENASIS_OPT_MLP_TCGEN05
+  int adv_grid[2] = {-1, -1};   // CTAs of the one-launch advance per MLP engine (0: not available; -1: not yet asked)
   unsigned* adv = nullptr;      // its barrier and all-plain words, then (at 256 B) one double per CTA
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   int g_nsteps = -1;
@@ -651,8 +724,9 @@ constexpr size_t kAdvanceBytes = 256 + kAdvanceMaxGrid * sizeof(double);
 
 bool one_launch_usable(genasis_learned* l) {
   if (!l->one_launch) return false;
-  if (l->adv_grid < 0) l->adv_grid = learned_advance_max_grid(l->solver);
-  return l->adv_grid > 0;
+  int& grid = l->adv_grid[l->mlp_tc];
+  if (grid < 0) grid = learned_advance_max_grid(l->solver, l->mlp_tc != 0);
+  return grid > 0;
 }
 
 // nsteps corrected RK2 steps in one cooperative launch (learned_advance.cu),
@@ -660,7 +734,8 @@ bool one_launch_usable(genasis_learned* l) {
 // FIN_FIXED: fixed_dt).  Needs one_launch_usable(l).
 int enqueue_one_launch(genasis_learned* l, int nsteps, int mode, double cfl, double fixed_dt, double t_end) {
   const long long tiles = (l->nf + LF_ADVANCE_THREADS - 1) / LF_ADVANCE_THREADS;
-  long long grid = l->adv_grid < tiles ? l->adv_grid : tiles;
+  const int max_grid = l->adv_grid[l->mlp_tc];
+  long long grid = max_grid < tiles ? max_grid : tiles;
   if (grid > kAdvanceMaxGrid) grid = kAdvanceMaxGrid;
   if (!l->adv) GH_CK(cudaMalloc((void**)&l->adv, kAdvanceBytes));
   // barrier, all-plain and speed words start at zero in every launch (even after one that gave up)
@@ -699,6 +774,7 @@ int enqueue_one_launch(genasis_learned* l, int nsteps, int mode, double cfl, dou
   P.flag[0] = l->flag[0];
   P.flag[1] = l->flag[1];
   P.W = l->corrected ? l->wimg : nullptr;
+  P.mlp_tc = l->mlp_tc;
   P.fct = l->fct ? 1 : 0;
   P.ylim = l->ylim;
   P.nfallback = l->nfallback;
@@ -754,7 +830,7 @@ int learned_enqueue_step(genasis_learned* l, double cfl, double t_end, double fi
       lf_faces_kernel<SOLVER_HLLC><<<nb, 256, 0, st>>>(l->M, un, kin, l->scal + SCAL_DT, l->F, l->corrected ? l->X : nullptr, l->scale);
     GH_CK(cudaGetLastError());
     if (l->corrected) {
-      GH_CK(launch_mlp_infer(l->wimg, l->X, l->nf, l->dY, st));
+      GH_CK(launch_mlp_infer(l->wimg, l->X, l->nf, l->dY, l->status, l->mlp_tc != 0, st));
     }
     UpdateArgs A;
     A.M = l->M;
@@ -1057,9 +1133,15 @@ int genasis_learned_step(genasis_learned_t l, double dt) {
 
 int genasis_learned_set_option(genasis_learned_t l, int option, int value) {
   if (!l) return fail(GENASIS_EINVAL, "NULL handle");
-  if (option != GENASIS_OPT_ONE_LAUNCH) return fail(GENASIS_EINVAL, "learned_set_option: unknown option %d", option);
-  if (value != 0 && value != 1) return fail(GENASIS_EINVAL, "GENASIS_OPT_ONE_LAUNCH takes 0 or 1");
-  l->one_launch = value;
+  if (option != GENASIS_OPT_ONE_LAUNCH && option != GENASIS_OPT_MLP_TCGEN05)
+    return fail(GENASIS_EINVAL, "learned_set_option: unknown option %d", option);
+  if (value != 0 && value != 1) return fail(GENASIS_EINVAL, "learned_set_option: option %d takes 0 or 1", option);
+  if (option == GENASIS_OPT_ONE_LAUNCH) {
+    l->one_launch = value;
+  } else if (l->mlp_tc != value) {
+    l->mlp_tc = value;
+    drop_graphs(l);
+  }
   return GENASIS_OK;
 }
 

@@ -12,9 +12,11 @@
 //   maximum does not depend on the order) and takes the same dt; CTA 0
 //   stores dt and t
 //   per stage:
-//     plain flux and features of a tile of 256 faces; each warp runs the
-//     network on its own 32 faces (BF16 weights in shared memory, loaded
-//     once per launch)                                           barrier
+//     plain flux and features of a tile of 256 faces, and the network on
+//     them (BF16 weights in shared memory, loaded once per launch): each warp
+//     on its own 32 faces with mma.sync, or, with the tcgen05 engine, each
+//     half of the CTA on its 128 faces (accumulators in TMEM, mlp_tc.cuh)
+//                                                                barrier
 //     FCT ratios of every cell (when limiting)                   barrier
 //     corrected update of every cell                             barrier
 //     only if a cell failed: the three widening passes and, if failures
@@ -33,6 +35,7 @@
 #include "grid_sync.cuh"
 #include "learned_internal.h"
 #include "learned_step.cuh"
+#include "mlp_tc.cuh"
 
 namespace gh {
 
@@ -41,13 +44,35 @@ namespace {
 constexpr int LFA_WARPS = LF_ADVANCE_THREADS / 32;
 constexpr int LFA_PASSES = 3;  // widening passes, as in the per-phase path
 
-template <int SOLVER>
-__global__ void __launch_bounds__(LF_ADVANCE_THREADS, 2) lf_advance_kernel(LfAdvanceArgs P) {
-  __shared__ mlp::InferWeights W;
-  __shared__ __align__(16) __nv_bfloat16 xs[LF_ADVANCE_THREADS][mlp::KIN];  // features of the tile's faces
-  __shared__ double red[LFA_WARPS];
+// tcgen05 engine: one group of four warps per 128 faces of a tile (the
+// network's MMA tile).
+constexpr int LFA_GROUPS = LF_ADVANCE_THREADS / mlptc::M;
+static_assert(LFA_GROUPS == 2, "a 256-face tile is two network tiles");
+// Dynamic shared memory, per engine: mma.sync: the BF16 weight image and one
+// feature row per thread; tcgen05: the weights as B operands and each
+// group's operand tile.  Sized so that at most 2 CTAs fit on an SM (with
+// tcgen05 their 2 x 256 TMEM columns fill the SM's 512: a third CTA could not
+// allocate while the others wait for it at a grid barrier).
+struct SmemSync {
+  mlp::InferWeights W;
+  __align__(16) __nv_bfloat16 xs[LF_ADVANCE_THREADS][mlp::KIN];
+};
+constexpr size_t LFA_SMEM = 80 * 1024;
+static_assert(sizeof(mlptc::Weights) + LFA_GROUPS * sizeof(mlptc::Tile) <= LFA_SMEM, "operand images fit");
+static_assert(sizeof(SmemSync) <= LFA_SMEM, "weight image and feature rows fit");
+static_assert(3 * LFA_SMEM > 228 * 1024, "at most two CTAs per SM");
+constexpr uint32_t LFA_TMEM_COLS = LFA_GROUPS * mlptc::TMEM_COLS;
+
+// Every step of the launch; returns early (on every thread of the CTA
+// together) when a grid barrier gives up.  TC: the network on tcgen05 (W,
+// tiles, mbar, tmem), else on mma.sync (S).
+template <int SOLVER, bool TC>
+__device__ __forceinline__ void lf_advance_body(const LfAdvanceArgs& P, SmemSync& S, const mlptc::Weights& W,
+                                                mlptc::Tile* tiles, unsigned long long* mbar, uint32_t tmem,
+                                                double* red) {
   const Mesh2& M = P.M;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, bx = blockIdx.x;
+  const int grp = tid / mlptc::M, row = tid % mlptc::M;  // network group and sample row
   const unsigned nb = gridDim.x;
   const long long ncell = (long long)M.nx * M.ny;
   const long long nxf = (long long)(M.nx + 1) * M.ny, nf = nxf + (long long)M.nx * (M.ny + 1);
@@ -55,7 +80,12 @@ __global__ void __launch_bounds__(LF_ADVANCE_THREADS, 2) lf_advance_kernel(LfAdv
   const bool corr = P.W != nullptr;
   unsigned* bar = P.sync;
   unsigned long long* speed_slot = reinterpret_cast<unsigned long long*>(P.sync + 8);  // one per step parity
-  if (corr) mlp::copy_weights(W, P.W);
+  // this thread's feature row: in its group's operand tile (tcgen05,
+  // core-matrix layout: 16-byte chunks 8 uint4 apart), or a plain row
+  __nv_bfloat16* xrow = TC ? tiles[grp].x + mlptc::core_idx(row, 0, mlp::KIN) : S.xs[tid];
+  constexpr int XSTRIDE = TC ? 8 : 1;
+  unsigned phase = 0;    // of the group's mbarrier
+  bool mlp_ok = true;    // the group's tensor-core waits have all completed
   unsigned my_gen = 0;
   bool failed = false;
   if (tid == 0) my_gen = atomicAdd(bar + 1, 0u);  // the generation at launch (no CTA can move it yet)
@@ -106,8 +136,28 @@ __global__ void __launch_bounds__(LF_ADVANCE_THREADS, 2) lf_advance_kernel(LfAdv
       // plain fluxes, and features and network outputs, of every face
       for (long long base = first; base < nf; base += stride) {
         const long long f = base + tid;
-        if (f < nf) lf_face<SOLVER, true>(M, un, kin, dt, f, nxf, nf, P.F, corr ? xs[tid] : nullptr, P.scale);
-        if (corr) {
+        if (f < nf) {
+          lf_face<SOLVER, true>(M, un, kin, dt, f, nxf, nf, P.F, corr ? xrow : nullptr, P.scale, XSTRIDE);
+        } else if (corr && TC) {
+#pragma unroll
+          for (int c = 0; c < mlp::KIN / 8; ++c)
+            *reinterpret_cast<uint4*>(xrow + 8 * XSTRIDE * c) = make_uint4(0, 0, 0, 0);
+        }
+        if (corr && TC) {
+          // the group's 128 faces through the network on the tensor cores
+          float y[4] = {NAN, NAN, NAN, NAN};
+          if (mlp_ok) {
+            mlp_ok = mlptc::forward_tile(W, tiles[grp], mbar + grp, phase, tmem + (uint32_t)(grp * mlptc::TMEM_COLS),
+                                         1 + grp, row, y);
+            if (!mlp_ok) {
+              y[0] = y[1] = y[2] = y[3] = NAN;
+              if (row == 0) atomicOr(P.status, STATUS_TIMEOUT);
+            }
+          }
+          if (f < nf) *reinterpret_cast<float4*>(P.dY + 4 * f) = make_float4(y[0], y[1], y[2], y[3]);
+        } else if (corr) {
+          // each warp runs the network on its own 32 faces (rows past nf
+          // read as zero), in two mma.sync tiles of 16
           __syncwarp();
 #pragma unroll 1
           for (int h = 0; h < 2; ++h) {
@@ -115,8 +165,8 @@ __global__ void __launch_bounds__(LF_ADVANCE_THREADS, 2) lf_advance_kernel(LfAdv
             if (left <= 0) break;
             const int rows = left < 16 ? (int)left : 16;
             mlp::Forward Fw;
-            mlp::load_x(Fw, &xs[32 * warp + 16 * h][0], rows);
-            mlp::forward(Fw, W);
+            mlp::load_x(Fw, &S.xs[32 * warp + 16 * h][0], rows);
+            mlp::forward(Fw, S.W);
             const int g = lane >> 2, q = lane & 3;
             if (q < 2) {
               if (g < rows) {
@@ -189,20 +239,55 @@ __global__ void __launch_bounds__(LF_ADVANCE_THREADS, 2) lf_advance_kernel(LfAdv
   }
 }
 
-const void* advance_fn(int solver) {
-  return solver == SOLVER_HLL ? reinterpret_cast<const void*>(&lf_advance_kernel<SOLVER_HLL>)
-                              : reinterpret_cast<const void*>(&lf_advance_kernel<SOLVER_HLLC>);
+template <int SOLVER, bool TC>
+__global__ void __launch_bounds__(LF_ADVANCE_THREADS, 2) lf_advance_kernel(LfAdvanceArgs P) {
+  extern __shared__ __align__(128) unsigned char lfa_smem[];
+  auto& S = *reinterpret_cast<SmemSync*>(lfa_smem);
+  auto& W = *reinterpret_cast<mlptc::Weights*>(lfa_smem);
+  auto* tiles = reinterpret_cast<mlptc::Tile*>(lfa_smem + sizeof(mlptc::Weights));
+  __shared__ unsigned long long mbar[LFA_GROUPS];
+  __shared__ uint32_t tmem_slot;
+  __shared__ double red[LFA_WARPS];
+  const bool corr = P.W != nullptr;
+  if (corr && TC) {
+    mlptc::load_weights(W, P.W);
+    if (threadIdx.x < LFA_GROUPS) tma::mbar_init(mbar + threadIdx.x, 1);
+    tma::fence_mbar_init();
+    if (threadIdx.x < 32) mlptc::tmem_alloc(&tmem_slot, LFA_TMEM_COLS);
+    mlptc::fence_before();
+  } else if (corr) {
+    mlp::copy_weights(S.W, P.W);
+  }
+  __syncthreads();
+  if (TC) mlptc::fence_after();
+  lf_advance_body<SOLVER, TC>(P, S, W, tiles, mbar, corr && TC ? tmem_slot : 0u, red);
+  if (corr && TC) {  // no MMA is in flight here: every network tile waited for its own
+    mlptc::fence_before();
+    __syncthreads();
+    mlptc::fence_after();
+    if (threadIdx.x < 32) mlptc::tmem_dealloc(tmem_slot, LFA_TMEM_COLS);
+  }
 }
+
+template <bool TC>
+const void* advance_fn_t(int solver) {
+  return solver == SOLVER_HLL ? reinterpret_cast<const void*>(&lf_advance_kernel<SOLVER_HLL, TC>)
+                              : reinterpret_cast<const void*>(&lf_advance_kernel<SOLVER_HLLC, TC>);
+}
+const void* advance_fn(int solver, bool tc) { return tc ? advance_fn_t<true>(solver) : advance_fn_t<false>(solver); }
 
 }  // namespace
 
-int learned_advance_max_grid(int solver) {
+int learned_advance_max_grid(int solver, bool mlp_tc) {
   int dev = 0, sms = 0, coop = 0, per_sm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, advance_fn(solver), LF_ADVANCE_THREADS, 0) != cudaSuccess)
+  const void* fn = advance_fn(solver, mlp_tc);
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LFA_SMEM) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, LF_ADVANCE_THREADS, LFA_SMEM) != cudaSuccess)
     return 0;
+  if (mlp_tc && per_sm > 2) per_sm = 2;  // the TMEM budget (the shared-memory size already ensures it)
   return per_sm * sms;
 }
 
@@ -210,7 +295,8 @@ cudaError_t launch_learned_advance(const LfAdvanceArgs& P, int solver, int grid,
   LfAdvanceArgs a = P;
   void* args[] = {&a};
   // cooperative: the CTAs wait on one another, so all must be resident
-  return cudaLaunchCooperativeKernel(advance_fn(solver), dim3(grid), dim3(LF_ADVANCE_THREADS), args, 0, st);
+  return cudaLaunchCooperativeKernel(advance_fn(solver, P.mlp_tc != 0), dim3(grid), dim3(LF_ADVANCE_THREADS), args,
+                                     LFA_SMEM, st);
 }
 
 }  // namespace gh

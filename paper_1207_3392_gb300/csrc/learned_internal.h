@@ -32,13 +32,14 @@ struct LfAdvanceArgs {
                                // [8..11] two 64-bit speed maxima; the first 48 bytes zero at launch
   double* dts;                 // one per CTA
   int nsteps;
+  int mlp_tc;                  // network on tcgen05 (1) or mma.sync (0)
 };
 
 // Largest cooperative grid of the one-launch advance (CTAs of
 // LF_ADVANCE_THREADS threads that fit on the device at once), 0 if none.
 constexpr int LF_ADVANCE_THREADS = 256;
-int learned_advance_max_grid(int solver);
-// Launch it with grid CTAs (1 <= grid <= learned_advance_max_grid).
+int learned_advance_max_grid(int solver, bool mlp_tc);
+// Launch it with grid CTAs (1 <= grid <= learned_advance_max_grid for P.mlp_tc).
 cudaError_t launch_learned_advance(const LfAdvanceArgs& P, int solver, int grid, cudaStream_t st);
 
 cudaError_t launch_face_flux_accumulate(const Mesh2& M, int solver, const float* un, const float* k, const double* dtp,

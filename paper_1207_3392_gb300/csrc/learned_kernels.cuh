@@ -91,9 +91,11 @@ __device__ __forceinline__ void plain_face_flux(const Mesh2& M, const float (&w)
 // rho/rho_bar - 1, v_n/c_bar, v_t/c_bar, p/p_bar - 1 with rho_bar, p_bar the
 // stencil means and c_bar = sqrt(gamma p_bar / rho_bar); scales
 // (rho_bar c_bar, rho_bar c_bar^2, rho_bar c_bar^2, rho_bar c_bar^3).
+// x receives the four 16-byte chunks of the row xstride uint4 apart (1: a
+// plain row; 8: a row of the tensor cores' core-matrix layout).
 template <int Q>
 __device__ __forceinline__ void face_features(const Mesh2& M, const float (&s)[6][4], __nv_bfloat16* __restrict__ x,
-                                              float* __restrict__ scale) {
+                                              float* __restrict__ scale, int xstride = 1) {
   // Every rounding is spelt out (the pressures as separate products, the
   // ratios minus one as fused multiply-adds), so that each kernel that inlines
   // this computes bitwise the same features.
@@ -118,7 +120,8 @@ __device__ __forceinline__ void face_features(const Mesh2& M, const float (&s)[6
   for (int k = 12; k < 16; ++k) packed[k] = 0u;
   uint4* dst = reinterpret_cast<uint4*>(x);
 #pragma unroll
-  for (int k = 0; k < 4; ++k) dst[k] = make_uint4(packed[4 * k], packed[4 * k + 1], packed[4 * k + 2], packed[4 * k + 3]);
+  for (int k = 0; k < 4; ++k)
+    dst[k * xstride] = make_uint4(packed[4 * k], packed[4 * k + 1], packed[4 * k + 2], packed[4 * k + 3]);
   const float rc = rbar * cbar;
   scale[0] = rc;
   scale[1] = rc * cbar;

@@ -48,10 +48,12 @@ __device__ __forceinline__ float4 lf_ld4(const float* p) {
 
 // Plain flux of face f (x faces (nx+1) x ny first, then y faces nx x (ny+1))
 // of the state un (+ dt k) into F [nf][4]; with x non-null also the face's 32
-// BF16 features at x and its 4 flux scales at scale + 4 f.
+// BF16 features at x (16-byte chunks xstride uint4 apart) and its 4 flux
+// scales at scale + 4 f.
 template <int SOLVER, bool COH>
 __device__ __forceinline__ void lf_face(const Mesh2& M, const float* un, const float* k, float dt, long long f,
-                                        long long nxf, long long nf, float* F, __nv_bfloat16* x, float* scale) {
+                                        long long nxf, long long nf, float* F, __nv_bfloat16* x, float* scale,
+                                        int xstride = 1) {
   float s[6][4], Fl[4];
   if (f < nxf) {
     const int i = (int)(f % (M.nx + 1)), j = (int)(f / (M.nx + 1));
@@ -59,7 +61,7 @@ __device__ __forceinline__ void lf_face(const Mesh2& M, const float* un, const f
     for (int c = 0; c < 6; ++c) cell_prim<COH>(M, un, k, dt, i - 3 + c, j, s[c]);
     const float(&w)[4][4] = *reinterpret_cast<const float(*)[4][4]>(&s[1][0]);
     plain_face_flux<0, SOLVER>(M, w, i - 1, Fl);
-    if (x) face_features<0>(M, s, x, scale + f * 4);
+    if (x) face_features<0>(M, s, x, scale + f * 4, xstride);
   } else {
     const long long gidx = f - nxf;
     const int i = (int)(gidx % M.nx), j = (int)(gidx / M.nx);
@@ -67,7 +69,7 @@ __device__ __forceinline__ void lf_face(const Mesh2& M, const float* un, const f
     for (int c = 0; c < 6; ++c) cell_prim<COH>(M, un, k, dt, i, j - 3 + c, s[c]);
     const float(&w)[4][4] = *reinterpret_cast<const float(*)[4][4]>(&s[1][0]);
     plain_face_flux<1, SOLVER>(M, w, j - 1, Fl);
-    if (x) face_features<1>(M, s, x, scale + f * 4);
+    if (x) face_features<1>(M, s, x, scale + f * 4, xstride);
   }
   reinterpret_cast<float4*>(F)[f] = make_float4(Fl[0], Fl[1], Fl[2], Fl[3]);
 }

@@ -22,6 +22,7 @@ BC_PERIODIC, BC_REFLECT, BC_OUTFLOW = 0, 1, 2
 FP64, FP32_MIXED, FP64_DW = 0, 1, 2  # FP64_DW: double-word FP32 pairs on the device, FP64 on the host
 OPT_STEP_TOTALS = 1
 OPT_ONE_LAUNCH = 2
+OPT_MLP_TCGEN05 = 3
 
 
 class HydroError(RuntimeError):
@@ -336,8 +337,13 @@ class Hydro:
         check(load().genasis_hydro_set_option(self._h, OPT_STEP_TOTALS, int(bool(enabled))))
 
     def set_one_launch(self, enabled):
-        """Small 1D meshes: all steps of a call in one cooperative launch (default on)."""
+        """Small 1D meshes and an attached network: all steps of a call in one
+        cooperative launch (default on)."""
         check(load().genasis_hydro_set_option(self._h, OPT_ONE_LAUNCH, int(bool(enabled))))
+
+    def set_mlp_tcgen05(self, enabled):
+        """An attached network on tcgen05 (True) or mma.sync (False, default)."""
+        check(load().genasis_hydro_set_option(self._h, OPT_MLP_TCGEN05, int(bool(enabled))))
 
     def status(self):
         return check(load().genasis_hydro_status(self._h))
@@ -788,6 +794,11 @@ class Learned:
         """All steps of a call in one cooperative launch (default on) or the
         per-phase launches; the results are bitwise the same."""
         check(load().genasis_learned_set_option(self._h, OPT_ONE_LAUNCH, int(bool(enabled))))
+
+    def set_mlp_tcgen05(self, enabled):
+        """Run the network on tcgen05 (True) or on mma.sync (False, the
+        default); the states agree to rounding."""
+        check(load().genasis_learned_set_option(self._h, OPT_MLP_TCGEN05, int(bool(enabled))))
 
     def launches_per_step(self):
         return check(load().genasis_learned_launches_per_step(self._h))

@@ -138,10 +138,12 @@ def test_learned_solver_without_network_matches_oracle():
     check(Ug, Uo, 2, TOL_FP32, "learned solver, no network")
 
 
-def test_learned_solver_matches_reference_corrected_step():
+@pytest.mark.parametrize("engine", ["mma.sync", "tcgen05"])
+def test_learned_solver_matches_reference_corrected_step(engine):
     pr = P.kelvin_helmholtz(48, seed=2)
     th = _random_net(8, last=0.02)
     L = H.Learned(pr, params=th.astype(np.float32))
+    L.set_mlp_tcgen05(engine == "tcgen05")
     L.set_fct(False)
     L.set_primitive(pr.rho, pr.vel, pr.p)
     g = O.Grid(pr)
@@ -198,12 +200,15 @@ def test_learned_solver_conserves_and_falls_back():
     L.close()
 
 
-def test_fct_limited_solver_matches_reference():
+@pytest.mark.parametrize("engine", ["mma.sync", "tcgen05"])
+def test_fct_limited_solver_matches_reference(engine):
     """Flux-corrected transport on the correction: the GPU step against the
-    reference FCT step, for a network whose raw correction is large."""
+    reference FCT step, for a network whose raw correction is large, with the
+    network on either engine."""
     pr = P.kelvin_helmholtz(48, seed=11)
     th = _random_net(12, last=0.3)
     L = H.Learned(pr, params=th.astype(np.float32))
+    L.set_mlp_tcgen05(engine == "tcgen05")
     L.set_primitive(pr.rho, pr.vel, pr.p)
     g = O.Grid(pr)
     U = O.initial_state(pr, g)
@@ -417,7 +422,7 @@ ONE_LAUNCH_CASES = {
 }
 
 
-def _learned_pair(case):
+def _learned_pair(case, tc=False):
     mk_pr, mk_net, fct, ylim, solver = ONE_LAUNCH_CASES[case]
     pr = mk_pr()
     th = mk_net()
@@ -425,6 +430,7 @@ def _learned_pair(case):
     for one in (False, True):
         L = H.Learned(pr, params=None if th is None else th.astype(np.float32), solver=solver)
         L.set_one_launch(one)
+        L.set_mlp_tcgen05(tc)
         L.set_fct(fct)
         if ylim is not None:
             L.set_limit(ylim)
@@ -433,12 +439,14 @@ def _learned_pair(case):
     return pr, th, out
 
 
+@pytest.mark.parametrize("engine", ["mma.sync", "tcgen05"])
 @pytest.mark.parametrize("case", sorted(ONE_LAUNCH_CASES))
-def test_one_launch_advance_is_the_per_phase_advance(case):
+def test_one_launch_advance_is_the_per_phase_advance(case, engine):
     """All steps of a call in one cooperative launch give bitwise the states,
-    times and fallback counts of the per-phase launches: CFL steps (the last
-    one clamped at t_end), then fixed-dt steps."""
-    pr, th, (Lp, L1) = _learned_pair(case)
+    times and fallback counts of the per-phase launches, with the network on
+    either engine: CFL steps (the last one clamped at t_end), then fixed-dt
+    steps."""
+    pr, th, (Lp, L1) = _learned_pair(case, tc=engine == "tcgen05")
     assert L1.launches_per_step() == 1
     assert Lp.launches_per_step() == (2 + 2 * (2 if th is None else (8 if ONE_LAUNCH_CASES[case][2] else 7)))
     tp = Lp.advance(3, 0.45)
@@ -486,3 +494,17 @@ def test_one_launch_handle_with_network_is_the_per_phase_handle():
     for U, t in res[1:]:
         np.testing.assert_array_equal(U, res[0][0])
         assert t == res[0][1]
+    # the network engine passes through the same way, before or after attaching
+    tc = []
+    for before in (True, False):
+        h = H.Hydro.from_problem(pr, precision=H.FP32_MIXED)
+        if before:
+            h.set_mlp_tcgen05(True)
+        h.set_flux_mlp(bits)
+        if not before:
+            h.set_mlp_tcgen05(True)
+        h.advance(4, 0.45)
+        tc.append(h.get_conserved())
+        h.close()
+    np.testing.assert_array_equal(tc[0], tc[1])
+    check(tc[0].astype(np.float64), res[0][0].astype(np.float64), 2, TOL_BF16, "tcgen05 against mma.sync")
