@@ -710,6 +710,7 @@ def measure_learned(steps, warmup, stream, sampler=None):
         return res
 
     ms_pp, _, lps_pp, _ = timed(False, None)
+    ms_pp_tc, _, _, _ = timed(False, None, tc=True)
     ms_tc, _, _, _ = timed(True, None, tc=True)
     ms, fb, lps, clocks = timed(True, sampler)
     cells = 256 * 256
@@ -721,7 +722,7 @@ def measure_learned(steps, warmup, stream, sampler=None):
             "per_phase_ms_per_step": ms_pp, "per_phase_launches_per_step": lps_pp,
             # the same one-launch step with the network on tcgen05 (accumulators
             # in tensor memory) instead of mma.sync fragments in registers
-            "tcgen05_ms_per_step": ms_tc,
+            "tcgen05_ms_per_step": ms_tc, "per_phase_tcgen05_ms_per_step": ms_pp_tc,
             # one advance call per step
             "gpu_launches": steps * lps, "clocks": clocks}
 
@@ -741,7 +742,8 @@ def run_learned(args):
             "config": {"workload": "learned_kh2d_256^2_hllc_fct", "cells": rec["cells"], "faces": 2 * rec["cells"],
                        "network": rec["network"], "l2": rec["l2"], "fallback_cells": rec["fallback_cells"],
                        "launch": rec["launch"], "per_phase_ms_per_step": rec["per_phase_ms_per_step"],
-                       "tcgen05_ms_per_step": rec["tcgen05_ms_per_step"]},
+                       "tcgen05_ms_per_step": rec["tcgen05_ms_per_step"],
+                       "per_phase_tcgen05_ms_per_step": rec["per_phase_tcgen05_ms_per_step"]},
             "roofline": None, "clocks": rec["clocks"], "gpu_launches": rec["gpu_launches"]}
     if rank == 0:
         print(json.dumps(line), flush=True)

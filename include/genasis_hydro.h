@@ -181,6 +181,10 @@ int genasis_hydro_get_tile(genasis_hydro_t h, int *info);
 
 /* Time every compiled tile shape (and a few plane counts) on the current
  * state for `trial_steps` steps each, keep the fastest, restore the state.
+ * It chooses among the tiles that give bitwise the same states as the
+ * default tile; the 3D FP32 tiles that take two march planes per thread on
+ * the packed FP32 instructions (tiles 11 to 13: the same arithmetic with
+ * other roundings) are chosen only with genasis_hydro_set_tile.
  * If cache_path is non-NULL the choice is read from / appended to that text
  * file, keyed by (ndim, n, precision, solver).  Synchronises. */
 int genasis_hydro_autotune(genasis_hydro_t h, int trial_steps, const char *cache_path);

@@ -983,6 +983,9 @@ int genasis_hydro_autotune(genasis_hydro_t h, int trial_steps, const char* cache
         !stage_variant(h->ndim, h->prec, h->solver, 2, tile, &probe2))
       continue;  // not compiled for this solver
     if ((probe.tma || probe2.tma) && !tma_usable(h)) continue;  // TMA tile on an unaligned mesh
+    // the paired tiles round differently (explicit roundings, not the
+    // compiler's fused products): tuning keeps the bits of the default tile
+    if (probe.pair || probe2.pair) continue;
     std::vector<int> kcs = {0};
     if (h->ndim == 2)  // small 2D meshes need short chunks to fill the GPU
       for (int kc : {2, 4, 8})
