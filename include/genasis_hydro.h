@@ -245,6 +245,17 @@ int genasis_hydro_get_centers(genasis_hydro_t h, int axis, double *x);
  * frees a small buffer, uses a private stream, takes ~0.5 s; synchronises. */
 int genasis_measure_fma_rate(int kind, double *tflops);
 
+/* Check that the kernels' bounded waits give up instead of hanging (the paper
+ * has no counterpart: a diagnostic of this library).  Runs two waits that
+ * cannot complete, on the legacy default stream: a grid barrier of two CTAs of
+ * which only one arrives (the barrier of the one-launch advances), and an
+ * mbarrier that nothing arrives on (the wait of the TMA and tcgen05 kernels).
+ * status[0], status[1] receive their status words: 2 (the timeout bit) when
+ * the wait gave up, 0 if it (impossibly) completed; seconds[0], seconds[1]
+ * their event-timed durations, about one second each.  No fault or trap is
+ * involved and the context stays usable.  Synchronises; ~2 s. */
+int genasis_check_bounded_waits(unsigned *status, double *seconds);
+
 /* ---------------------------------------------------------------------------
  * The batched and learned workloads behind genasis_hydro_t.
  *

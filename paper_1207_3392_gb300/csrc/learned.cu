@@ -58,50 +58,57 @@ __global__ void __launch_bounds__(256) mlp_infer_kernel(const mlp::InferWeights*
 }
 
 // Y[n][4] = net(X[n][32]) on the tensor cores (mlp_tc.cuh): a persistent
-// grid over tiles of 128 samples, one sample per thread, weights in shared
-// memory once per CTA, 128 TMEM columns per CTA.  If a wait for the tensor
-// cores runs out, *status (if non-null) gets STATUS_TIMEOUT and the rows of
-// the CTA's remaining tiles are NaN.
-constexpr size_t MLP_TC_SMEM = 50 * 1024;  // at most 4 CTAs per SM: 4 x 128 TMEM columns fit the SM's 512
-static_assert(sizeof(mlptc::Weights) + sizeof(mlptc::Tile) <= MLP_TC_SMEM, "operand images fit");
+// grid over tiles of MLP_TC_GROUPS x 128 samples, one sample per thread; each
+// group of four warps runs its 128 samples with its own mbarrier, operand tile
+// and 128 TMEM columns.  The weights sit in shared memory once per CTA.  One
+// CTA per SM, which takes all 512 TMEM columns: the shared-memory request
+// keeps a second CTA off the SM.  If a wait for the tensor cores runs out,
+// *status (if non-null) gets STATUS_TIMEOUT and the rows of the group's
+// remaining tiles are NaN.
+constexpr int MLP_TC_GROUPS = 4;
+constexpr int MLP_TC_THREADS = MLP_TC_GROUPS * mlptc::M;
+constexpr size_t MLP_TC_SMEM = 120 * 1024;  // > 228 KB / 2: one CTA per SM
+static_assert(sizeof(mlptc::Weights) + MLP_TC_GROUPS * sizeof(mlptc::Tile) <= MLP_TC_SMEM, "operand images fit");
+static_assert(MLP_TC_GROUPS * mlptc::TMEM_COLS <= 512, "the CTA's TMEM fits the SM");
 
-__global__ void __launch_bounds__(mlptc::M, 4) mlp_infer_tc_kernel(const mlp::InferWeights* __restrict__ Wg,
-                                                                 const __nv_bfloat16* __restrict__ X, long long n,
-                                                                 float* __restrict__ Y, unsigned* status) {
+__global__ void __launch_bounds__(MLP_TC_THREADS, 1) mlp_infer_tc_kernel(const mlp::InferWeights* __restrict__ Wg,
+                                                                       const __nv_bfloat16* __restrict__ X,
+                                                                       long long n, float* __restrict__ Y,
+                                                                       unsigned* status) {
   extern __shared__ __align__(128) unsigned char smem_mlptc[];
   auto& W = *reinterpret_cast<mlptc::Weights*>(smem_mlptc);
-  auto& T = *reinterpret_cast<mlptc::Tile*>(smem_mlptc + sizeof(mlptc::Weights));
-  __shared__ unsigned long long mbar;
+  auto* tiles = reinterpret_cast<mlptc::Tile*>(smem_mlptc + sizeof(mlptc::Weights));
+  __shared__ unsigned long long mbar[MLP_TC_GROUPS];
   __shared__ uint32_t tmem_slot;
-  const int t = threadIdx.x;
+  const int grp = threadIdx.x / mlptc::M, t = threadIdx.x % mlptc::M;
   mlptc::load_weights(W, Wg);
-  if (t == 0) {
-    tma::mbar_init(&mbar, 1);
-    tma::fence_mbar_init();
-  }
-  if (t < 32) mlptc::tmem_alloc(&tmem_slot, mlptc::TMEM_COLS);
+  if (threadIdx.x < MLP_TC_GROUPS) tma::mbar_init(mbar + threadIdx.x, 1);
+  tma::fence_mbar_init();
+  if (threadIdx.x < 32) mlptc::tmem_alloc(&tmem_slot, MLP_TC_GROUPS * mlptc::TMEM_COLS);
   mlptc::fence_before();
   __syncthreads();
   mlptc::fence_after();
-  const uint32_t tmem = tmem_slot;
+  const uint32_t tmem = tmem_slot + (uint32_t)(grp * mlptc::TMEM_COLS);
+  mlptc::Tile& T = tiles[grp];
   unsigned phase = 0;
-  const long long ntile = (n + mlptc::M - 1) / mlptc::M;
-  long long tile = blockIdx.x;
+  const long long ntile = (n + mlptc::M - 1) / mlptc::M;  // 128-sample tiles, group-strided
+  long long tile = (long long)blockIdx.x * MLP_TC_GROUPS + grp;
+  const long long step = (long long)gridDim.x * MLP_TC_GROUPS;
   bool ok = true;
-  for (; tile < ntile; tile += gridDim.x) {
+  for (; tile < ntile; tile += step) {
     const long long r = tile * mlptc::M + t;
     const uint4* src = reinterpret_cast<const uint4*>(X + r * mlp::KIN);
 #pragma unroll
     for (int c = 0; c < mlp::KIN / 8; ++c)
       *reinterpret_cast<uint4*>(T.x + mlptc::core_idx(t, 8 * c, mlp::KIN)) = r < n ? __ldg(src + c) : make_uint4(0, 0, 0, 0);
     float y[4];
-    ok = mlptc::forward_tile(W, T, &mbar, phase, tmem, 1, t, y);
+    ok = mlptc::forward_tile(W, T, mbar + grp, phase, tmem, 1 + grp, t, y);
     if (!ok) break;
     if (r < n) *reinterpret_cast<float4*>(Y + r * 4) = make_float4(y[0], y[1], y[2], y[3]);
   }
-  if (!ok) {  // poison what this CTA did not compute
+  if (!ok) {  // poison what this group did not compute
     if (t == 0 && status) atomicOr(status, STATUS_TIMEOUT);
-    for (; tile < ntile; tile += gridDim.x) {
+    for (; tile < ntile; tile += step) {
       const long long r = tile * mlptc::M + t;
       if (r < n) *reinterpret_cast<float4*>(Y + r * 4) = make_float4(NAN, NAN, NAN, NAN);
     }
@@ -109,12 +116,12 @@ __global__ void __launch_bounds__(mlptc::M, 4) mlp_infer_tc_kernel(const mlp::In
   mlptc::fence_before();
   __syncthreads();
   mlptc::fence_after();
-  if (t < 32) mlptc::tmem_dealloc(tmem, mlptc::TMEM_COLS);
+  if (threadIdx.x < 32) mlptc::tmem_dealloc(tmem_slot, MLP_TC_GROUPS * mlptc::TMEM_COLS);
 }
 
-// Inference over n samples with a persistent grid of up to 4 CTAs per SM:
-// on mma.sync fragments in registers (tc = false, the default engine: for a
-// network this small it is twice as fast), or on tcgen05 (tc = true).
+// Inference over n samples with a persistent grid: on mma.sync fragments in
+// registers (tc = false, the default engine, up to 4 CTAs per SM), or on
+// tcgen05 (tc = true, one CTA per SM).
 cudaError_t launch_mlp_infer(const mlp::InferWeights* W, const __nv_bfloat16* X, long long n, float* Y,
                              unsigned* status, bool tc, cudaStream_t st) {
   static bool attr_set = false;
@@ -133,8 +140,9 @@ cudaError_t launch_mlp_infer(const mlp::InferWeights* W, const __nv_bfloat16* X,
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  const long long tiles = (n + mlptc::M - 1) / mlptc::M;
-  mlp_infer_tc_kernel<<<(int)(tiles < cap ? tiles : cap), mlptc::M, MLP_TC_SMEM, st>>>(W, X, n, Y, status);
+  const long long tiles = (n + MLP_TC_THREADS - 1) / MLP_TC_THREADS, one_per_sm = sms;
+  mlp_infer_tc_kernel<<<(int)(tiles < one_per_sm ? tiles : one_per_sm), MLP_TC_THREADS, MLP_TC_SMEM, st>>>(W, X, n, Y,
+                                                                                                         status);
   return cudaGetLastError();
 }
 
@@ -733,7 +741,8 @@ bool one_launch_usable(genasis_learned* l) {
 // dt by the finalize rule `mode` (FIN_CFL: cfl * dt_CFL clamped at t_end > 0;
 // FIN_FIXED: fixed_dt).  Needs one_launch_usable(l).
 int enqueue_one_launch(genasis_learned* l, int nsteps, int mode, double cfl, double fixed_dt, double t_end) {
-  const long long tiles = (l->nf + LF_ADVANCE_THREADS - 1) / LF_ADVANCE_THREADS;
+  const long long threads = lf_advance_threads(l->mlp_tc != 0);
+  const long long tiles = (l->nf + threads - 1) / threads;
   const int max_grid = l->adv_grid[l->mlp_tc];
   long long grid = max_grid < tiles ? max_grid : tiles;
   if (grid > kAdvanceMaxGrid) grid = kAdvanceMaxGrid;

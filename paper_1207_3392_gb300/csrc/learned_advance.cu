@@ -12,11 +12,12 @@
 //   maximum does not depend on the order) and takes the same dt; CTA 0
 //   stores dt and t
 //   per stage:
-//     plain flux and features of a tile of 256 faces, and the network on
-//     them (BF16 weights in shared memory, loaded once per launch): each warp
-//     on its own 32 faces with mma.sync, or, with the tcgen05 engine, each
-//     half of the CTA on its 128 faces (accumulators in TMEM, mlp_tc.cuh)
-//                                                                barrier
+//     plain flux and features of a tile of one face per thread, and the
+//     network on them (BF16 weights in shared memory, loaded once per
+//     launch): each warp on its own 32 faces with mma.sync (CTAs of 256
+//     threads, 2 per SM), or, with the tcgen05 engine, each group of four
+//     warps on its 128 faces (accumulators in TMEM, mlp_tc.cuh; CTAs of 512
+//     threads, 1 per SM)                                        barrier
 //     FCT ratios of every cell (when limiting)                   barrier
 //     corrected update of every cell                             barrier
 //     only if a cell failed: the three widening passes and, if failures
@@ -41,35 +42,44 @@ namespace gh {
 
 namespace {
 
-constexpr int LFA_WARPS = LF_ADVANCE_THREADS / 32;
 constexpr int LFA_PASSES = 3;  // widening passes, as in the per-phase path
 
-// tcgen05 engine: one group of four warps per 128 faces of a tile (the
-// network's MMA tile).
-constexpr int LFA_GROUPS = LF_ADVANCE_THREADS / mlptc::M;
-static_assert(LFA_GROUPS == 2, "a 256-face tile is two network tiles");
-// Dynamic shared memory, per engine: mma.sync: the BF16 weight image and one
-// feature row per thread; tcgen05: the weights as B operands and each
-// group's operand tile.  Sized so that at most 2 CTAs fit on an SM (with
-// tcgen05 their 2 x 256 TMEM columns fill the SM's 512: a third CTA could not
-// allocate while the others wait for it at a grid barrier).
-struct SmemSync {
-  mlp::InferWeights W;
-  __align__(16) __nv_bfloat16 xs[LF_ADVANCE_THREADS][mlp::KIN];
+// The CTA shape and shared memory per network engine.  tcgen05: one group of
+// four warps per 128 faces of a tile (the network's MMA tile).  Dynamic
+// shared memory: mma.sync: the BF16 weight image and one feature row per
+// thread; tcgen05: the weights as B operands and each group's operand tile.
+// It is sized so that at most CTAS CTAs fit on an SM (with tcgen05 their TMEM
+// columns then fill at most the SM's 512: another CTA could not allocate
+// while the others wait for it at a grid barrier).
+template <bool TC>
+struct Lfa {
+  static constexpr int CTAS = lf_advance_ctas_per_sm(TC);
+  static constexpr int THREADS = lf_advance_threads(TC);
+  static constexpr int WARPS = THREADS / 32;
+  static constexpr int GROUPS = THREADS / mlptc::M;
+  static_assert(GROUPS * mlptc::M == THREADS, "a tile is whole network tiles");
+  struct SmemSync {
+    mlp::InferWeights W;
+    __align__(16) __nv_bfloat16 xs[THREADS][mlp::KIN];
+  };
+  static constexpr size_t SMEM_MIN = 228 * 1024 / (CTAS + 1) + 1024;
+  static constexpr size_t NEED = TC ? sizeof(mlptc::Weights) + GROUPS * sizeof(mlptc::Tile) : sizeof(SmemSync);
+  static constexpr size_t SMEM = ((NEED > SMEM_MIN ? NEED : SMEM_MIN) + 1023) / 1024 * 1024;
+  static_assert((CTAS + 1) * SMEM > 228 * 1024, "at most CTAS CTAs per SM");
+  static_assert(SMEM <= 227 * 1024, "fits one CTA's shared memory");
+  static constexpr uint32_t TMEM_COLS = GROUPS * mlptc::TMEM_COLS;
+  static_assert(!TC || TMEM_COLS * CTAS <= 512, "the resident CTAs' TMEM fits the SM");
 };
-constexpr size_t LFA_SMEM = 80 * 1024;
-static_assert(sizeof(mlptc::Weights) + LFA_GROUPS * sizeof(mlptc::Tile) <= LFA_SMEM, "operand images fit");
-static_assert(sizeof(SmemSync) <= LFA_SMEM, "weight image and feature rows fit");
-static_assert(3 * LFA_SMEM > 228 * 1024, "at most two CTAs per SM");
-constexpr uint32_t LFA_TMEM_COLS = LFA_GROUPS * mlptc::TMEM_COLS;
 
 // Every step of the launch; returns early (on every thread of the CTA
 // together) when a grid barrier gives up.  TC: the network on tcgen05 (W,
 // tiles, mbar, tmem), else on mma.sync (S).
 template <int SOLVER, bool TC>
-__device__ __forceinline__ void lf_advance_body(const LfAdvanceArgs& P, SmemSync& S, const mlptc::Weights& W,
-                                                mlptc::Tile* tiles, unsigned long long* mbar, uint32_t tmem,
-                                                double* red) {
+__device__ __forceinline__ void lf_advance_body(const LfAdvanceArgs& P, typename Lfa<TC>::SmemSync& S,
+                                                const mlptc::Weights& W, mlptc::Tile* tiles,
+                                                unsigned long long* mbar, uint32_t tmem, double* red) {
+  constexpr int LF_ADVANCE_THREADS = Lfa<TC>::THREADS;
+  constexpr int LFA_WARPS = Lfa<TC>::WARPS;
   const Mesh2& M = P.M;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, bx = blockIdx.x;
   const int grp = tid / mlptc::M, row = tid % mlptc::M;  // network group and sample row
@@ -240,20 +250,21 @@ __device__ __forceinline__ void lf_advance_body(const LfAdvanceArgs& P, SmemSync
 }
 
 template <int SOLVER, bool TC>
-__global__ void __launch_bounds__(LF_ADVANCE_THREADS, 2) lf_advance_kernel(LfAdvanceArgs P) {
+__global__ void __launch_bounds__(Lfa<TC>::THREADS, Lfa<TC>::CTAS) lf_advance_kernel(LfAdvanceArgs P) {
+  using L = Lfa<TC>;
   extern __shared__ __align__(128) unsigned char lfa_smem[];
-  auto& S = *reinterpret_cast<SmemSync*>(lfa_smem);
+  auto& S = *reinterpret_cast<typename L::SmemSync*>(lfa_smem);
   auto& W = *reinterpret_cast<mlptc::Weights*>(lfa_smem);
   auto* tiles = reinterpret_cast<mlptc::Tile*>(lfa_smem + sizeof(mlptc::Weights));
-  __shared__ unsigned long long mbar[LFA_GROUPS];
+  __shared__ unsigned long long mbar[L::GROUPS];
   __shared__ uint32_t tmem_slot;
-  __shared__ double red[LFA_WARPS];
+  __shared__ double red[L::WARPS];
   const bool corr = P.W != nullptr;
   if (corr && TC) {
     mlptc::load_weights(W, P.W);
-    if (threadIdx.x < LFA_GROUPS) tma::mbar_init(mbar + threadIdx.x, 1);
+    if (threadIdx.x < L::GROUPS) tma::mbar_init(mbar + threadIdx.x, 1);
     tma::fence_mbar_init();
-    if (threadIdx.x < 32) mlptc::tmem_alloc(&tmem_slot, LFA_TMEM_COLS);
+    if (threadIdx.x < 32) mlptc::tmem_alloc(&tmem_slot, L::TMEM_COLS);
     mlptc::fence_before();
   } else if (corr) {
     mlp::copy_weights(S.W, P.W);
@@ -265,7 +276,7 @@ __global__ void __launch_bounds__(LF_ADVANCE_THREADS, 2) lf_advance_kernel(LfAdv
     mlptc::fence_before();
     __syncthreads();
     mlptc::fence_after();
-    if (threadIdx.x < 32) mlptc::tmem_dealloc(tmem_slot, LFA_TMEM_COLS);
+    if (threadIdx.x < 32) mlptc::tmem_dealloc(tmem_slot, L::TMEM_COLS);
   }
 }
 
@@ -284,10 +295,11 @@ int learned_advance_max_grid(int solver, bool mlp_tc) {
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return 0;
   const void* fn = advance_fn(solver, mlp_tc);
-  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LFA_SMEM) != cudaSuccess) return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, LF_ADVANCE_THREADS, LFA_SMEM) != cudaSuccess)
-    return 0;
-  if (mlp_tc && per_sm > 2) per_sm = 2;  // the TMEM budget (the shared-memory size already ensures it)
+  const size_t smem = mlp_tc ? Lfa<true>::SMEM : Lfa<false>::SMEM;
+  const int threads = lf_advance_threads(mlp_tc), cap = lf_advance_ctas_per_sm(mlp_tc);
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem) != cudaSuccess) return 0;
+  if (per_sm > cap) per_sm = cap;  // the shared-memory size already ensures it
   return per_sm * sms;
 }
 
@@ -295,8 +307,9 @@ cudaError_t launch_learned_advance(const LfAdvanceArgs& P, int solver, int grid,
   LfAdvanceArgs a = P;
   void* args[] = {&a};
   // cooperative: the CTAs wait on one another, so all must be resident
-  return cudaLaunchCooperativeKernel(advance_fn(solver, P.mlp_tc != 0), dim3(grid), dim3(LF_ADVANCE_THREADS), args,
-                                     LFA_SMEM, st);
+  const bool tc = P.mlp_tc != 0;
+  return cudaLaunchCooperativeKernel(advance_fn(solver, tc), dim3(grid), dim3(lf_advance_threads(tc)), args,
+                                     tc ? Lfa<true>::SMEM : Lfa<false>::SMEM, st);
 }
 
 }  // namespace gh

@@ -35,9 +35,13 @@ struct LfAdvanceArgs {
   int mlp_tc;                  // network on tcgen05 (1) or mma.sync (0)
 };
 
-// Largest cooperative grid of the one-launch advance (CTAs of
-// LF_ADVANCE_THREADS threads that fit on the device at once), 0 if none.
-constexpr int LF_ADVANCE_THREADS = 256;
+// CTA shape of the one-launch advance per network engine (measured: the
+// mma.sync network runs best as 2 CTAs of 256 threads per SM, the tcgen05
+// one as 1 CTA of 512 threads, four MMA groups sharing the SM's TMEM).
+constexpr int lf_advance_ctas_per_sm(bool mlp_tc) { return mlp_tc ? 1 : 2; }
+constexpr int lf_advance_threads(bool mlp_tc) { return 512 / lf_advance_ctas_per_sm(mlp_tc); }
+// Largest cooperative grid of the one-launch advance (CTAs that fit on the
+// device at once), 0 if none.
 int learned_advance_max_grid(int solver, bool mlp_tc);
 // Launch it with grid CTAs (1 <= grid <= learned_advance_max_grid for P.mlp_tc).
 cudaError_t launch_learned_advance(const LfAdvanceArgs& P, int solver, int grid, cudaStream_t st);

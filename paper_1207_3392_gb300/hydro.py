@@ -93,6 +93,7 @@ SIGNATURES = {
     "genasis_learned_get_conserved": [_P, _P],
     "genasis_learned_advance": [_P, _I, _D, _D, _P],
     "genasis_learned_fallbacks": [_P, _P],
+    "genasis_check_bounded_waits": [_P, _P],
     "genasis_learned_set_option": [_P, ctypes.c_int, ctypes.c_int],
     "genasis_learned_launches_per_step": [_P],
     "genasis_learned_features": [_P, _P, _P],
@@ -640,6 +641,16 @@ class HydroBatch:
             self.close()
         except Exception:
             pass
+
+
+def check_bounded_waits():
+    """Run the two waits that cannot complete (grid barrier, mbarrier) and
+    return ([status word per wait], [seconds per wait]); a status of 2 means
+    the wait gave up within its bound (about a second)."""
+    st = (ctypes.c_uint * 2)()
+    sec = (ctypes.c_double * 2)()
+    check(load().genasis_check_bounded_waits(st, sec))
+    return [int(st[0]), int(st[1])], [float(sec[0]), float(sec[1])]
 
 
 def measure_fma_rate(kind):
