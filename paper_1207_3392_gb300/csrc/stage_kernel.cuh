@@ -105,13 +105,16 @@ struct StageKernel {
   // one float4 (variables 0..3) and one float (variable 4), so a slot is read
   // or written with two accesses instead of five.  Otherwise each variable
   // has its own plane.  The values are the same either way.
-  // Stage 2 only: stage 1 also carries the column totals through the march,
-  // and holding whole slots there spilled (measured: stage 1 slower, stage 2
-  // 4% faster).
-  static constexpr bool VEC = NDIM == 3 && PRE && STAGE == 2 && std::is_same<T, float>::value;
+  // In 3D, stage 2 only: stage 1 also carries the column totals through the
+  // march, and holding whole slots there spilled (measured: stage 1 slower,
+  // stage 2 4% faster).  2D FP32 (4 values per slot): one float4 per slot.
+  static constexpr bool VEC5 = NDIM == 3 && PRE && STAGE == 2 && std::is_same<T, float>::value;
+  static constexpr bool VEC4 = NDIM == 2 && std::is_same<T, float>::value;
+  static constexpr bool VEC = VEC5 || VEC4;
   static constexpr bool VECF = VEC;
   static constexpr int P = VEC ? 1 : 0;  // plane arrays collapse to one element under VEC
-  static constexpr int Q = VEC ? 0 : 1;  // and the float4 / float arrays otherwise
+  static constexpr int Q = VEC ? 0 : 1;  // and the float4 arrays otherwise
+  static constexpr int Q5 = VEC5 ? 0 : 1;  // the float arrays of the fifth value
   static constexpr int PF = VECF ? 1 : 0;
   static constexpr int QF = VECF ? 0 : 1;
 
@@ -129,17 +132,17 @@ struct StageKernel {
     T xs[PRE && !P ? 2 : 1][PRE && !P ? NV : 1][PRE && !P ? TY : 1][PRE && !P ? TX + 2 : 1];
     T ys[PRE && HAS_Y && !P ? 2 : 1][PRE && HAS_Y && !P ? NV : 1][PRE && HAS_Y && !P ? TY + 2 : 1]
         [PRE && HAS_Y && !P ? TX : 1];
-    // VEC: the same arrays as float4 + float slots
+    // VEC: the same arrays as float4 (+ float in 3D) slots
     float4 w4[Q ? 1 : NB][Q ? 1 : SY][Q ? 1 : SX];
-    float w1[Q ? 1 : NB][Q ? 1 : SY][Q ? 1 : SX];
+    float w1[Q5 ? 1 : NB][Q5 ? 1 : SY][Q5 ? 1 : SX];
     float4 fx4[QF ? 1 : TY][QF ? 1 : TX + 1];
-    float fx1[QF ? 1 : TY][QF ? 1 : TX + 1];
-    float4 fy4[QF ? 1 : TY + 1][QF ? 1 : TX];
-    float fy1[QF ? 1 : TY + 1][QF ? 1 : TX];
-    float4 xs4[Q ? 1 : 2][Q ? 1 : TY][Q ? 1 : TX + 2];
-    float xs1[Q ? 1 : 2][Q ? 1 : TY][Q ? 1 : TX + 2];
-    float4 ys4[Q ? 1 : 2][Q ? 1 : TY + 2][Q ? 1 : TX];
-    float ys1[Q ? 1 : 2][Q ? 1 : TY + 2][Q ? 1 : TX];
+    float fx1[Q5 ? 1 : TY][Q5 ? 1 : TX + 1];
+    float4 fy4[Q5 ? 1 : TY + 1][Q5 ? 1 : TX];
+    float fy1[Q5 ? 1 : TY + 1][Q5 ? 1 : TX];
+    float4 xs4[Q5 ? 1 : 2][Q5 ? 1 : TY][Q5 ? 1 : TX + 2];
+    float xs1[Q5 ? 1 : 2][Q5 ? 1 : TY][Q5 ? 1 : TX + 2];
+    float4 ys4[Q5 ? 1 : 2][Q5 ? 1 : TY + 2][Q5 ? 1 : TX];
+    float ys1[Q5 ? 1 : 2][Q5 ? 1 : TY + 2][Q5 ? 1 : TX];
   };
 
   // Slot accessors of the shared arrays (all NV values of one slot).
@@ -148,15 +151,15 @@ struct StageKernel {
     o[1] = q.y;
     o[2] = q.z;
     o[3] = q.w;
-    o[4] = s;
+    if constexpr (NV == 5) o[4] = s;
   }
   static __device__ __forceinline__ void pack(const T (&i)[NV], float4& q, float& s) {
     q = make_float4(i[0], i[1], i[2], i[3]);
-    s = i[4];
+    if constexpr (NV == 5) s = i[4];
   }
   static __device__ __forceinline__ void get_w(const Smem& S, int b, int r, int c, T (&o)[NV]) {
     if constexpr (VEC) {
-      unpack(S.w4[b][r][c], S.w1[b][r][c], o);
+      unpack(S.w4[b][r][c], S.w1[VEC5 ? b : 0][VEC5 ? r : 0][VEC5 ? c : 0], o);
     } else {
 #pragma unroll
       for (int v = 0; v < NV; ++v) o[v] = S.w[b][v][r][c];
@@ -164,7 +167,7 @@ struct StageKernel {
   }
   static __device__ __forceinline__ void put_w(Smem& S, int b, int r, int c, const T (&i)[NV]) {
     if constexpr (VEC) {
-      pack(i, S.w4[b][r][c], S.w1[b][r][c]);
+      pack(i, S.w4[b][r][c], S.w1[VEC5 ? b : 0][VEC5 ? r : 0][VEC5 ? c : 0]);
     } else {
 #pragma unroll
       for (int v = 0; v < NV; ++v) S.w[b][v][r][c] = i[v];
@@ -204,7 +207,7 @@ struct StageKernel {
   }
   static __device__ __forceinline__ void get_fx(const Smem& S, int r, int c, T (&o)[NV]) {
     if constexpr (VECF) {
-      unpack(S.fx4[r][c], S.fx1[r][c], o);
+      unpack(S.fx4[r][c], S.fx1[VEC5 ? r : 0][VEC5 ? c : 0], o);
     } else {
 #pragma unroll
       for (int v = 0; v < NV; ++v) o[v] = S.fx[v][r][c];
@@ -212,7 +215,7 @@ struct StageKernel {
   }
   static __device__ __forceinline__ void put_fx(Smem& S, int r, int c, const T (&i)[NV]) {
     if constexpr (VECF) {
-      pack(i, S.fx4[r][c], S.fx1[r][c]);
+      pack(i, S.fx4[r][c], S.fx1[VEC5 ? r : 0][VEC5 ? c : 0]);
     } else {
 #pragma unroll
       for (int v = 0; v < NV; ++v) S.fx[v][r][c] = i[v];
@@ -314,12 +317,15 @@ struct StageKernel {
       get_xs(S, 0, frow, face + 1, wr);
     } else {
       const Geo<T> gl = S.gx[face + 1], gr = S.gx[face + 2];
+      T w0[NV], w1[NV], w2[NV], w3[NV];
+      get_w(S, b, srow, sl - 1, w0);
+      get_w(S, b, srow, sl, w1);
+      get_w(S, b, srow, sl + 1, w2);
+      get_w(S, b, srow, sl + 2, w3);
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        const T w0 = S.w[b][v][srow][sl - 1], w1 = S.w[b][v][srow][sl], w2 = S.w[b][v][srow][sl + 1],
-                w3 = S.w[b][v][srow][sl + 2];
-        wl[v] = fma(limited_slope(w0, w1, w2, gl), gl.h, w1);
-        wr[v] = fma(-limited_slope(w1, w2, w3, gr), gr.h, w2);
+        wl[v] = fma(limited_slope(w0[v], w1[v], w2[v], gl), gl.h, w1[v]);
+        wr[v] = fma(-limited_slope(w1[v], w2[v], w3[v], gr), gr.h, w2[v]);
       }
     }
     flux<0>(A, wl, wr, SW ? (unsigned)(S.fl[b][SW ? srow : 0][SW ? sl : 0] | S.fl[b][SW ? srow : 0][SW ? sl + 1 : 0]) : 0u,
@@ -335,12 +341,15 @@ struct StageKernel {
       get_ys(S, 0, face + 1, scol - 2, wr);
     } else {
       const Geo<T> gl = S.gy[face + 1], gr = S.gy[face + 2];
+      T w0[NV], w1[NV], w2[NV], w3[NV];
+      get_w(S, b, sl - 1, scol, w0);
+      get_w(S, b, sl, scol, w1);
+      get_w(S, b, sl + 1, scol, w2);
+      get_w(S, b, sl + 2, scol, w3);
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        const T w0 = S.w[b][v][sl - 1][scol], w1 = S.w[b][v][sl][scol], w2 = S.w[b][v][sl + 1][scol],
-                w3 = S.w[b][v][sl + 2][scol];
-        wl[v] = fma(limited_slope(w0, w1, w2, gl), gl.h, w1);
-        wr[v] = fma(-limited_slope(w1, w2, w3, gr), gr.h, w2);
+        wl[v] = fma(limited_slope(w0[v], w1[v], w2[v], gl), gl.h, w1[v]);
+        wr[v] = fma(-limited_slope(w1[v], w2[v], w3[v], gr), gr.h, w2[v]);
       }
     }
     flux<1>(A, wl, wr, SW ? (unsigned)(S.fl[b][SW ? sl : 0][SW ? scol : 0] | S.fl[b][SW ? sl + 1 : 0][SW ? scol : 0]) : 0u,
