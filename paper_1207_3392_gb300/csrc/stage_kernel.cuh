@@ -107,9 +107,10 @@ struct StageKernel {
   // has its own plane.  The values are the same either way.
   // In 3D, stage 2 only: stage 1 also carries the column totals through the
   // march, and holding whole slots there spilled (measured: stage 1 slower,
-  // stage 2 4% faster).  2D FP32 (4 values per slot): one float4 per slot.
+  // stage 2 4% faster).  1D and 2D FP32 (3 or 4 values per slot): one float4
+  // per slot (in 1D its last lane is unused).
   static constexpr bool VEC5 = NDIM == 3 && PRE && STAGE == 2 && std::is_same<T, float>::value;
-  static constexpr bool VEC4 = NDIM == 2 && std::is_same<T, float>::value;
+  static constexpr bool VEC4 = NDIM <= 2 && std::is_same<T, float>::value;
   static constexpr bool VEC = VEC5 || VEC4;
   static constexpr bool VECF = VEC;
   static constexpr int P = VEC ? 1 : 0;  // plane arrays collapse to one element under VEC
@@ -150,11 +151,12 @@ struct StageKernel {
     o[0] = q.x;
     o[1] = q.y;
     o[2] = q.z;
-    o[3] = q.w;
+    if constexpr (NV >= 4) o[3] = q.w;
     if constexpr (NV == 5) o[4] = s;
   }
   static __device__ __forceinline__ void pack(const T (&i)[NV], float4& q, float& s) {
-    q = make_float4(i[0], i[1], i[2], i[3]);
+    if constexpr (NV >= 4) q = make_float4(i[0], i[1], i[2], i[3]);
+    else q = make_float4(i[0], i[1], i[2], 0.0f);
     if constexpr (NV == 5) s = i[4];
   }
   static __device__ __forceinline__ void get_w(const Smem& S, int b, int r, int c, T (&o)[NV]) {
