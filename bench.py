@@ -155,7 +155,7 @@ FLOPS_STEP_3D["hllc_switch"] = FLOPS_STEP_3D["hllc"]
 # 8, 40 planes per CTA; profiles/stage_fp32_hllc_sedov256_ncu.md).  Other
 # configurations, precisions and sizes report no traffic.
 TRAFFIC_FP32_HLLC_256 = {
-    (8, 40): {"stage1": 356.879360e6 + 299.414272e6, "stage2": 731.254016e6 + 311.632896e6},
+    (8, 40): {"stage1": 357.344768e6 + 300.076544e6, "stage2": 731.768832e6 + 312.215040e6},
 }
 PRECISION_LABEL = {
     "fp32": ("FP32 storage, FP32 fluxes and FP32 per-cell CFL speeds; the internal-energy recovery "
