@@ -452,6 +452,16 @@ def run_ours(args):
                        "pipeline": f"{nh} handles on {nh} streams, page-locked host buffers"}
         for hh in hs:
             hh.close()
+        # the end-to-end roofline: each step copies its state in and out over
+        # the host link, whose copy rates are measured here (both directions
+        # at once is the pipeline's case)
+        link = {"h2d": H.measure_link_rate(0), "d2h": H.measure_link_rate(1), "both": H.measure_link_rate(2)}
+        achieved = 2 * nbytes / (el / k) / 1e9
+        line["e2e"]["roofline"] = {"bound": "host link", "achieved": achieved, "peak": link["both"], "unit": "GB/s",
+                                   "frac": achieved / link["both"],
+                                   "peak_source": "measured cudaMemcpyAsync, host to device and device to host "
+                                                  "at once (genasis_measure_link_rate)",
+                                   "link_gbs": link}
     h.close()
 
     # other precision / solver combinations of the same workload (context)

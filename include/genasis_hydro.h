@@ -244,6 +244,13 @@ int genasis_hydro_get_centers(genasis_hydro_t h, int axis, double *x);
  * roofline that the update's kernels are reported against.  Allocates and
  * frees a small buffer, uses a private stream, takes ~0.5 s; synchronises. */
 int genasis_measure_fma_rate(int kind, double *tflops);
+/* Host-link copy rate in GB/s (the paper has no counterpart: the measured
+ * denominator of the end-to-end roofline, whose steps copy the state in and
+ * out): 256 MiB page-locked host buffers copied with cudaMemcpyAsync, kind 0
+ * host to device, 1 device to host, 2 both directions at once on two
+ * streams (the rate of the two together).  Allocates and frees ~1 GB (half
+ * page-locked host memory), uses private streams, takes ~0.1 s; synchronises. */
+int genasis_measure_link_rate(int kind, double *gbs);
 
 /* Check that the kernels' bounded waits give up instead of hanging (the paper
  * has no counterpart: a diagnostic of this library).  Runs two waits that

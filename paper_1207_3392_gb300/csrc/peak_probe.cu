@@ -1,7 +1,11 @@
 // peak_probe.cu -- genasis_measure_fma_rate: the vector FMA throughput of the
 // current GPU, measured with independent FMA chains (the denominator of the
-// arithmetic roofline of the stage kernels).  Not part of the update.
+// arithmetic roofline of the stage kernels); genasis_measure_link_rate: the
+// host-link copy rate (the denominator of the end-to-end roofline).  Not
+// part of the update.
 #include <cuda_runtime.h>
+
+#include <string.h>
 
 #include "common.h"
 #include "genasis_hydro.h"
@@ -92,5 +96,60 @@ extern "C" int genasis_measure_fma_rate(int kind, double* tflops) {
   if (rc) return rc;
   const double fmas = (double)blocks * THREADS * CHAINS * iters * (kind == 2 ? 2.0 : 1.0);
   *tflops = 2.0 * fmas / (ms * 1e-3) / 1e12;
+  return GENASIS_OK;
+}
+
+// Host-link copy rate (the denominator of the end-to-end roofline): 256 MiB
+// page-locked host buffers and device buffers, copied with cudaMemcpyAsync on
+// private streams, kind 0 host to device, 1 device to host, 2 both directions
+// at once on two streams (GB/s of the two together).  One warm-up, then the
+// mean of four timed copies.
+extern "C" int genasis_measure_link_rate(int kind, double* gbs) {
+  if (!gbs || kind < 0 || kind > 2) return gh::fail(GENASIS_EINVAL, "measure_link_rate: bad argument");
+  const size_t bytes = (size_t)256 << 20;
+  void *h_in = nullptr, *h_out = nullptr, *d_a = nullptr, *d_b = nullptr;
+  cudaStream_t s[2] = {nullptr, nullptr};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  float ms = 0.0f;
+  cudaError_t e = cudaHostAlloc(&h_in, bytes, cudaHostAllocDefault);
+  if (e == cudaSuccess) e = cudaHostAlloc(&h_out, bytes, cudaHostAllocDefault);
+  if (e == cudaSuccess) e = cudaMalloc(&d_a, bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&d_b, bytes);
+  if (e == cudaSuccess) memset(h_in, 0, bytes);
+  if (e == cudaSuccess) e = cudaMemset(d_b, 0, bytes);
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaStreamCreateWithFlags(&s[i], cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  const int reps = 4;
+  for (int round = 0; round < 2 && e == cudaSuccess; ++round) {  // the first round warms up
+    const int n = round == 0 ? 1 : reps;
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaEventRecord(e0, s[0]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s[1], e0, 0);
+    for (int r = 0; r < n && e == cudaSuccess; ++r) {
+      if (kind != 1) e = cudaMemcpyAsync(d_a, h_in, bytes, cudaMemcpyHostToDevice, s[0]);
+      if (kind != 0 && e == cudaSuccess) e = cudaMemcpyAsync(h_out, d_b, bytes, cudaMemcpyDeviceToHost, s[1]);
+    }
+    // the end event on s[0] after s[1]'s copies too
+    cudaEvent_t join = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(join, s[1]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s[0], join, 0);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s[0]);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (join) cudaEventDestroy(join);
+  }
+  const int rc = e == cudaSuccess ? GENASIS_OK : gh::fail(GENASIS_ECUDA, "measure_link_rate: %s", cudaGetErrorString(e));
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  for (int i = 0; i < 2; ++i)
+    if (s[i]) cudaStreamDestroy(s[i]);
+  cudaFreeHost(h_in);
+  cudaFreeHost(h_out);
+  cudaFree(d_a);
+  cudaFree(d_b);
+  if (rc) return rc;
+  *gbs = (kind == 2 ? 2.0 : 1.0) * (double)bytes * reps / (ms * 1e-3) / 1e9;
   return GENASIS_OK;
 }

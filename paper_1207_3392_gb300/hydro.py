@@ -93,6 +93,7 @@ SIGNATURES = {
     "genasis_learned_get_conserved": [_P, _P],
     "genasis_learned_advance": [_P, _I, _D, _D, _P],
     "genasis_learned_fallbacks": [_P, _P],
+    "genasis_measure_link_rate": [ctypes.c_int, _P],
     "genasis_check_bounded_waits": [_P, _P],
     "genasis_learned_set_option": [_P, ctypes.c_int, ctypes.c_int],
     "genasis_learned_launches_per_step": [_P],
@@ -658,6 +659,14 @@ def measure_fma_rate(kind):
     2 FP32 with the packed two-lane FMA."""
     out = ctypes.c_double()
     check(load().genasis_measure_fma_rate(int(kind), ctypes.byref(out)))
+    return out.value
+
+
+def measure_link_rate(kind):
+    """Measured host-link copy rate in GB/s: kind 0 host to device, 1 device
+    to host, 2 both directions at once (their sum)."""
+    out = ctypes.c_double()
+    check(load().genasis_measure_link_rate(int(kind), ctypes.byref(out)))
     return out.value
 
 

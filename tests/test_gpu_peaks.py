@@ -1,6 +1,7 @@
-"""The measured vector FMA rates that the arithmetic roofline divides by:
-each within a factor of two of the GPU's nominal rate (GB300: 152 SMs x 128
-FP32 lanes x 2 x ~2 GHz ~ 80 TFLOP/s; FP64 1.25 TFLOP/s nominal)."""
+"""The measured rates that the rooflines divide by: the vector FMA rates of
+the arithmetic roofline, each within a factor of two of the GPU's nominal
+rate (GB300: 152 SMs x 128 FP32 lanes x 2 x ~2 GHz ~ 80 TFLOP/s; FP64
+1.25 TFLOP/s nominal), and the host-link copy rates of the end-to-end one."""
 import pytest
 
 from paper_1207_3392_gb300 import hydro as H
@@ -26,3 +27,16 @@ def test_fma_rates_are_plausible():
     assert 40.0 < fp32x2 < 320.0, fp32x2
     with pytest.raises(H.HydroError):
         H.measure_fma_rate(3)
+
+
+def test_link_rates_are_plausible():
+    """The host-link copy rates that the end-to-end roofline divides by: each
+    direction between 20 GB/s (slower than any PCIe or NVLink-C2C host link of
+    this class) and 1 TB/s, and both directions at once no slower than one."""
+    h2d, d2h, both = (H.measure_link_rate(k) for k in range(3))
+    print(f"link rates: H2D {h2d:.0f}, D2H {d2h:.0f}, both {both:.0f} GB/s")
+    for r in (h2d, d2h):
+        assert 20.0 < r < 1000.0, r
+    assert 0.9 * max(h2d, d2h) < both < 2000.0, (h2d, d2h, both)
+    with pytest.raises(H.HydroError):
+        H.measure_link_rate(3)
