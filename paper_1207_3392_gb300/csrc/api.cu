@@ -217,11 +217,18 @@ int configure(genasis_hydro* h, int tile, int kchunk_req) {
   h->kchunk = kchunk;
   h->grid = dim3(gx, gy, gz);
   h->grid2 = dim3(gx2, gy2, gz);
+  void* bufs[3] = {h->U[0], h->U[1], h->K};
   const StageVariant* vt = v1.tma ? &v1 : (v2.tma ? &v2 : nullptr);
   if (vt) {
-    void* bufs[3] = {h->U[0], h->U[1], h->K};
     for (int i = 0; i < 3; ++i) {
       const int rc = encode_state_map(&h->tmap[i], bufs[i], h->n, vt->box_x, vt->box_y);
+      if (rc) return rc;
+    }
+  }
+  h->flags_tma = h->solver == GENASIS_HLLC_SWITCH && flags_tma_usable(h->ndim, h->prec == GENASIS_FP32_MIXED, h->n);
+  if (h->flags_tma) {  // stage 1 reads U^n: maps of the two state buffers
+    for (int i = 0; i < 2; ++i) {
+      const int rc = encode_state_map(&h->fmap[i], bufs[i], h->n, FLAGS_TMA_BOX_X, FLAGS_TMA_BOX_Y);
       if (rc) return rc;
     }
   }
@@ -252,6 +259,13 @@ int enqueue_flags(genasis_hydro* h, int stage) {
     F.flags = h->flags;
     F.ncell = h->ncell;
     F.stage = stage;
+    F.status = h->status;
+    if constexpr (std::is_same<T, float>::value) {
+      if (h->flags_tma && stage == 1) {
+        GH_CK(launch_shock_flags_tma(F, h->fmap[h->cur], h->stream));
+        return GENASIS_OK;
+      }
+    }
     GH_CK(launch_shock_flags<T>(h->ndim, F, h->stream));
   }
   return GENASIS_OK;

@@ -4,6 +4,7 @@
 #include "aux_kernels.h"
 #include "finalize.cuh"
 #include "hydro_device.cuh"
+#include "shock_flags.cuh"
 
 namespace gh {
 
@@ -131,49 +132,92 @@ __global__ void __launch_bounds__(32) finalize_kernel(FinalizeArgs A) {
   fin::finish(A, s, mb, lane);
 }
 
-// Shock detector of the HLLC -> HLL switch (Sec. 3.2 describes the switch, not
-// the detector): cell c lies on a shock moving along axis r when, across its
-// two neighbours along r (boundary-mapped like the stage kernel's ghosts), the
-// flow is compressive, v_r(+) - v_r(-) < 0, and the pressure jumps by more
-// than half the smaller pressure.  Bit r of flags[c] records it.
-template <class T, int NDIM>
-__global__ void shock_flags_kernel(FlagArgs<T> A) {
-  constexpr int NV = NDIM + 2;
+// Shock detector of the HLLC -> HLL switch (the test: shock_flags.cuh): the
+// pass of Runge-Kutta stage 2 everywhere, and of stage 1 on the meshes the
+// TMA pass of flags_tma.cu does not take (2D, FP64, rows that are not
+// 16-byte multiples, an n below 3).  One CTA covers a TX x TY tile of the (x, y) plane
+// and marches along z over a chunk of planes.  Every cell's pressure and
+// velocity is recovered once per CTA: the tile's cells of the next plane in
+// registers, the current plane with a one-cell ring of x and y neighbours in
+// shared memory, the previous plane's (p, v_z) in registers.  Only the ring
+// and the two planes that bound a chunk are recovered by more than one CTA.
+template <class T, int NDIM, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY) shock_flags_kernel(FlagArgs<T> A, int kz) {
+  static_assert(NDIM == 2 || NDIM == 3, "the switch runs in 2D and 3D");
+  static_assert(2 * (TX + TY) <= TX * TY, "one ring cell per thread at most");
+  __shared__ T sp[TY + 2][TX + 2], svx[TY + 2][TX + 2], svy[TY + 2][TX + 2];
   const T gm1 = (T)(A.gamma - 1.0);
   const T dt = A.stage == 2 ? (T)(*A.dt) : T(0);
-  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < A.ncell; c += (size_t)gridDim.x * blockDim.x) {
-    int idx[3] = {0, 0, 0};
-    size_t r_ = c;
+  const int nx = A.n[0], ny = A.n[1], nz = A.n[2];
+  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const int x = x0 + tx, y = y0 + ty;
+  const int z0 = NDIM > 2 ? blockIdx.z * kz : 0;
+  const int z1 = NDIM > 2 ? min(z0 + kz, nz) : 1;
+  // own column: a mesh cell, or the ghost just past the high x or y edge
+  const bool own = x <= nx && y <= ny;
+  // ring cell of this thread: left/right columns, then bottom/top rows
+  int ri = -2, rj = -2, rs = -1, rx = 0, ry = 0;
+  if (threadIdx.x < 2 * TY) {
+    const int side = threadIdx.x / TY, row = threadIdx.x % TY;
+    ri = side ? x0 + TX : x0 - 1;
+    rj = y0 + row;
+    rs = 0;
+    rx = side ? TX + 1 : 0;
+    ry = row + 1;
+  } else if (threadIdx.x < 2 * (TX + TY)) {
+    const int t = threadIdx.x - 2 * TY, side = t / TX, col = t % TX;
+    ri = x0 + col;
+    rj = side ? y0 + TY : y0 - 1;
+    rs = 1;
+    rx = col + 1;
+    ry = side ? TY + 1 : 0;
+  }
+  const bool ring = rs >= 0 && ri <= nx && rj <= ny;
+  T pm = T(0), vzm = T(0), pc = T(0), vc[NDIM];
 #pragma unroll
-    for (int q = 0; q < NDIM; ++q) {
-      idx[q] = (int)(r_ % A.n[q]);
-      r_ /= A.n[q];
+  for (int q = 0; q < NDIM; ++q) vc[q] = T(0);
+  if (own) {
+    if constexpr (NDIM > 2) {
+      T vv[NDIM];
+      shock::cell_pv<T, NDIM>(A, gm1, dt, x, y, z0 - 1, pm, vv);
+      vzm = vv[2];
     }
-    unsigned bits = 0;
+    shock::cell_pv<T, NDIM>(A, gm1, dt, x, y, z0, pc, vc);
+  }
+  for (int z = z0; z < z1; ++z) {
+    T pn = T(0), vn[NDIM];
 #pragma unroll
-    for (int r = 0; r < NDIM; ++r) {
-      T p[2], v[2];
-#pragma unroll
-      for (int side = 0; side < 2; ++side) {
-        int j[3] = {idx[0], idx[1], idx[2]};
-        bool flip = false;
-        j[r] = bc_map(idx[r] + (side ? 1 : -1), A.n[r], A.bc_lo[r], A.bc_hi[r], flip);
-        const size_t cc = ((size_t)j[2] * A.n[1] + j[1]) * A.n[0] + j[0];
-        T u[NV], w[NV];
-#pragma unroll
-        for (int k = 0; k < NV; ++k) {
-          T x = A.un[k * A.ncell + cc];
-          if (A.stage == 2) x = fma(dt, A.k1[k * A.ncell + cc], x);
-          u[k] = x;
-        }
-        if (flip) u[1 + r] = -u[1 + r];
-        recover<NDIM>(u, w);
-        p[side] = gm1 * w[NV - 1];
-        v[side] = w[1 + r];
-      }
-      if (v[1] - v[0] < T(0) && fabs(p[1] - p[0]) > T(0.5) * fmin(p[0], p[1])) bits |= 1u << r;
+    for (int q = 0; q < NDIM; ++q) vn[q] = T(0);
+    if constexpr (NDIM > 2)
+      if (own) shock::cell_pv<T, NDIM>(A, gm1, dt, x, y, z + 1, pn, vn);
+    if (ring) {
+      T pr, vr[NDIM];
+      shock::cell_pv<T, NDIM>(A, gm1, dt, ri, rj, z, pr, vr);
+      sp[ry][rx] = pr;
+      if (rs == 0) svx[ry][rx] = vr[0];
+      else svy[ry][rx] = vr[1];
     }
-    A.flags[c] = (unsigned char)bits;
+    sp[ty + 1][tx + 1] = pc;
+    svx[ty + 1][tx + 1] = vc[0];
+    svy[ty + 1][tx + 1] = vc[1];
+    __syncthreads();
+    if (x < nx && y < ny) {
+      unsigned bits = 0;
+      if (shock::jump(sp[ty + 1][tx], svx[ty + 1][tx], sp[ty + 1][tx + 2], svx[ty + 1][tx + 2])) bits |= 1u;
+      if (shock::jump(sp[ty][tx + 1], svy[ty][tx + 1], sp[ty + 2][tx + 1], svy[ty + 2][tx + 1])) bits |= 2u;
+      if constexpr (NDIM > 2)
+        if (shock::jump(pm, vzm, pn, vn[2])) bits |= 4u;
+      A.flags[((size_t)z * ny + y) * nx + x] = (unsigned char)bits;
+    }
+    __syncthreads();
+    if constexpr (NDIM > 2) {
+      pm = pc;
+      vzm = vc[2];
+      pc = pn;
+#pragma unroll
+      for (int q = 0; q < NDIM; ++q) vc[q] = vn[q];
+    }
   }
 }
 
@@ -220,12 +264,30 @@ cudaError_t launch_totals(int ndim, const ReduceArgs<T>& A, cudaStream_t s) {
 
 template <class T>
 cudaError_t launch_shock_flags(int ndim, const FlagArgs<T>& A, cudaStream_t s) {
-  const int nb = grid_for(A.ncell, 256, 4096);
-  switch (ndim) {
-    case 1: shock_flags_kernel<T, 1><<<nb, 256, 0, s>>>(A); break;
-    case 2: shock_flags_kernel<T, 2><<<nb, 256, 0, s>>>(A); break;
-    default: shock_flags_kernel<T, 3><<<nb, 256, 0, s>>>(A); break;
+  if (ndim == 2) {
+    constexpr int TX = 32, TY = 8;
+    const long long bx = (A.n[0] + TX - 1) / TX, by = (A.n[1] + TY - 1) / TY;
+    if (by > 65535) return cudaErrorInvalidConfiguration;
+    shock_flags_kernel<T, 2, TX, TY><<<dim3((unsigned)bx, (unsigned)by, 1), TX * TY, 0, s>>>(A, 1);
+    return cudaGetLastError();
   }
+  if (ndim != 3) return cudaErrorInvalidValue;  // 1D runs plain HLLC
+  // 32 x 4 tiles (many small CTAs keep the most loads in flight); z chunks
+  // for about 32 CTAs per SM
+  constexpr int TX = 32, TY = 4;
+  const long long bx = (A.n[0] + TX - 1) / TX, by = (A.n[1] + TY - 1) / TY;
+  if (by > 65535) return cudaErrorInvalidConfiguration;
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const long long target = 32LL * (sms > 0 ? sms : 1);
+  const int nz = A.n[2];
+  long long chunks = (target + bx * by - 1) / (bx * by);
+  chunks = chunks < 1 ? 1 : (chunks > nz ? nz : (chunks > 65535 ? 65535 : chunks));
+  const int kz = (int)((nz + chunks - 1) / chunks);
+  chunks = (nz + kz - 1) / kz;
+  shock_flags_kernel<T, 3, TX, TY><<<dim3((unsigned)bx, (unsigned)by, (unsigned)chunks), TX * TY, 0, s>>>(A, kz);
   return cudaGetLastError();
 }
 

@@ -1,6 +1,7 @@
 // aux_kernels.h -- launchers of the small kernels around the stage kernels.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
 
@@ -54,10 +55,19 @@ struct FlagArgs {
   unsigned char* flags;
   size_t ncell;
   int stage;
+  unsigned* status;   // STATUS_TIMEOUT when a bounded wait of the TMA pass gives up
 };
 
 template <class T>
 cudaError_t launch_shock_flags(int ndim, const FlagArgs<T>& A, cudaStream_t s);
+
+// The detector of Runge-Kutta stage 1 on 3D FP32 meshes with the state
+// planes staged by TMA (flags_tma.cu).  Usable when n[0] is a multiple of 4
+// (16-byte rows) and every n >= 3.  map_u is a 4D map (x, y, z, variable) of
+// U^n with the box FLAGS_TMA_BOX_X x FLAGS_TMA_BOX_Y x 1 x 5.
+constexpr int FLAGS_TMA_BOX_X = 40, FLAGS_TMA_BOX_Y = 10;
+bool flags_tma_usable(int ndim, bool fp32, const int* n);
+cudaError_t launch_shock_flags_tma(const FlagArgs<float>& A, const CUtensorMap& map_u, cudaStream_t s);
 
 template <class T>
 cudaError_t launch_init_from_primitive(int ndim, size_t ncell, double gamma, const double* rho, const double* vel,

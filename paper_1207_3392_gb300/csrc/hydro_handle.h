@@ -42,6 +42,8 @@ struct genasis_hydro {
   dim3 grid, grid2;  // stage 1 / stage 2 (the two may use different tile shapes)
   // tensor maps of U[0], U[1] and K for TMA variants (valid when v1.tma or v2.tma)
   CUtensorMap tmap[3];
+  CUtensorMap fmap[2];     // U[0], U[1] with the box of the TMA shock-flag pass
+  bool flags_tma = false;  // the switch's stage-1 detector runs the TMA pass
   int want_totals = 1;
   int one_launch = 1;  // small 1D meshes: a whole advance in one cooperative launch
   int mlp_tc = 0;      // attached network: on tcgen05 (1) or mma.sync (0)

@@ -57,35 +57,6 @@ struct TmaStageArgs {
   CUtensorMap map_k;
 };
 
-namespace tma {
-
-__device__ __forceinline__ void load_4d(void* dst, const CUtensorMap* map, int x, int y, int z, int v,
-                                        unsigned long long* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
-      "[%6];" ::"r"(smem_u32(dst)),
-      "l"((unsigned long long)map), "r"(x), "r"(y), "r"(z), "r"(v), "r"(smem_u32(bar))
-      : "memory");
-}
-// Barrier of the compute threads only (named barrier 1; the producer warp
-// takes no part) that also ORs a flag over them: every thread leaves with
-// the same answer, so a decision taken on it is uniform.
-template <int N>
-__device__ __forceinline__ bool sync_compute_or(bool flag) {
-  unsigned out;
-  asm volatile(
-      "{\n\t.reg .pred p, q;\n\t"
-      "setp.ne.u32 p, %1, 0;\n\t"
-      "bar.red.or.pred q, 1, %2, p;\n\t"
-      "selp.u32 %0, 1, 0, q;\n\t}"
-      : "=r"(out)
-      : "r"((unsigned)flag), "n"(N)
-      : "memory");
-  return out != 0u;
-}
-
-}  // namespace tma
-
 template <int SOLVER, int STAGE, int TX, int TY, int NS>
 struct StageTma {
   using T = float;

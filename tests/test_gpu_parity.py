@@ -400,6 +400,21 @@ def test_shock_switch_matches_oracle_3d(axis):
         _check(Ug, Uo, 3, tol, f"shock switch 3d axis {axis} prec={precision}")
 
 
+@pytest.mark.parametrize("bc", [P.PERIODIC, P.REFLECT, P.OUTFLOW])
+@pytest.mark.parametrize("shape", [(4, 3, 5), (36, 9, 3), (100, 17, 70)])
+def test_shock_switch_edge_meshes_3d(shape, bc):
+    """The switch on piecewise-constant random blocks at the edges of the
+    detector's passes (in FP32 the stage-1 detector stages planes by TMA):
+    rows of 4 cells, axes of 3 cells (almost every cell in the boundary
+    shell that is flagged cell by cell), tiles ragged in x and y, a z march
+    in chunks; every boundary kind, both precisions."""
+    pr = P.random_blocks(3, shape, seed=sum(shape), bc=bc)
+    Uo, _ = oracle_run(pr, solver=P.HLLC_SWITCH, steps=4)
+    for precision, tol in PRECISIONS:
+        Ug, _ = gpu_run(pr, precision, solver=P.HLLC_SWITCH, steps=4)
+        _check(Ug, Uo, 3, tol, f"switch blocks {shape} bc={bc} prec={precision}")
+
+
 def test_shock_switch_tiles_identical():
     """Every tile compiled with the switch (3D FP32) gives bitwise the same state."""
     pr = P.planar_shock_3d(n_long=64, n_cross=10, axis=0, solver=P.HLLC_SWITCH)
