@@ -47,6 +47,8 @@ def _args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="sedov", choices=["sedov", "batch", "learned", "fmr"])
     ap.add_argument("--levels", type=int, default=4, help="fmr workload: nested levels")
+    ap.add_argument("--problems", type=int, default=4096,
+                    help="batch workload: problems per GPU (each drawn from the same size mix)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default tile instead of autotuning")
     ap.add_argument("--tile", type=int, default=-1, help="use this tile (and --kchunk) instead of autotuning")
     ap.add_argument("--kchunk", type=int, default=0)
@@ -496,6 +498,18 @@ def run_ours(args):
                 peak, _ = _peaks()
                 variants[key] = {"value": cells * 2 / (mv * 1e-3), "ms_per_step": mv,
                                  "hbm_frac_step": 5 * 5 * bv * cells / (mv * 1e-3) / 1e9 / peak}
+                if pname in ("fp32", "fp64"):
+                    # the arithmetic roofline of the step: the oracle-counted
+                    # operations against the measured FMA rate of the pipe that
+                    # runs them (double word runs FP64 operations as FP32 ones,
+                    # so it has no such rate)
+                    if not _PEAKS:
+                        _PEAKS.update(_fma_peaks())
+                    fl = FLOPS_STEP_3D[sname] * cells / (mv * 1e-3) / 1e12
+                    pk = _PEAKS.get(pname)
+                    variants[key]["alu_step"] = {"achieved": fl, "peak": pk, "unit": "TFLOP/s",
+                                                 "frac": fl / pk if pk else None,
+                                                 "flops_per_cell": FLOPS_STEP_3D[sname]}
                 hv.close()
         # the centrally refined 320^3 pulse (stretched widths, gamma = 5/3), FP32 HLLC
         pr = P.stretched_pulse_3d(320)
@@ -549,9 +563,9 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def _batch_specs(world=1, rank=0):
+def _batch_specs(world=1, rank=0, per_rank=4096):
     from paper_1207_3392_gb300 import shard
-    all_specs = shard.weak_scaling_specs(world)
+    all_specs = shard.weak_scaling_specs(world, per_rank=per_rank)
     return all_specs, shard.rank_specs(all_specs, rank, world)
 
 
@@ -651,7 +665,7 @@ def run_batch(args):
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     build.build()
-    all_specs, specs = _batch_specs(world, rank)
+    all_specs, specs = _batch_specs(world, rank, args.problems)
     total_cells = sum(sp.n ** sp.ndim for sp in all_specs)
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
@@ -668,7 +682,7 @@ def run_batch(args):
     line = {"metric": METRIC, "value": total_cells * 2 / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
             "steps": rec["steps"], "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": rec["dtype"], "data": "synthetic",
-            "config": {"workload": f"batched_riemann_4096_{args.precision}", "problems": len(all_specs),
+            "config": {"workload": f"batched_riemann_{args.problems}_{args.precision}", "problems": len(all_specs),
                        "cells": total_cells, "rank0_problems": len(specs), "rank0_cells": rec["cells"],
                        "parallelism": f"{world} GPU(s), problems LPT-sharded by cells x steps, no exchange",
                        "tile": rec["tile"], "cfl": 0.5, "solver": "HLLC", "l2": rec["l2"]},
