@@ -415,6 +415,34 @@ def test_shock_switch_edge_meshes_3d(shape, bc):
         _check(Ug, Uo, 3, tol, f"switch blocks {shape} bc={bc} prec={precision}")
 
 
+def test_shock_switch_full_size_step_from_an_evolved_state():
+    """The switch at the bench's size (256^3 blast) and, in FP32, its launch
+    configuration (tile 8, 40 planes per CTA): 20 GPU steps, so that a moving
+    shock front sets flags in both detector passes, then one GPU step from that
+    state against one oracle step from the same state widened to FP64, with
+    the oracle's dt."""
+    prob = P.sedov_3d(256, solver=P.HLLC_SWITCH)
+    g = O.Grid(prob)
+    for precision, tol in PRECISIONS:
+        h = H.Hydro.from_problem(prob, precision=precision)
+        if precision == H.FP32_MIXED:
+            h.set_tile(8, 40)
+        t0 = h.advance(20, prob.cfl)
+        U0 = h.get_conserved(precision=H.FP64)
+        t1 = h.advance(1, prob.cfl)
+        Ug = h.get_conserved(precision=H.FP64)
+        h.close()
+        dt = prob.cfl * O.cfl_dt(g, U0)
+        assert t1 - t0 == pytest.approx(dt, rel=1e-9 if precision == H.FP64 else 1e-5)
+        Uo = O.step(g, U0, dt)
+        e, _ = check(Ug, Uo, 3, tol, f"switch 256^3 step 21 prec={precision}")
+        # the switch acted in this step: plain HLLC from the same state is
+        # farther from the GPU result than the switched oracle by 10x or more
+        Uh = O.step(O.Grid(prob, solver=P.HLLC), U0, dt)
+        del U0
+        assert rel_l1(Ug, Uh, 3).max() > 10.0 * e.max(), (rel_l1(Ug, Uh, 3), e)
+
+
 def test_shock_switch_tiles_identical():
     """Every tile compiled with the switch (3D FP32) gives bitwise the same state."""
     pr = P.planar_shock_3d(n_long=64, n_cross=10, axis=0, solver=P.HLLC_SWITCH)
