@@ -415,32 +415,50 @@ def test_shock_switch_edge_meshes_3d(shape, bc):
         _check(Ug, Uo, 3, tol, f"switch blocks {shape} bc={bc} prec={precision}")
 
 
-def test_shock_switch_full_size_step_from_an_evolved_state():
-    """The switch at the bench's size (256^3 blast) and, in FP32, its launch
-    configuration (tile 8, 40 planes per CTA): 20 GPU steps, so that a moving
-    shock front sets flags in both detector passes, then one GPU step from that
-    state against one oracle step from the same state widened to FP64, with
-    the oracle's dt."""
-    prob = P.sedov_3d(256, solver=P.HLLC_SWITCH)
+def _step_from_evolved(prob, precisions, what, steps=20, tile=None):
+    """`steps` GPU steps, so that a moving front exists, then one GPU step from
+    that state against one oracle step from the same state widened to FP64,
+    with the oracle's dt.  Returns {precision: (GPU state, start state, dt,
+    rel L1)} for further checks."""
     g = O.Grid(prob)
-    for precision, tol in PRECISIONS:
+    out = {}
+    for precision, tol in precisions:
         h = H.Hydro.from_problem(prob, precision=precision)
-        if precision == H.FP32_MIXED:
-            h.set_tile(8, 40)
-        t0 = h.advance(20, prob.cfl)
+        if tile is not None and precision == H.FP32_MIXED:
+            h.set_tile(*tile)
+        t0 = h.advance(steps, prob.cfl)
         U0 = h.get_conserved(precision=H.FP64)
         t1 = h.advance(1, prob.cfl)
         Ug = h.get_conserved(precision=H.FP64)
         h.close()
         dt = prob.cfl * O.cfl_dt(g, U0)
-        assert t1 - t0 == pytest.approx(dt, rel=1e-9 if precision == H.FP64 else 1e-5)
+        assert t1 - t0 == pytest.approx(dt, rel=1e-5 if precision == H.FP32_MIXED else 1e-9)
         Uo = O.step(g, U0, dt)
-        e, _ = check(Ug, Uo, 3, tol, f"switch 256^3 step 21 prec={precision}")
-        # the switch acted in this step: plain HLLC from the same state is
-        # farther from the GPU result than the switched oracle by 10x or more
-        Uh = O.step(O.Grid(prob, solver=P.HLLC), U0, dt)
-        del U0
-        assert rel_l1(Ug, Uh, 3).max() > 10.0 * e.max(), (rel_l1(Ug, Uh, 3), e)
+        e, _ = check(Ug, Uo, prob.ndim, tol, f"{what} step {steps + 1} prec={precision}")
+        out[precision] = (Ug, U0, dt, e)
+    return out
+
+
+def test_shock_switch_full_size_step_from_an_evolved_state():
+    """The switch at the bench's size (256^3 blast) and, in FP32, its launch
+    configuration (tile 8, 40 planes per CTA): a moving shock front sets flags
+    in both detector passes.  Plain HLLC from the same state is at least 10x
+    farther from the GPU result than the switched oracle step, so the switch
+    acted in that step."""
+    prob = P.sedov_3d(256, solver=P.HLLC_SWITCH)
+    res = _step_from_evolved(prob, PRECISIONS, "switch 256^3", tile=(8, 40))
+    gh = O.Grid(prob, solver=P.HLLC)
+    for precision, (Ug, U0, dt, e) in res.items():
+        Uh = O.step(gh, U0, dt)
+        assert rel_l1(Ug, Uh, 3).max() > 10.0 * e.max(), (precision, rel_l1(Ug, Uh, 3), e)
+
+
+def test_full_size_hll_and_double_word_steps_from_an_evolved_state():
+    """The other blast variants of the bench at 256^3: HLL in FP64 and FP32
+    (tile 8, 40 planes per CTA) and HLLC in double word, one step from a state
+    20 steps in."""
+    _step_from_evolved(P.sedov_3d(256, solver=P.HLL), PRECISIONS, "hll 256^3", tile=(8, 40))
+    _step_from_evolved(P.sedov_3d(256), ((H.FP64_DW, TOL_FP64),), "double word 256^3")
 
 
 def test_shock_switch_tiles_identical():
@@ -606,9 +624,9 @@ def _one_step_full(prob, precisions, pair_tile=None):
 
 
 def test_sedov_full_size_one_step():
-    """256^3 point blast, one step, both precisions; FP32 also on the paired
-    tile that the bench offers, at 40 planes per CTA."""
-    _one_step_full(P.sedov_3d(256), PRECISIONS, pair_tile=PAIR_TILES[2])
+    """256^3 point blast, one step, in FP64, FP32-mixed and double word; FP32
+    also on the paired tile that the bench offers, at 40 planes per CTA."""
+    _one_step_full(P.sedov_3d(256), ALL_PRECISIONS, pair_tile=PAIR_TILES[2])
 
 
 def test_stretched_pulse_full_size_one_step():
