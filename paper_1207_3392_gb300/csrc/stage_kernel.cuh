@@ -290,6 +290,23 @@ struct StageKernel {
     if constexpr (SW) fl = A.flags[c];
   }
 
+  // L2 prefetch of the cell (ref, m) that load_col will read PFD - 2 march
+  // iterations later (the same boundary-mapped address, so always inside the
+  // arrays): the load then meets L2 latency instead of DRAM latency.  Only
+  // the 2D march (rows of one CTA) gains; in 3D the extra instructions cost
+  // more than the latency they hide.
+  static constexpr int PFD = NDIM == 2 ? 3 : 0;
+  static __device__ __forceinline__ void prefetch_col(const StageArgs<T>& A, const ColRef& r, int m, size_t vs) {
+    bool fm = false;
+    const int sm = bc_map(m, A.n[AM], A.bc_lo[AM], A.bc_hi[AM], fm);
+    const size_t c = r.off + (size_t)sm * (HAS_Y ? (size_t)A.n[0] * A.n[1] : (size_t)A.n[0]);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(A.un + v * vs + c));
+      if (STAGE == 2) asm volatile("prefetch.global.L2 [%0];" ::"l"(A.k1 + v * vs + c));
+    }
+  }
+
   // Face flux along axis Q; with the switch, HLL when either cell's shock
   // bits name an axis other than Q (a shock moving transverse to the face).
   template <int Q>
@@ -616,6 +633,7 @@ struct StageKernel {
       unsigned char fk2 = 0, fown = 0;
       if constexpr (MARCH) {
         if (live) {
+          if (PFD > 0 && m + PFD < m1 + 2) prefetch_col(A, own, m + PFD, vs);
           load_col(A, own, m + 2, dt, vs, wk2, fk2);
           const Geo<T> g0 = geo(A, AM, m), g1 = geo(A, AM, m + 1);
           slopes(A, wk, wk1, wk2, g1, sk1);
