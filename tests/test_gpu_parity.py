@@ -401,13 +401,14 @@ def test_shock_switch_matches_oracle_3d(axis):
 
 
 @pytest.mark.parametrize("bc", [P.PERIODIC, P.REFLECT, P.OUTFLOW])
-@pytest.mark.parametrize("shape", [(4, 3, 5), (36, 9, 3), (100, 17, 70)])
+@pytest.mark.parametrize("shape", [(4, 3, 5), (36, 9, 3), (100, 17, 70), (8, 2, 3), (2, 5, 4)])
 def test_shock_switch_edge_meshes_3d(shape, bc):
     """The switch on piecewise-constant random blocks at the edges of the
     detector's passes (in FP32 the stage-1 detector stages planes by TMA):
     rows of 4 cells, axes of 3 cells (almost every cell in the boundary
     shell that is flagged cell by cell), tiles ragged in x and y, a z march
-    in chunks; every boundary kind, both precisions."""
+    in chunks; axes of 2 cells (the register-tile pass in both stages); every
+    boundary kind, both precisions."""
     pr = P.random_blocks(3, shape, seed=sum(shape), bc=bc)
     Uo, _ = oracle_run(pr, solver=P.HLLC_SWITCH, steps=4)
     for precision, tol in PRECISIONS:
