@@ -13,7 +13,8 @@
 //     z.  One producer warp issues, per plane z0 - 1 .. z1 of the chunk, one
 //     4D cp.async.bulk.tensor load of the box x in [a0 - 4, a0 + TX + 4),
 //     y in [b0 - 1, b0 + TY + 1), all five conserved variables, into a ring
-//     of NS slots, completing on the slot's `full` mbarrier.  x starts on a 16-byte boundary (a0 is a multiple of 32).
+//     of NS slots, completing on the slot's `full` mbarrier.  x starts on a
+//     16-byte boundary (a0 is a multiple of 32).
 //     The TX x TY compute threads turn the tile's cells and its one-cell
 //     ring (no corners) into (p, v) once, into a ring of three planes.
 //     After one compute barrier, one thread releases the slot (its `empty`
