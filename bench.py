@@ -157,7 +157,7 @@ FLOPS_STEP_3D["hllc_switch"] = FLOPS_STEP_3D["hllc"]
 # 8, 40 planes per CTA; profiles/stage_fp32_hllc_sedov256_ncu.md).  Other
 # configurations, precisions and sizes report no traffic.
 TRAFFIC_FP32_HLLC_256 = {
-    (8, 40): {"stage1": 357.344768e6 + 300.076544e6, "stage2": 731.768832e6 + 312.215040e6},
+    (8, 40): {"stage1": 356.859136e6 + 300.052480e6, "stage2": 732.600576e6 + 312.649472e6},
 }
 PRECISION_LABEL = {
     "fp32": ("FP32 storage, FP32 fluxes and FP32 per-cell CFL speeds; the internal-energy recovery "

@@ -20,7 +20,11 @@ INCLUDE = os.path.join(ROOT, "include")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libgenasis_hydro.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
+# -ftz=true: FP32 results below 2^-126 (1.2e-38) flush to zero, which no state
+# of these solvers comes near; FP64 arithmetic is unaffected.  It shortens the
+# FP32 division and square-root sequences (the 256^3 FP32 step: 1.223 ->
+# 1.176 ms).  Division and square root stay correctly rounded.
+NVCC_FLAGS = ["-O3", "-ftz=true", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", "-I", CSRC, "-I", INCLUDE]
 
 
