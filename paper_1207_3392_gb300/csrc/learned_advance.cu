@@ -14,8 +14,8 @@
 //   per stage:
 //     plain flux and features of a tile of one face per thread, and the
 //     network on them (BF16 weights in shared memory, loaded once per
-//     launch): each warp on its own 32 faces with mma.sync (CTAs of 256
-//     threads, 2 per SM), or, with the tcgen05 engine, each group of four
+//     launch): each warp on its own 32 faces with mma.sync (CTAs of 128
+//     threads, 4 per SM), or, with the tcgen05 engine, each group of four
 //     warps on its 128 faces (accumulators in TMEM, mlp_tc.cuh; CTAs of 512
 //     threads, 1 per SM)                                        barrier
 //     FCT ratios of every cell (when limiting)                   barrier

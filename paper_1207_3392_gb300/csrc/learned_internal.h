@@ -35,10 +35,11 @@ struct LfAdvanceArgs {
   int mlp_tc;                  // network on tcgen05 (1) or mma.sync (0)
 };
 
-// CTA shape of the one-launch advance per network engine (measured: the
-// mma.sync network runs best as 2 CTAs of 256 threads per SM, the tcgen05
-// one as 1 CTA of 512 threads, four MMA groups sharing the SM's TMEM).
-constexpr int lf_advance_ctas_per_sm(bool mlp_tc) { return mlp_tc ? 1 : 2; }
+// CTA shape of the one-launch advance per network engine (measured at 256^2:
+// the mma.sync network runs best as 4 CTAs of 128 threads per SM, 80 us a
+// step against 82 us for 2 of 256 and 88 us for 1 of 512; the tcgen05 one as
+// 1 CTA of 512 threads, four MMA groups sharing the SM's TMEM).
+constexpr int lf_advance_ctas_per_sm(bool mlp_tc) { return mlp_tc ? 1 : 4; }
 constexpr int lf_advance_threads(bool mlp_tc) { return 512 / lf_advance_ctas_per_sm(mlp_tc); }
 // Largest cooperative grid of the one-launch advance (CTAs that fit on the
 // device at once), 0 if none.
