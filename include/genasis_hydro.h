@@ -70,7 +70,8 @@ extern "C" {
 #define GENASIS_BC_OUTFLOW 2   /* copy of the edge cell */
 
 #define GENASIS_FP64 0         /* state stored and processed in FP64 */
-#define GENASIS_FP32_MIXED 1   /* state stored and fluxes in FP32; internal-energy
+#define GENASIS_FP32_MIXED 1   /* state stored and fluxes in FP32 (FP32 results
+                                  below 2^-126 flush to zero); internal-energy
                                   cancellation, dt and totals reductions in FP64 */
 #define GENASIS_FP64_DW 2      /* state and arithmetic as double-word pairs of FP32
                                   (hi + lo, ~48 bits) on the FP32 pipes; the same
