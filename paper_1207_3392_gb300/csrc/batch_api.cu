@@ -584,7 +584,7 @@ int genasis_batch_autotune(genasis_batch_t b, int trial_steps, const char* cache
   float best = 1e30f;
   int best_tile = 0, best_chunk = 32, rc = GENASIS_OK;
   for (int tile = 0; tile < batch_tile_count() && !rc; ++tile)
-    for (int ch : {16, 32, 64}) {
+    for (int ch : {16, 32, 64, 128, 256}) {
       rc = configure(b, tile, ch);
       if (!rc) rc = run_steps(b, 1, 0.1, 0.0);  // warm-up and capture
       if (!rc) {
